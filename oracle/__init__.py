@@ -1,0 +1,29 @@
+"""Plain FP64 CPU oracle of the space-time least-squares Schroedinger solver.
+
+TEST INFRASTRUCTURE ONLY. This package is the slow, obviously-correct
+restatement of the method of Bressan, Kushova, Sangalli and Tani
+(arXiv 2311.18461) that the CUDA path is checked against. Only the tests,
+`__graft_entry__.smoke()` and the `cpu_baseline` / `--impl reference` legs
+of `bench.py` may import it. The CUDA library never calls into it and it
+never calls into the CUDA library: the two share no code. Seeded input
+generators live in the separate `inputs` package, which holds none of the
+method's arithmetic.
+
+Modules, each citing the passage of the paper it restates:
+  bspline   -- open knot vectors, Cox-de Boor B-splines and derivatives (Sec. 3.1)
+  matrices  -- univariate Galerkin matrices, Dirichlet/initial restriction (Eq. time_mat, Eq. space_mat, Sec. 3.2)
+  system    -- Kronecker form of the least-squares matrix A (Eq. syst_mat),
+               its separable-potential extension, mode products (Eq. kron_vec_multi)
+  direct    -- independent (d+1)-dimensional quadrature of (S B_j, S B_i) (Sec. 4.3)
+  fd        -- the preconditioner P-hat (Eq. prec_definition) and Algorithm 1
+  pcg       -- preconditioned conjugate gradients (Sec. 5.3, Sec. 6)
+  rhs       -- load vector F(S B_i) and liftings of initial / boundary data (Sec. 2.2, Sec. 4.3)
+  norms     -- L2 and V-norm errors (Sec. 2.1, Theorem 2)
+
+Parity status: every function here is pinned by a `-m "not gpu"` test against
+closed forms, the paper's printed numbers, invariants or brute force, except
+the separable-potential terms, whose Kronecker expansion is pinned only by
+brute-force quadrature of the same sesquilinear form (the paper has no
+potential), and the inexact-preconditioner (flexible) CG variant, which the
+paper does not define: parity unpinned beyond the exact-preconditioner case.
+"""

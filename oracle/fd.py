@@ -1,0 +1,77 @@
+"""The preconditioner P-hat and its Fast Diagonalization (Eq. prec_definition, Eq. space_eig,
+Eq. preconditioner_str2, Algorithm 1 of Sec. 5).
+
+Test infrastructure: part of the CPU oracle, see `oracle/__init__.py`.
+
+P-hat = M_s (x) L_t + nu^2 L_s^T M_s^{-1} L_s (x) M_t + nu L_s (x) (W_t + W_t^*)
+with the spatial factors of the parametric box (0,1)^d (the spatial matrices
+of the potential-free operator, Sec. 5). Algorithm 1:
+  1. generalized eigendecompositions L_l U_l = M_l U_l Lambda_l, U_l^T M_l U_l = I;
+  2. y = (U_s^T (x) I_t) r;
+  3. x_i = H_i^{-1} y_i with H_i = L_t + nu^2 lambda_i^2 M_t + nu lambda_i (W_t + W_t^*),
+     lambda_i = [Lambda_s]_{ii} = sum_l lambda_{l, i_l};
+  4. s = (U_s (x) I_t) x.
+(Step 4 prints an undefined s-tilde; it is read as the vector x of step 3.)
+"""
+import numpy as np
+import scipy.linalg
+
+from .system import mode_product
+
+
+def dense_P(disc):
+    """Assembled P-hat (dense; tiny meshes only), straight from Eq. prec_definition."""
+    d, nu = disc.d, disc.nu
+    Ms = np.ones((1, 1))
+    Ls = np.zeros((1, 1))
+    for l in range(1, d + 1):
+        M, L = disc.sp[l]["M"], disc.sp[l]["L"]
+        Ls = np.kron(M, Ls) + np.kron(L, Ms)
+        Ms = np.kron(M, Ms)
+    LML = Ls.T @ np.linalg.solve(Ms, Ls)
+    return np.kron(Ms, disc.Lt) + nu ** 2 * np.kron(LML, disc.Mt) + nu * np.kron(Ls, disc.Wsym)
+
+
+class FastDiagonalization:
+    """Algorithm 1 (setup = step 1 and the H_i; apply = steps 2-4)."""
+
+    def __init__(self, disc):
+        self.disc = disc
+        self.U, self.lam = [None], [None]
+        for l in range(1, disc.d + 1):
+            lam, U = scipy.linalg.eigh(disc.sp[l]["L"], disc.sp[l]["M"])   # step 1, Eq. space_eig
+            self.U.append(U)
+            self.lam.append(lam)
+        # Lambda_s in vec order (x_1 fastest): spatial array of shape (n_d, ..., n_1)
+        lam_s = np.zeros(disc.shape[:-1])
+        for l in range(1, disc.d + 1):
+            shp = [1] * disc.d
+            shp[disc.d - l] = disc.n[l]
+            lam_s = lam_s + self.lam[l].reshape(shp)
+        self.lam_s = lam_s.ravel()
+
+    def H(self, lam_i):
+        """H_i = L_t + nu^2 lambda_i^2 M_t + nu lambda_i (W_t + W_t^*)."""
+        disc = self.disc
+        return disc.Lt + disc.nu ** 2 * lam_i ** 2 * disc.Mt + disc.nu * lam_i * disc.Wsym
+
+    def apply(self, r, chunk=512):
+        """s = P-hat^{-1} r by steps 2-4 of Algorithm 1."""
+        disc = self.disc
+        Y = np.asarray(r, dtype=complex).reshape(disc.shape)
+        for l in range(1, disc.d + 1):                      # step 2: y = (U_s^T (x) I) r
+            Y = mode_product(Y, self.U[l].T, disc.axis(l))
+        Yf = Y.reshape(disc.N_s, disc.n[0])
+        Xf = np.empty_like(Yf)
+        for a in range(0, disc.N_s, chunk):                 # step 3: x_i = H_i^{-1} y_i (pagewise solve)
+            lam = self.lam_s[a:a + chunk]
+            Hs = np.stack([self.H(li) for li in lam])
+            Xf[a:a + chunk] = np.linalg.solve(Hs, Yf[a:a + chunk][:, :, None])[:, :, 0]
+        X = Xf.reshape(disc.shape)
+        for l in range(1, disc.d + 1):                      # step 4: s = (U_s (x) I) x
+            X = mode_product(X, self.U[l], disc.axis(l))
+        return X.ravel()
+
+    def kappa_U(self, l):
+        """kappa_2(U_l) = ||U_l||_2 ||U_l^{-1}||_2 (Table cond_number_space)."""
+        return np.linalg.cond(self.U[l], 2)
