@@ -1,0 +1,422 @@
+#!/usr/bin/env python
+"""Benchmark of the P-hat-preconditioned CG solve of the space-time least-squares system.
+
+One step = one solve as timed in the paper's Table 1: preconditioner setup
+(generalized eigendecompositions and the banded factors of every H_i,
+stst_build_fd) plus PCG from the zero initial guess to relative residual tol
+(stst_pcg_solve), on the 2D+t workload with p=3, 64^2 x 64 elements, the
+harmonic potential scaled to [0,10] and a windowed Gaussian wavepacket as
+initial datum (278,850 complex unknowns). Inputs are resident in HBM when
+the timed region starts; the L2 cache is flushed before every step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--config c2] [--prec fp64|fp32]
+
+One JSON line on rank 0. With --impl reference the CPU oracle is timed
+instead (a bounded sample: setup plus a few PCG iterations, extrapolated to
+the iteration count of the full oracle solve, which runs once untimed).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PCG solve time to rel. residual 1e-8 and apply_prec DOF/s; fraction of roofline"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+N_SM = 152
+FP64_FMA_PER_CLK_SM = 2      # 1.25 TFLOP/s nominal FP64 at 2.07 GHz over 152 SMs
+FP32_FMA_PER_CLK_SM = 128
+SM_MAX_MHZ_NOMINAL = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c2")
+    ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32"])
+    ap.add_argument("--solver", default="pcg", choices=["pcg", "ir"])
+    ap.add_argument("--inner-tol", type=float, default=1e-4)
+    return ap.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return dict(PEAKS_FALLBACK), "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2311_18461_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path))
+    except Exception:
+        return None
+    if rec.get("source_hash") != source_hash():
+        return None
+    v = rec.get("kernels", {}).get(kernel)
+    return v.get("dram_bytes_per_launch") if v else None
+
+
+def workload(cfg_name):
+    from inputs import CONFIGS, potential, initial_factors
+    cfg = CONFIGS[cfg_name]
+    return cfg, potential(cfg), initial_factors(cfg)
+
+
+def sample_1d(prob, fn, l):
+    import numpy as np
+    x = prob.quad_points(l).cpu().numpy()
+    return np.asarray(fn(x)) * np.ones_like(x)
+
+
+def build_problem(cfg, V, u0, prec, stream):
+    import numpy as np
+    import torch
+    import paper_2311_18461_gb300 as S
+    d = cfg["d"]
+    prob = S.Problem(d, cfg["n_el"], [cfg["p"]] * (d + 1), T=cfg["T"], nu=cfg["nu"],
+                     prec_mode=S.STST_PREC_FP64 if prec == "fp64" else S.STST_PREC_FP32, stream=stream)
+    if V:
+        cols = [sample_1d(prob, term[l - 1], l) for term in V for l in range(1, d + 1)]
+        prob.set_potential(torch.tensor(np.concatenate(cols), dtype=torch.float64, device="cuda"), len(V))
+    grids = [prob.quad_points(l).cpu().numpy() for l in range(1, d + 1)]
+    U = np.ones([1] * d, dtype=complex)
+    for l, g in enumerate(u0):
+        shp = [1] * d
+        shp[d - 1 - l] = len(grids[l])
+        U = U * np.asarray(g(grids[l])).reshape(shp)
+    u0_qp = torch.tensor(np.ascontiguousarray(U).ravel(), dtype=torch.complex128, device="cuda")
+    b = prob.rhs(None, u0_qp)
+    torch.cuda.synchronize()
+    return prob, b
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import paper_2311_18461_gb300 as S
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    cfg, V, u0 = workload(args.config)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        prob, b = build_problem(cfg, V, u0, args.prec, stream)
+    tol = 1e-8
+    x = prob.vec()
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+
+    def solve(xv, rhs=None):
+        rhs = b if rhs is None else rhs
+        xv.zero_()
+        prob.build_fd()
+        if args.solver == "ir":
+            st, inner, outer, rr = S.stst_ir_solve(prob.h, rhs, xv, tol, 30, args.inner_tol, 200)
+            return st, inner, rr
+        return S.stst_pcg_solve(prob.h, rhs, xv, tol, 200)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            st, it, rr = solve(x)
+        assert st == 0, f"solve failed: status {st}"
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local)
+        sampler.start()
+        times, iters = [], []
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st, it, rr = solve(x)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            iters.append(it)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        if dist:
+            dist.barrier()
+        ms = statistics.mean(times)
+        if dist:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+
+        # end to end through the C ABI with host buffers: pinned rhs in, solution out, every step
+        b_host = b.cpu().pin_memory()
+        x_host = torch.empty_like(b_host).pin_memory()
+        b_dev = torch.empty_like(b)
+        e2e = []
+        for k in range(args.steps + 1):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b_dev.copy_(b_host, non_blocking=True)
+            st, it2, rr2 = solve(x, b_dev)
+            x_host.copy_(x, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            if k > 0:
+                e2e.append(e0.elapsed_time(e1))
+        e2e_ms = statistics.mean(e2e)
+
+        # per-kernel device times of one solve (profiled run: plain launches bracketed by events)
+        S.stst_profile(prob.h, 1)
+        flush.fill_(1)
+        solve(x)
+        prof = S.stst_profile_read(prob.h)
+        S.stst_profile(prob.h, 0)
+        # standalone operator timings
+        r = prob.vec()
+        r.real.normal_()
+        s = prob.vec()
+        y = prob.vec()
+
+        def tm(fn, n=30):
+            for _ in range(3):
+                fn()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(n):
+                fn()
+            e1.record(stream)
+            e1.synchronize()
+            return e0.elapsed_time(e1) / n
+
+        t_prec = tm(lambda: S.stst_apply_prec(prob.h, r, s))
+        t_sys = tm(lambda: S.stst_apply_sys(prob.h, r, y))
+
+    n_dof = prob.n_dof
+    d = cfg["d"]
+    n_l = prob.n[1:]
+    n_passes, band_apps, flops_dof = S.stst_plan_info(prob.h)
+    peaks, peak_src = load_peaks()
+    clk = clocks.get("sm_mhz") or SM_MAX_MHZ_NOMINAL
+    fp64_peak = N_SM * FP64_FMA_PER_CLK_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+    fp32_peak = N_SM * FP32_FMA_PER_CLK_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+    # dominant kernel of the step = largest total device time in the profiled solve
+    dom = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
+    roof = None
+    if dom:
+        cnt, tot = prof[dom]
+        per_launch_s = tot / cnt / 1e3
+        if dom.startswith("modeprod"):
+            flops = 4.0 * (sum(n_l) / d) * n_dof
+            peak = fp64_peak if dom.endswith("f64") else fp32_peak
+            roof = {"kernel": dom, "bound": "alu", "achieved": flops / per_launch_s / 1e12,
+                    "peak": peak, "unit": "TFLOP/s"}
+        elif dom.startswith("pass"):
+            flops = flops_dof * n_dof / n_passes
+            peak = fp64_peak if dom.endswith("f64") else fp32_peak
+            roof = {"kernel": dom, "bound": "alu", "achieved": flops / per_launch_s / 1e12,
+                    "peak": peak, "unit": "TFLOP/s"}
+        else:
+            vec_bytes = 16 * n_dof
+            roof = {"kernel": dom, "bound": "hbm", "achieved": 3 * vec_bytes / per_launch_s / 1e9,
+                    "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+        roof["peak_source"] = ("derived: %d SMs x %d FMA/clk x 2 x %.0f MHz (nominal max clock)"
+                               % (N_SM, FP64_FMA_PER_CLK_SM if dom.endswith("f64") else FP32_FMA_PER_CLK_SM,
+                                  SM_MAX_MHZ_NOMINAL)) if roof["bound"] == "alu" else f"hbm_gbs of {peak_src}"
+        roof["launch_ms"] = per_launch_s * 1e3
+        roof["traffic"] = traffic_for(dom)
+        roof["share_of_solve"] = tot / sum(v[1] for v in prof.values())
+    out = {
+        "metric": METRIC,
+        "value": ms / 1e3,
+        "unit": "s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": max(args.warmup, 3),
+        "ms_per_step": ms,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if args.prec == "fp64" else "f64+f32",
+        "data": "synthetic",
+        "config": {"workload": f"{args.config}: 2D+t p={cfg['p']} {cfg['n_el'][1]}^2x{cfg['n_el'][0]} elements, "
+                               f"harmonic V in [0,10], windowed Gaussian wavepacket u0, complex128, tol {tol:g}",
+                   "n_dof": n_dof, "preconditioner": args.prec, "solver": args.solver,
+                   "pcg_iterations": statistics.median(iters),
+                   "step": "build_fd (setup) + pcg_solve from x0 = 0", "l2": "flushed (512 MB write) before each step",
+                   "parallelism": f"replicas x{world}"},
+        "apply_prec_dofs_per_s": n_dof / (t_prec / 1e3),
+        "apply_prec_ms": t_prec,
+        "apply_sys_ms": t_sys,
+        "mat_vec_plan": {"passes": n_passes, "band_apps_per_dof": band_apps, "flops_per_dof": flops_dof},
+        "kernels_ms_per_solve": {k: round(v[1], 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
+        "kernel_launches_per_solve": {k: v[0] for k, v in prof.items()},
+        "gpu_launches": int(sum(v[0] for v in prof.values())) * args.steps,
+        "roofline": roof,
+        "clocks": clocks,
+        "e2e": {"value": e2e_ms / 1e3, "unit": "s", "h2d_bytes_per_step": 16 * n_dof, "d2h_bytes_per_step": 16 * n_dof},
+        "paper_context": {"table": "Table 1, p=3, n_el=64, V=0 travelling wave, 1 CPU thread at 1 GHz",
+                          "seconds": 4.7142, "iterations": 8},
+    }
+    if rank == 0 and world == 1:
+        out["cpu_baseline"] = cpu_baseline(args.config, iters_full=None)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    prob.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def _oracle_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        return max(i.get("num_threads", 1) for i in threadpool_info()) or os.cpu_count()
+    except Exception:
+        return os.cpu_count()
+
+
+def cpu_baseline(cfg_name, iters_full=None, sample_iters=2):
+    """The oracle timed on this host: setup + `sample_iters` PCG iterations, extrapolated to the full count."""
+    import numpy as np
+    from inputs import CONFIGS, potential, initial_factors, product_fn
+    from oracle import fd, pcg, rhs
+    from oracle.system import Discretization
+    cfg = CONFIGS[cfg_name]
+    d = cfg["d"]
+    disc = Discretization(cfg["n_el"], [cfg["p"]] * (d + 1), T=cfg["T"], nu=cfg["nu"], potential=potential(cfg))
+    b, _ = rhs.rhs_initial(disc, None, product_fn(initial_factors(cfg)))
+    terms = disc.terms()
+    if iters_full is None:
+        F = fd.FastDiagonalization(disc)
+        _, iters_full, _, _ = pcg.pcg(disc.apply, F.apply, b, tol=1e-8, maxit=200)
+    t0 = time.perf_counter()
+    F = fd.FastDiagonalization(disc)
+    t1 = time.perf_counter()
+    pcg.pcg(disc.apply, F.apply, b, tol=0.0, maxit=sample_iters)
+    t2 = time.perf_counter()
+    per_it = (t2 - t1) / sample_iters
+    value = (t1 - t0) + per_it * iters_full
+    return {"value": value, "unit": "s", "cores": _oracle_threads(), "kind": "oracle",
+            "sample": f"FD setup + {sample_iters} PCG iterations of the same workload, extrapolated to the "
+                      f"{iters_full} iterations of the full oracle solve (numpy FP64, {len(terms)} Kronecker terms)"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    from inputs import CONFIGS, potential, initial_factors, product_fn
+    from oracle import fd, pcg, rhs
+    from oracle.system import Discretization
+    cfg = CONFIGS[args.config]
+    d = cfg["d"]
+    disc = Discretization(cfg["n_el"], [cfg["p"]] * (d + 1), T=cfg["T"], nu=cfg["nu"], potential=potential(cfg))
+    b, _ = rhs.rhs_initial(disc, None, product_fn(initial_factors(cfg)))
+    F = fd.FastDiagonalization(disc)
+    _, iters_full, _, _ = pcg.pcg(disc.apply, F.apply, b, tol=1e-8, maxit=200)
+    vals = []
+    for k in range(args.warmup + args.steps):
+        r = cpu_baseline(args.config, iters_full=iters_full)
+        if k >= args.warmup:
+            vals.append(r["value"])
+    v = statistics.mean(vals)
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"{args.config} (same as ours)", "pcg_iterations": iters_full},
+           "cpu_baseline": {"value": v, "unit": "s", "cores": r["cores"], "kind": "oracle", "sample": r["sample"]},
+           "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        from paper_2311_18461_gb300 import build
+        build.build()
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

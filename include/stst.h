@@ -1,0 +1,195 @@
+/*
+ * stst.h -- C ABI of the GB300 space-time least-squares Schroedinger solver.
+ *
+ * The library solves the Hermitian positive definite linear system A u = f of
+ * the space-time isogeometric least-squares discretization of
+ *     i d_t u - nu Delta u (+ V(x) u) = f  in (0,T) x (0,1)^d,
+ *     u = 0 on (0,T) x boundary,  u(0) = u0,
+ * (Bressan, Kushova, Sangalli, Tani, arXiv 2311.18461: Sec. 2, Sec. 4.2-4.3)
+ * by conjugate gradients preconditioned with the paper's P-hat, applied by
+ * Fast Diagonalization (Sec. 5, Algorithm 1). Every numerical step runs in
+ * the library's CUDA kernels on the device the handle was created on.
+ *
+ * Conventions shared by all calls
+ *  - Directions: index 0 is time, 1..d are the spatial directions.
+ *  - Discretization: uniform open knot vectors with n_el[l] elements, degree
+ *    p[l], maximal regularity (Sec. 3.1); time basis without its first
+ *    function (n_t = n_el[0] + p[0] - 1), spatial bases without the two end
+ *    functions (n_l = n_el[l] + p[l] - 2) (Sec. 3.2, Eq. all_basis).
+ *  - Vectors: complex128 stored as interleaved (re, im) doubles, ordered by the
+ *    vec operator of Sec. 3.3 with time as the FASTEST index:
+ *      index = i_t + n_t * (i_1 + n_1 * (i_2 + n_2 * i_3)),  length N_dof = n_t * prod n_l.
+ *  - Quadrature: (p[l] + 2) Gauss-Legendre points per element in every
+ *    direction, element by element from left to right.
+ *  - Memory: every vector argument is a DEVICE pointer owned by the caller,
+ *    16-byte aligned; calls are ordered on the handle's CUDA stream. The
+ *    library owns all factors and workspaces of a handle; no call after
+ *    stst_create allocates device memory, except stst_set_potential (which
+ *    re-plans) and stst_batch_create.
+ *  - Return value: STST_OK (0); a positive value is a numerical outcome, a
+ *    negative value is a usage or CUDA error (see stst_strerror).
+ */
+#ifndef STST_H
+#define STST_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  STST_OK = 0,
+  STST_NOT_CONVERGED = 1, /* maxit reached before the tolerance                          */
+  STST_BREAKDOWN = 2,     /* <p, A p> <= 0 or not finite in CG                            */
+  STST_NOT_HPD = 3,       /* a factorization met a non-positive pivot                     */
+  STST_TIMEOUT = 4,       /* a bounded device-side wait expired                           */
+  STST_ERR_ARG = -1,      /* invalid argument (null pointer, size out of range, ...)      */
+  STST_ERR_HANDLE = -2,   /* null or destroyed handle                                     */
+  STST_ERR_OOM = -3,      /* device allocation failed                                     */
+  STST_ERR_CUDA = -4,     /* a CUDA runtime call failed                                   */
+  STST_ERR_STATE = -5     /* call out of order (e.g. apply_prec before build_fd)          */
+};
+
+/* Precision of the preconditioner's Fast Diagonalization (the system
+ * mat-vec, residuals, inner products and updates are always FP64). */
+enum {
+  STST_PREC_FP64 = 0, /* mode products and time solves in FP64                        */
+  STST_PREC_FP32 = 1, /* mode products and time solves in FP32                        */
+  STST_PREC_BF16 = 2  /* mode products on tensor cores, BF16 operands, FP32 accumulate */
+};
+
+typedef struct stst_problem *stst_handle;
+
+/*
+ * stst_create: set up a discretization (Sec. 3-4) on the unit box (0,1)^d in
+ * space and (0,T) in time, with coefficient nu > 0 (Eq. problem).
+ *   d          number of spatial directions, 1..3
+ *   n_el[d+1]  elements per direction (time first), each >= 1
+ *   p[d+1]     degrees per direction (time first); p[0] in 1..8, p[l] in 2..8
+ *              (C^1 in space, Assumption 2); n_l = n_el[l]+p[l]-2 <= 128
+ *   T, nu      final time and diffusion coefficient, > 0
+ *   prec_mode  STST_PREC_*
+ *   stream     cudaStream_t used by every call of the handle (NULL: legacy default stream)
+ * Assembles the 1D matrices on the device (Eq. time_mat, Eq. space_mat).
+ * Allocates the handle's device memory. Errors: ERR_ARG, ERR_OOM, ERR_CUDA.
+ */
+int stst_create(stst_handle *h, int d, const int *n_el, const int *p, double T, double nu, int prec_mode,
+                void *stream);
+
+/* stst_destroy: free the handle and all its device memory (synchronizes its stream). */
+int stst_destroy(stst_handle h);
+
+/* stst_strerror: static description of a status code. */
+const char *stst_strerror(int status);
+
+/* stst_sizes: n_dof (unknowns) and the reduced sizes n[0..d] (time first). Host outputs. */
+int stst_sizes(stst_handle h, long long *n_dof, int *n);
+
+/*
+ * stst_quadrature_points: the n_el[dir]*(p[dir]+2) Gauss points of direction
+ * dir (0 = time on (0,T), else (0,1)), written to the device array pts.
+ * Callers sample potentials, forcing and initial data at these points.
+ */
+int stst_quadrature_points(stst_handle h, int dir, double *pts);
+
+/*
+ * stst_assemble_1d: univariate Galerkin matrices of Eq. time_mat / Eq. space_mat
+ * for degree p, n_el uniform elements on (0, length):
+ *   M = int b_i b_j, L = int b'_j b'_i, J = int b''_i b''_j, K = int b'_j b_i,
+ *   K2 = int b''_j b_i  (times the weight w(x) if weight != NULL).
+ * bc: 0 keep all m = n_el+p functions, 1 drop the first (time), 2 drop the
+ * first and last (space). weight: NULL or a device array with the weight at
+ * the n_el*(p+2) quadrature points of (0, length).
+ * Outputs (device, any may be NULL): band storage, row-major n x (2p+1),
+ * out[i*(2p+1) + (j-i+p)] = A[i][j] for |i-j| <= p (zero outside the matrix).
+ * n_out (host, may be NULL) receives the number of rows n. Ordered on `stream`.
+ */
+int stst_assemble_1d(int p, int n_el, double length, int bc, const double *weight, double *M, double *L, double *J,
+                     double *K, double *K2, int *n_out, void *stream);
+
+/*
+ * stst_set_potential: a separable potential V(x) = sum_{r<rank} prod_l v_{r,l}(x_l)
+ * added to the operator, S_V = i d_t - nu Delta + V (an extension; the paper
+ * treats V = 0). v_qp (device) packs, for r = 0..rank-1 and l = 1..d, the values
+ * of v_{r,l} at the quadrature points of direction l (stst_quadrature_points).
+ * rank = 0 removes the potential. The preconditioner stays the V-free P-hat
+ * (Eq. prec_definition). Re-plans the mat-vec; may allocate. rank <= 3.
+ */
+int stst_set_potential(stst_handle h, int rank, const double *v_qp);
+
+/*
+ * stst_build_fd: preconditioner setup, step 1 of Algorithm 1 plus the
+ * per-eigenvalue time operators H_i = L_t + nu^2 lambda_i^2 M_t + nu lambda_i (W_t + W_t^*)
+ * (Sec. 5.2). Generalized eigenpairs of (L_l, M_l) with U_l^T M_l U_l = I
+ * (Eq. space_eig), banded Cholesky factors of every H_i. Returns STST_NOT_HPD
+ * if a factorization meets a non-positive pivot.
+ */
+int stst_build_fd(stst_handle h);
+
+/* stst_apply_sys: y = A x, Eq. syst_mat (+ potential terms). x, y: device, N_dof complex, distinct. */
+int stst_apply_sys(stst_handle h, const double *x, double *y);
+
+/* stst_apply_prec: s = P-hat^{-1} r by Algorithm 1 steps 2-4 in the handle's precision. Needs build_fd. */
+int stst_apply_prec(stst_handle h, const double *r, double *s);
+
+/*
+ * stst_rhs: right-hand side of the reduced system (Sec. 4.3, Sec. 2.2):
+ *   rhs_i = int f conj(S_V B_i)  -  sum_j A_full(b_1 B_j, S_V B_i) c_j,
+ * where c = M_s^{-1} (u0, B_j) is the L2 projection of u0 onto the spatial
+ * space and b_1 the first time basis function (the lifting of the initial datum).
+ *   f_qp   NULL (f = 0) or device complex array on the space-time quadrature
+ *          grid, time fastest: f_qp[q_t + Q_t*(q_1 + Q_1*(q_2 + ...))]
+ *   u0_qp  NULL (u0 = 0) or device complex array on the spatial grid, x_1 fastest
+ *   rhs    device, N_dof complex (output)
+ *   c0     NULL or device, N_s complex: receives c (the lifted initial datum;
+ *          the discrete solution is u_h = u_bar + b_1(t) sum_j c_j B_j(x)).
+ */
+int stst_rhs(stst_handle h, const double *f_qp, const double *u0_qp, double *rhs, double *c0);
+
+/*
+ * stst_pcg_solve: P-hat-preconditioned conjugate gradients (Sec. 5.3, Sec. 6)
+ * from the initial guess in x (x is overwritten by the solution). Stops when
+ * ||rhs - A x_k||_2 <= tol ||rhs||_2 (recursive residual) or after maxit
+ * iterations. With a low-precision preconditioner the Polak-Ribiere
+ * (flexible) beta is used. iters, relres: host outputs (may be NULL).
+ * Needs build_fd. Returns OK, NOT_CONVERGED or BREAKDOWN. The loop runs as
+ * one CUDA graph with a device-side while condition: the host waits once.
+ */
+int stst_pcg_solve(stst_handle h, const double *rhs, double *x, double tol, int maxit, int *iters, double *relres);
+
+/*
+ * stst_ir_solve: mixed-precision iterative refinement (an extension): FP64
+ * residual rhs - A x and FP64 update x += d around an inner FP32 PCG on
+ * A d = r (FP32 mat-vec, FP32/BF16 preconditioner, inner tolerance inner_tol).
+ * Stops when the FP64 relative residual <= tol or after maxit outer steps.
+ * iters receives the total inner iterations, outer the outer steps.
+ */
+int stst_ir_solve(stst_handle h, const double *rhs, double *x, double tol, int maxit, double inner_tol,
+                  int inner_maxit, int *iters, int *outer, double *relres);
+
+/*
+ * stst_profile: enable (1) or disable (0) per-kernel timing for the handle's
+ * calls. Enabling clears previous records. While enabled every kernel launch
+ * of a call is bracketed by CUDA events on the handle's stream and the call
+ * synchronizes on return; stst_pcg_solve then runs its loop as plain launches
+ * with one host check per iteration instead of the CUDA graph.
+ * stst_profile_read: record idx (0-based) -> kernel name (NUL-terminated, at
+ * most name_len bytes), launch count and total device milliseconds. Returns
+ * STST_ERR_ARG past the last record. Host outputs.
+ */
+int stst_profile(stst_handle h, int enable);
+
+/*
+ * stst_plan_info: the sum-factorised mat-vec chosen for this handle.
+ * n_passes (host, may be NULL): kernel launches per stst_apply_sys.
+ * band_apps (host, may be NULL): banded 1D applications per unknown (each is
+ * 2p+1 complex-by-real multiply-adds, 4(2p+1) flops).
+ * flops_per_dof (host, may be NULL): the algorithmic flops of one apply_sys per unknown.
+ */
+int stst_plan_info(stst_handle h, int *n_passes, int *band_apps, double *flops_per_dof);
+int stst_profile_read(stst_handle h, int idx, char *name, int name_len, long long *count, double *total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STST_H */

@@ -1,0 +1,19 @@
+"""GB300-native space-time least-squares solver for the Schroedinger equation.
+
+A thin ctypes binding of the CUDA library `libstst.so` (C ABI declared in
+include/stst.h). The functions keep the C names and only marshal arguments:
+every numerical step runs in the library's CUDA kernels. PyTorch provides
+device memory and streams. Importing works without a GPU; calling into the
+library needs the built extension and raises if it is missing.
+"""
+from ._lib import (StstError, lib, library_path, stst_create, stst_destroy, stst_strerror, stst_sizes,
+                   stst_quadrature_points, stst_assemble_1d, stst_set_potential, stst_build_fd, stst_apply_sys,
+                   stst_apply_prec, stst_rhs, stst_pcg_solve, stst_ir_solve, stst_profile,
+                   stst_profile_read, stst_plan_info, Problem,
+                   STST_PREC_FP64, STST_PREC_FP32, STST_PREC_BF16)
+
+__all__ = ["StstError", "lib", "library_path", "stst_create", "stst_destroy", "stst_strerror", "stst_sizes",
+           "stst_quadrature_points", "stst_assemble_1d", "stst_set_potential", "stst_build_fd", "stst_apply_sys",
+           "stst_apply_prec", "stst_rhs", "stst_pcg_solve", "stst_ir_solve", "stst_profile",
+           "stst_profile_read", "stst_plan_info", "Problem",
+           "STST_PREC_FP64", "STST_PREC_FP32", "STST_PREC_BF16"]

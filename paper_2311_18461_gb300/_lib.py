@@ -1,0 +1,259 @@
+"""ctypes binding of libstst.so: one Python function per C entry point, same names and argument order.
+
+Vectors are torch tensors on the CUDA device (complex128, contiguous) or raw
+device pointers (int); the binding passes their addresses. Negative status
+codes raise StstError; non-negative ones are returned.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+library_path = os.path.join(HERE, "libstst.so")
+
+STST_PREC_FP64, STST_PREC_FP32, STST_PREC_BF16 = 0, 1, 2
+STATUS = {0: "OK", 1: "NOT_CONVERGED", 2: "BREAKDOWN", 3: "NOT_HPD", 4: "TIMEOUT", -1: "ERR_ARG",
+          -2: "ERR_HANDLE", -3: "ERR_OOM", -4: "ERR_CUDA", -5: "ERR_STATE"}
+
+
+class StstError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({_strerror(status)})")
+
+
+_lib = None
+
+
+def lib():
+    """Load libstst.so (raises if it has not been built: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(library_path):
+            raise RuntimeError(f"CUDA library not built: {library_path} missing (run __graft_entry__.build())")
+        L = ctypes.CDLL(library_path)
+        P, I, D, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+        IP, DP = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+        sig = {
+            "stst_create": [ctypes.POINTER(P), I, IP, IP, D, D, I, P],
+            "stst_destroy": [P],
+            "stst_sizes": [P, ctypes.POINTER(LL), IP],
+            "stst_quadrature_points": [P, I, P],
+            "stst_assemble_1d": [I, I, D, I, P, P, P, P, P, P, IP, P],
+            "stst_set_potential": [P, I, P],
+            "stst_build_fd": [P],
+            "stst_apply_sys": [P, P, P],
+            "stst_apply_prec": [P, P, P],
+            "stst_rhs": [P, P, P, P, P],
+            "stst_pcg_solve": [P, P, P, D, I, IP, DP],
+            "stst_ir_solve": [P, P, P, D, I, D, I, IP, IP, DP],
+            "stst_profile": [P, I],
+            "stst_plan_info": [P, IP, IP, DP],
+            "stst_profile_read": [P, I, ctypes.c_char_p, I, ctypes.POINTER(LL), DP],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = I
+        L.stst_strerror.argtypes = [I]
+        L.stst_strerror.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _strerror(status):
+    try:
+        return lib().stst_strerror(status).decode()
+    except Exception:
+        return ""
+
+
+def stst_strerror(status):
+    return lib().stst_strerror(status).decode()
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda:
+        raise ValueError("device tensor expected")
+    if not t.is_contiguous():
+        raise ValueError("contiguous tensor expected")
+    return t.data_ptr()
+
+
+def _chk(status, where):
+    if status < 0:
+        raise StstError(status, where)
+    return status
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def stst_create(d, n_el, p, T=1.0, nu=1.0, prec_mode=STST_PREC_FP64, stream=None):
+    h = ctypes.c_void_p()
+    ne = (ctypes.c_int * (d + 1))(*n_el)
+    pp = (ctypes.c_int * (d + 1))(*p)
+    _chk(lib().stst_create(ctypes.byref(h), d, ne, pp, float(T), float(nu), int(prec_mode), _stream_ptr(stream)),
+         "stst_create")
+    return h
+
+
+def stst_destroy(h):
+    return _chk(lib().stst_destroy(h), "stst_destroy")
+
+
+def stst_sizes(h, d):
+    n_dof = ctypes.c_longlong()
+    n = (ctypes.c_int * (d + 1))()
+    _chk(lib().stst_sizes(h, ctypes.byref(n_dof), n), "stst_sizes")
+    return n_dof.value, list(n)
+
+
+def stst_quadrature_points(h, dir, pts):
+    return _chk(lib().stst_quadrature_points(h, int(dir), _ptr(pts)), "stst_quadrature_points")
+
+
+def stst_assemble_1d(p, n_el, length, bc, weight, M, L, J, K, K2, stream=None):
+    n = ctypes.c_int()
+    _chk(lib().stst_assemble_1d(int(p), int(n_el), float(length), int(bc), _ptr(weight), _ptr(M), _ptr(L), _ptr(J),
+                                _ptr(K), _ptr(K2), ctypes.byref(n), _stream_ptr(stream)), "stst_assemble_1d")
+    return n.value
+
+
+def stst_set_potential(h, rank, v_qp):
+    return _chk(lib().stst_set_potential(h, int(rank), _ptr(v_qp)), "stst_set_potential")
+
+
+def stst_build_fd(h):
+    return _chk(lib().stst_build_fd(h), "stst_build_fd")
+
+
+def stst_apply_sys(h, x, y):
+    return _chk(lib().stst_apply_sys(h, _ptr(x), _ptr(y)), "stst_apply_sys")
+
+
+def stst_apply_prec(h, r, s):
+    return _chk(lib().stst_apply_prec(h, _ptr(r), _ptr(s)), "stst_apply_prec")
+
+
+def stst_rhs(h, f_qp, u0_qp, rhs, c0):
+    return _chk(lib().stst_rhs(h, _ptr(f_qp), _ptr(u0_qp), _ptr(rhs), _ptr(c0)), "stst_rhs")
+
+
+def stst_pcg_solve(h, rhs, x, tol, maxit):
+    it = ctypes.c_int()
+    rr = ctypes.c_double()
+    s = _chk(lib().stst_pcg_solve(h, _ptr(rhs), _ptr(x), float(tol), int(maxit), ctypes.byref(it), ctypes.byref(rr)),
+             "stst_pcg_solve")
+    return s, it.value, rr.value
+
+
+def stst_ir_solve(h, rhs, x, tol, maxit, inner_tol, inner_maxit):
+    it = ctypes.c_int()
+    outer = ctypes.c_int()
+    rr = ctypes.c_double()
+    s = _chk(lib().stst_ir_solve(h, _ptr(rhs), _ptr(x), float(tol), int(maxit), float(inner_tol), int(inner_maxit),
+                                 ctypes.byref(it), ctypes.byref(outer), ctypes.byref(rr)), "stst_ir_solve")
+    return s, it.value, outer.value, rr.value
+
+
+def stst_profile(h, enable):
+    return _chk(lib().stst_profile(h, int(enable)), "stst_profile")
+
+
+def stst_plan_info(h):
+    n = ctypes.c_int()
+    a = ctypes.c_int()
+    f = ctypes.c_double()
+    _chk(lib().stst_plan_info(h, ctypes.byref(n), ctypes.byref(a), ctypes.byref(f)), "stst_plan_info")
+    return n.value, a.value, f.value
+
+
+def stst_profile_read(h):
+    """All records as {kernel name: (launches, total ms)}."""
+    out = {}
+    idx = 0
+    while True:
+        name = ctypes.create_string_buffer(64)
+        cnt = ctypes.c_longlong()
+        ms = ctypes.c_double()
+        if lib().stst_profile_read(h, idx, name, 64, ctypes.byref(cnt), ctypes.byref(ms)) != 0:
+            break
+        out[name.value.decode()] = (cnt.value, ms.value)
+        idx += 1
+    return out
+
+
+class Problem:
+    """Owns a handle; convenience around the C calls (allocation of device vectors via torch)."""
+
+    def __init__(self, d, n_el, p, T=1.0, nu=1.0, prec_mode=STST_PREC_FP64, stream=None, device="cuda"):
+        import torch
+        self.torch = torch
+        self.d = d
+        if isinstance(p, int):
+            p = [p] * (d + 1)
+        self.p = list(p)
+        self.n_el = list(n_el)
+        self.device = device
+        self.h = stst_create(d, n_el, p, T, nu, prec_mode, stream)
+        self.n_dof, self.n = stst_sizes(self.h, d)
+        self.N_s = self.n_dof // self.n[0]
+
+    def close(self):
+        if self.h is not None:
+            stst_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def vec(self):
+        return self.torch.zeros(self.n_dof, dtype=self.torch.complex128, device=self.device)
+
+    def quad_points(self, l):
+        Q = self.n_el[l] * (self.p[l] + 2)
+        t = self.torch.empty(Q, dtype=self.torch.float64, device=self.device)
+        stst_quadrature_points(self.h, l, t)
+        return t
+
+    def set_potential(self, v_qp, rank):
+        return stst_set_potential(self.h, rank, v_qp)
+
+    def build_fd(self):
+        return stst_build_fd(self.h)
+
+    def apply_sys(self, x, y=None):
+        y = self.vec() if y is None else y
+        stst_apply_sys(self.h, x, y)
+        return y
+
+    def apply_prec(self, r, s=None):
+        s = self.vec() if s is None else s
+        stst_apply_prec(self.h, r, s)
+        return s
+
+    def rhs(self, f_qp=None, u0_qp=None, want_c0=False):
+        b = self.vec()
+        c0 = self.torch.zeros(self.N_s, dtype=self.torch.complex128, device=self.device) if want_c0 else None
+        stst_rhs(self.h, f_qp, u0_qp, b, c0)
+        return (b, c0) if want_c0 else b
+
+    def pcg(self, rhs, x=None, tol=1e-8, maxit=200):
+        x = self.vec() if x is None else x
+        s, it, rr = stst_pcg_solve(self.h, rhs, x, tol, maxit)
+        return x, s, it, rr
+
+    def ir(self, rhs, x=None, tol=1e-8, maxit=20, inner_tol=1e-4, inner_maxit=50):
+        x = self.vec() if x is None else x
+        s, it, outer, rr = stst_ir_solve(self.h, rhs, x, tol, maxit, inner_tol, inner_maxit)
+        return x, s, it, outer, rr

@@ -1,0 +1,543 @@
+// Operator applications on the device.
+//  * k_pass: one level of the sum-factorised Kronecker mat-vec (Eq. syst_mat applied matrix-free
+//    through Eq. kron_vec_multi): banded 1D matrices applied along one tensor mode, several inputs
+//    combined into several outputs with real (or imaginary) coefficients.
+//  * k_modeprod: dense mode-n product with a spatial eigenvector matrix (Algorithm 1, steps 2 and 4).
+//  * k_timesolve: the N_s independent banded Hermitian solves H_i x_i = y_i (Algorithm 1, step 3,
+//    Eq. independent_problems) with precomputed Cholesky factors, one thread per system.
+#include "common.cuh"
+
+template <typename R> struct C2;
+template <> struct C2<double> { using T = double2; };
+template <> struct C2<float> { using T = float2; };
+
+template <typename T> __device__ __forceinline__ double2 to_d2(T v) { return make_double2((double)v.x, (double)v.y); }
+template <typename T> __device__ __forceinline__ T from_d2(double2 v);
+template <> __device__ __forceinline__ double2 from_d2<double2>(double2 v) { return v; }
+template <> __device__ __forceinline__ float2 from_d2<float2>(double2 v) { return make_float2((float)v.x, (float)v.y); }
+
+// Deterministic block reduction of one double (blockDim.x multiple of 32, <= 1024).
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    int nw = blockDim.x >> 5;
+    t = (l < nw) ? sh[l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  return t;  // valid in thread 0
+}
+
+// ------------------------------------------------------------------------------------------------
+// Pass kernel. Output element (o, j, c) of output b = sum over its contributions (input a,
+// matrix m, coefficient s): s * sum_k m[j][k] * in_a[o, j + row_off - P + k, c].
+// ------------------------------------------------------------------------------------------------
+struct PassK {
+  int n_out;
+  int c_start[PASS_MAXOUT + 1];
+  int c_in[PASS_MAXAPP];
+  int c_imag[PASS_MAXAPP];
+  double c_coef[PASS_MAXAPP];
+  const void *c_mat[PASS_MAXAPP];
+  const void *in[PASS_MAXIN];
+  void *out[PASS_MAXOUT];
+  int n_mode_out, n_mode_in, row_off;
+  long long inner, outer;
+  int epi;
+  const void *b;
+  const void *dotvec;
+  double *dot_partials;
+  double *dot2_partials;
+  const int *done;
+};
+
+template <typename R, int P>
+__global__ void __launch_bounds__(256) k_pass(const __grid_constant__ PassK k) {
+  using T = typename C2<R>::T;
+  if (k.done && *k.done) return;
+  __shared__ double sh[32];
+  const long long total = k.outer * k.n_mode_out * k.inner;
+  double dacc = 0.0, d2acc = 0.0;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    long long c = idx % k.inner;
+    long long t = idx / k.inner;
+    int j = (int)(t % k.n_mode_out);
+    long long o = t / k.n_mode_out;
+    const long long base = o * k.n_mode_in * k.inner + c;
+    for (int b = 0; b < k.n_out; ++b) {
+      R ax = 0, ay = 0;
+      for (int ci = k.c_start[b]; ci < k.c_start[b + 1]; ++ci) {
+        const T *in = (const T *)k.in[k.c_in[ci]];
+        const R *m = (const R *)k.c_mat[ci] + j * (2 * P + 1);
+        R vx = 0, vy = 0;
+#pragma unroll
+        for (int q = 0; q <= 2 * P; ++q) {
+          int jj = j + k.row_off - P + q;
+          if (jj >= 0 && jj < k.n_mode_in) {
+            T xv = in[base + (long long)jj * k.inner];
+            R mv = m[q];
+            vx += mv * xv.x;
+            vy += mv * xv.y;
+          }
+        }
+        R s = (R)k.c_coef[ci];
+        if (k.c_imag[ci]) {  // s * i * v
+          ax -= s * vy;
+          ay += s * vx;
+        } else {
+          ax += s * vx;
+          ay += s * vy;
+        }
+      }
+      T *out = (T *)k.out[b];
+      if (k.epi == 1) {  // out = b - v
+        T bv = ((const T *)k.b)[idx];
+        ax = bv.x - ax;
+        ay = bv.y - ay;
+      }
+      T res;
+      res.x = ax;
+      res.y = ay;
+      out[idx] = res;
+      if (k.dotvec) {
+        T dv = ((const T *)k.dotvec)[idx];
+        dacc += (double)dv.x * (double)ax + (double)dv.y * (double)ay;  // Re(conj(d) * out)
+      }
+      if (k.dot2_partials) d2acc += (double)ax * ax + (double)ay * ay;
+    }
+  }
+  if (k.dot_partials) {
+    double s = block_sum(dacc, sh);
+    if (threadIdx.x == 0) k.dot_partials[blockIdx.x] = s;
+  }
+  if (k.dot2_partials) {
+    double s = block_sum(d2acc, sh);
+    if (threadIdx.x == 0) k.dot2_partials[blockIdx.x] = s;
+  }
+}
+
+template <typename R>
+static int launch_pass_t(const PassK &k, int p, int grid, cudaStream_t s) {
+  STST_PROF(sizeof(R) == 8 ? "pass_f64" : "pass_f32", s);
+  switch (p) {
+#define CASE(PP) case PP: k_pass<R, PP><<<grid, 256, 0, s>>>(k); break;
+    CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+#undef CASE
+    default: return STST_ERR_ARG;
+  }
+  STST_CUDA(cudaGetLastError());
+  return STST_OK;
+}
+
+// Number of CTAs of every kernel that produces per-CTA partial sums.
+int reduction_grid(long long total) {
+  int g = grid_for(total, 256);
+  if (g > 1024) g = 1024;
+  if (g < 1) g = 1;
+  return g;
+}
+
+int run_plan(const Plan &plan, const void *x, void *y, int precision, int epi, const void *b, const void *dotvec,
+             double *dot_partials, const int *done, cudaStream_t s, const void *dot2vec, double *dot2_partials) {
+  (void)dot2vec;
+  const int np = (int)plan.passes.size();
+  for (int ip = 0; ip < np; ++ip) {
+    const PassParams &pp = plan.passes[ip];
+    PassK k;
+    k.n_out = pp.n_out;
+    int c = 0;
+    k.c_start[0] = 0;
+    // contributions are stored output-major in PassParams (app == contribution)
+    for (int a = 0; a < pp.n_app; ++a) {
+      k.c_in[a] = pp.app_in[a];
+      k.c_imag[a] = pp.app_imag[a];
+      k.c_mat[a] = precision == 1 ? (const void *)pp.mat32[a] : (const void *)pp.mat[a];
+    }
+    for (int bo = 0; bo < pp.n_out; ++bo) {
+      for (int a = 0; a < pp.n_app; ++a) {
+        if (pp.coef[a][bo] != 0.0) c++;
+      }
+      k.c_start[bo + 1] = c;
+    }
+    // reorder contributions output-major
+    {
+      int pos = 0;
+      int tin[PASS_MAXAPP], tim[PASS_MAXAPP];
+      double tco[PASS_MAXAPP];
+      const void *tma[PASS_MAXAPP];
+      for (int bo = 0; bo < pp.n_out; ++bo)
+        for (int a = 0; a < pp.n_app; ++a)
+          if (pp.coef[a][bo] != 0.0) {
+            if (pos >= PASS_MAXAPP) return STST_ERR_ARG;
+            tin[pos] = pp.app_in[a];
+            tim[pos] = pp.app_imag[a];
+            tco[pos] = pp.coef[a][bo];
+            tma[pos] = precision == 1 ? (const void *)pp.mat32[a] : (const void *)pp.mat[a];
+            pos++;
+          }
+      for (int q = 0; q < pos; ++q) {
+        k.c_in[q] = tin[q];
+        k.c_imag[q] = tim[q];
+        k.c_coef[q] = tco[q];
+        k.c_mat[q] = tma[q];
+      }
+    }
+    for (int a = 0; a < pp.n_in; ++a) k.in[a] = pp.in[a];
+    for (int bo = 0; bo < pp.n_out; ++bo) k.out[bo] = pp.out[bo];
+    if (ip == 0) k.in[0] = x;
+    k.n_mode_out = pp.n_mode_out;
+    k.n_mode_in = pp.n_mode_in;
+    k.row_off = pp.row_off;
+    k.inner = pp.inner;
+    k.outer = pp.outer;
+    k.epi = 0;
+    k.b = nullptr;
+    k.dotvec = nullptr;
+    k.dot_partials = nullptr;
+    k.dot2_partials = nullptr;
+    k.done = done;
+    long long total = pp.outer * (long long)pp.n_mode_out * pp.inner;
+    int grid = reduction_grid(total);
+    if (ip == np - 1) {
+      k.out[0] = y;
+      k.epi = epi;
+      k.b = b;
+      k.dotvec = dotvec;
+      k.dot_partials = dot_partials;
+      k.dot2_partials = dot2_partials;
+    } else {
+      grid = grid_for(total, 256);
+      if (grid > 152 * 16) grid = 152 * 16;
+    }
+    int st = precision == 1 ? launch_pass_t<float>(k, pp.p, grid, s) : launch_pass_t<double>(k, pp.p, grid, s);
+    if (st != STST_OK) return st;
+  }
+  return STST_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Mode product with a dense n x n matrix U (row-major U[i*n + j]):
+//   forward (Algorithm 1 step 2): y[o, j, c] = sum_i U[i][j] x[o, i, c]   (x times U^T along the mode)
+//   backward (step 4):            y[o, i, c] = sum_j U[i][j] x[o, j, c]
+// CTA: a tile of CW flattened columns (o, c); U and the x tile staged in shared memory.
+// ------------------------------------------------------------------------------------------------
+template <typename R, typename TI, typename TO, int CW>
+__global__ void __launch_bounds__(256) k_modeprod(const TI *__restrict__ X, TO *__restrict__ Y, const R *__restrict__ U,
+                                                  int n, long long inner, long long ncols, int backward,
+                                                  const TO *__restrict__ dotvec, double *dot_partials,
+                                                  const int *done) {
+  using T = typename C2<R>::T;
+  if (done && *done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R *sU = (R *)smem_raw;                               // n*n
+  T *sX = (T *)(smem_raw + ((n * n * sizeof(R) + 15) / 16) * 16);  // n * CW
+  __shared__ double sh[32];
+  const long long col0 = (long long)blockIdx.x * CW;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    int i = e / n, j = e % n;
+    sU[e] = backward ? U[j * n + i] : U[e];  // sU[i*n + j] = coefficient of x_i in y_j
+  }
+  for (int e = threadIdx.x; e < n * CW; e += blockDim.x) {
+    int i = e / CW, cc = e % CW;
+    long long col = col0 + cc;
+    T v;
+    v.x = 0;
+    v.y = 0;
+    if (col < ncols) {
+      long long o = col / inner, c = col % inner;
+      TI xv = X[(o * n + i) * inner + c];
+      v.x = (R)xv.x;
+      v.y = (R)xv.y;
+    }
+    sX[i * CW + cc] = v;
+  }
+  __syncthreads();
+  constexpr int G = 256 / CW;  // row groups
+  const int cc = threadIdx.x % CW, g = threadIdx.x / CW;
+  const long long col = col0 + cc;
+  double dacc = 0.0;
+  long long o = col / inner, c = col % inner;
+  for (int j0 = g * 4; j0 < n; j0 += G * 4) {
+    R ax[4] = {0, 0, 0, 0}, ay[4] = {0, 0, 0, 0};
+    for (int i = 0; i < n; ++i) {
+      T xv = sX[i * CW + cc];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        R u = (j0 + q < n) ? sU[i * n + j0 + q] : (R)0;
+        ax[q] += u * xv.x;
+        ay[q] += u * xv.y;
+      }
+    }
+    if (col < ncols) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        int j = j0 + q;
+        if (j < n) {
+          long long idx = (o * n + j) * inner + c;
+          TO r;
+          r.x = ax[q];
+          r.y = ay[q];
+          Y[idx] = r;
+          if (dotvec) {
+            TO dv = dotvec[idx];
+            dacc += (double)dv.x * (double)r.x + (double)dv.y * (double)r.y;
+          }
+        }
+      }
+    }
+  }
+  if (dot_partials) {
+    double s = block_sum(dacc, sh);
+    if (threadIdx.x == 0) dot_partials[blockIdx.x] = s;
+  }
+}
+
+template <typename R, typename TI, typename TO>
+static int launch_modeprod(const TI *X, TO *Y, const R *U, int n, long long inner, long long outer, int backward,
+                           const TO *dotvec, double *dot_partials, const int *done, cudaStream_t s,
+                           int *grid_out) {
+  long long ncols = inner * outer;
+  constexpr int CW = 32;
+  int grid = grid_for(ncols, CW);
+  if (dot_partials && grid > STST_MAXPART) return STST_ERR_ARG;
+  STST_PROF(sizeof(R) == 8 ? "modeprod_f64" : "modeprod_f32", s);
+  size_t sm = ((n * n * sizeof(R) + 15) / 16) * 16 + (size_t)n * CW * sizeof(typename C2<R>::T);
+  if (sm > 48 * 1024) {
+    STST_CUDA(cudaFuncSetAttribute(k_modeprod<R, TI, TO, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  }
+  k_modeprod<R, TI, TO, CW><<<grid, 256, sm, s>>>(X, Y, U, n, inner, ncols, backward, dotvec, dot_partials, done);
+  STST_CUDA(cudaGetLastError());
+  if (grid_out) *grid_out = grid;
+  return STST_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Time solves. Factor layout: G[(t*P + (k-1))*Ns + i] = G_i[t][t-k] (complex), D[t*Ns + i] = 1/G_i[t][t].
+// Data layout: time fastest, y[i*nt + t]. A CTA of 32 threads handles 32 systems and stages
+// TC time steps of its systems through shared memory so global accesses stay coalesced.
+// ------------------------------------------------------------------------------------------------
+template <typename R, int P, int TC>
+__global__ void __launch_bounds__(32) k_timesolve(void *__restrict__ Yv, const void *__restrict__ Gv,
+                                                  const R *__restrict__ D, int nt, long long Ns, const int *done) {
+  using T = typename C2<R>::T;
+  if (done && *done) return;
+  T *Y = (T *)Yv;
+  const T *G = (const T *)Gv;
+  __shared__ T tile[TC][33];
+  const long long i0 = (long long)blockIdx.x * 32;
+  const int s = threadIdx.x;
+  const long long i = i0 + s;
+  const bool act = i < Ns;
+  T zw[P];
+#pragma unroll
+  for (int a = 0; a < P; ++a) { zw[a].x = 0; zw[a].y = 0; }
+  // forward substitution: G z = y
+  for (int t0 = 0; t0 < nt; t0 += TC) {
+    int tc = min(TC, nt - t0);
+    for (int e = s; e < 32 * TC; e += 32) {
+      int ss = e / TC, u = e % TC;
+      if (u < tc && i0 + ss < Ns) tile[u][ss] = Y[(i0 + ss) * nt + t0 + u];
+    }
+    __syncwarp();
+    if (act) {
+      for (int u = 0; u < tc; ++u) {
+        int t = t0 + u;
+        T y = tile[u][s];
+        R ax = y.x, ay = y.y;
+#pragma unroll
+        for (int k = 1; k <= P; ++k) {
+          T g = G[((long long)t * P + (k - 1)) * Ns + i];
+          T z = zw[k - 1];
+          ax -= g.x * z.x - g.y * z.y;
+          ay -= g.x * z.y + g.y * z.x;
+        }
+        R dinv = D[(long long)t * Ns + i];
+        T z;
+        z.x = ax * dinv;
+        z.y = ay * dinv;
+#pragma unroll
+        for (int a = P - 1; a > 0; --a) zw[a] = zw[a - 1];
+        zw[0] = z;
+        tile[u][s] = z;
+      }
+    }
+    __syncwarp();
+    for (int e = s; e < 32 * TC; e += 32) {
+      int ss = e / TC, u = e % TC;
+      if (u < tc && i0 + ss < Ns) Y[(i0 + ss) * nt + t0 + u] = tile[u][ss];
+    }
+    __syncwarp();
+  }
+  // backward substitution: G^H x = z ; x_t = (z_t - sum_k conj(G[t+k][t]) x_{t+k}) / G[t][t]
+  T xw[P];
+  T gw[P][P];  // gw[a][k-1] = G[t+1+a][t+1+a-k]
+#pragma unroll
+  for (int a = 0; a < P; ++a) {
+    xw[a].x = 0;
+    xw[a].y = 0;
+#pragma unroll
+    for (int k = 0; k < P; ++k) { gw[a][k].x = 0; gw[a][k].y = 0; }
+  }
+  const int nchunks = (nt + TC - 1) / TC;
+  for (int ch = nchunks - 1; ch >= 0; --ch) {
+    int t0 = ch * TC;
+    int tc = min(TC, nt - t0);
+    for (int e = s; e < 32 * TC; e += 32) {
+      int ss = e / TC, u = e % TC;
+      if (u < tc && i0 + ss < Ns) tile[u][ss] = Y[(i0 + ss) * nt + t0 + u];
+    }
+    __syncwarp();
+    if (act) {
+      for (int u = tc - 1; u >= 0; --u) {
+        int t = t0 + u;
+        T z = tile[u][s];
+        R ax = z.x, ay = z.y;
+#pragma unroll
+        for (int a = 0; a < P; ++a) {
+          T g = gw[a][a];  // G[t+1+a][t] (offset a+1)
+          T xv = xw[a];
+          // conj(g) * x
+          ax -= g.x * xv.x + g.y * xv.y;
+          ay -= g.x * xv.y - g.y * xv.x;
+        }
+        R dinv = D[(long long)t * Ns + i];
+        T x;
+        x.x = ax * dinv;
+        x.y = ay * dinv;
+#pragma unroll
+        for (int a = P - 1; a > 0; --a) {
+          xw[a] = xw[a - 1];
+#pragma unroll
+          for (int k = 0; k < P; ++k) gw[a][k] = gw[a - 1][k];
+        }
+        xw[0] = x;
+#pragma unroll
+        for (int k = 1; k <= P; ++k) gw[0][k - 1] = G[((long long)t * P + (k - 1)) * Ns + i];
+        tile[u][s] = x;
+      }
+    }
+    __syncwarp();
+    for (int e = s; e < 32 * TC; e += 32) {
+      int ss = e / TC, u = e % TC;
+      if (u < tc && i0 + ss < Ns) Y[(i0 + ss) * nt + t0 + u] = tile[u][ss];
+    }
+    __syncwarp();
+  }
+}
+
+template <typename R>
+static int launch_timesolve(void *Y, const void *G, const R *D, int nt, long long Ns, int P, const int *done,
+                            cudaStream_t s) {
+  int grid = grid_for(Ns, 32);
+  STST_PROF(sizeof(R) == 8 ? "timesolve_f64" : "timesolve_f32", s);
+  switch (P) {
+#define CASE(PP) case PP: k_timesolve<R, PP, 16><<<grid, 32, 0, s>>>(Y, G, D, nt, Ns, done); break;
+    CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+#undef CASE
+    default: return STST_ERR_ARG;
+  }
+  STST_CUDA(cudaGetLastError());
+  return STST_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Algorithm 1 steps 2-4: s = (U_s (x) I) H^{-1} (U_s^T (x) I) r.
+// precision 0: FP64 throughout (scratch buffers are double2); 1: FP32 mode products and solves
+// (r read as FP64, s written as FP64; intermediates float2 in the scratch buffers).
+// in32 / out32: optional FP32 input / output (inner FP32 solver), replacing r / s.
+// The final mode product optionally accumulates per-CTA partials of Re<r, s> into dot_partials.
+// ------------------------------------------------------------------------------------------------
+int fd_apply(stst_problem *h, const double *r, double *s, int precision, const void *dotvec, double *dot_partials,
+             const int *done, void *bufA, void *bufB, float *out32, const float *in32) {
+  const int d = h->d, nt = h->n_t();
+  const long long Ns = h->N_s;
+  cudaStream_t st = h->stream;
+  // tensor geometry of mode l (1..d) in the time-fastest layout: inner = nt * prod_{k<l} n_k
+  long long inner[STST_MAXD + 1], outer[STST_MAXD + 1];
+  {
+    long long acc = nt;
+    for (int l = 1; l <= d; ++l) {
+      inner[l] = acc;
+      acc *= h->dir[l].n;
+    }
+    long long tot = acc;
+    for (int l = 1; l <= d; ++l) outer[l] = tot / (inner[l] * h->dir[l].n);
+  }
+  if (precision == 0) {
+    // forward: r -> A -> B -> ... (alternating), solve in place, backward to s
+    const double2 *src = (const double2 *)r;
+    double2 *bufs[2] = {(double2 *)bufA, (double2 *)bufB};
+    int cur = 0;
+    for (int l = 1; l <= d; ++l) {
+      double2 *dst = bufs[cur];
+      STST_TRY((launch_modeprod<double, double2, double2>(src, dst, h->U[l], h->dir[l].n, inner[l], outer[l], 0,
+                                                           nullptr, nullptr, done, st, nullptr)));
+      src = dst;
+      cur ^= 1;
+    }
+    STST_TRY(launch_timesolve<double>((void *)src, h->Hg, h->Hd, nt, Ns, h->dir[0].p, done, st));
+    for (int l = d; l >= 1; --l) {
+      double2 *dst = (l == 1) ? (double2 *)s : bufs[cur];
+      int grid = 0;
+      STST_TRY((launch_modeprod<double, double2, double2>(src, dst, h->U[l], h->dir[l].n, inner[l], outer[l], 1,
+                                                           l == 1 ? (const double2 *)dotvec : nullptr,
+                                                           l == 1 ? dot_partials : nullptr, done, st, &grid)));
+      src = dst;
+      cur ^= 1;
+    }
+    return STST_OK;
+  }
+  // FP32
+  float2 *bufs[2] = {(float2 *)bufA, (float2 *)bufB};
+  int cur = 0;
+  const float2 *src32 = nullptr;
+  for (int l = 1; l <= d; ++l) {
+    float2 *dst = bufs[cur];
+    if (l == 1) {
+      if (in32) {
+        STST_TRY((launch_modeprod<float, float2, float2>((const float2 *)in32, dst, h->U32[l], h->dir[l].n, inner[l],
+                                                         outer[l], 0, nullptr, nullptr, done, st, nullptr)));
+      } else {
+        STST_TRY((launch_modeprod<float, double2, float2>((const double2 *)r, dst, h->U32[l], h->dir[l].n, inner[l],
+                                                          outer[l], 0, nullptr, nullptr, done, st, nullptr)));
+      }
+    } else {
+      STST_TRY((launch_modeprod<float, float2, float2>(src32, dst, h->U32[l], h->dir[l].n, inner[l], outer[l], 0,
+                                                       nullptr, nullptr, done, st, nullptr)));
+    }
+    src32 = dst;
+    cur ^= 1;
+  }
+  STST_TRY(launch_timesolve<float>((void *)src32, h->Hg32, h->Hd32, nt, Ns, h->dir[0].p, done, st));
+  for (int l = d; l >= 1; --l) {
+    if (l == 1) {
+      if (out32) {
+        STST_TRY((launch_modeprod<float, float2, float2>(src32, (float2 *)out32, h->U32[l], h->dir[l].n, inner[l],
+                                                         outer[l], 1, (const float2 *)dotvec, dot_partials, done, st,
+                                                         nullptr)));
+      } else {
+        STST_TRY((launch_modeprod<float, float2, double2>(src32, (double2 *)s, h->U32[l], h->dir[l].n, inner[l],
+                                                          outer[l], 1, (const double2 *)dotvec, dot_partials, done,
+                                                          st, nullptr)));
+      }
+    } else {
+      float2 *dst = bufs[cur];
+      STST_TRY((launch_modeprod<float, float2, float2>(src32, dst, h->U32[l], h->dir[l].n, inner[l], outer[l], 1,
+                                                       nullptr, nullptr, done, st, nullptr)));
+      src32 = dst;
+      cur ^= 1;
+    }
+  }
+  return STST_OK;
+}
+
+// grid of the last backward mode product (number of partials it writes)
+int fd_partials_count(stst_problem *h) {
+  long long ncols = h->N_dof / h->dir[1].n;
+  return grid_for(ncols, 32);
+}

@@ -1,0 +1,188 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <vector>
+#include "../../include/stst.h"
+#include "prof.cuh"
+
+#define STST_MAXD 3
+#define STST_MAXP 8
+#define STST_MAXN_SPACE 128
+
+// ---- error handling -------------------------------------------------------------------------
+#define STST_CUDA(call)                                   \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) { stst_last_cuda = e_; return STST_ERR_CUDA; } \
+  } while (0)
+#define STST_TRY(call)                  \
+  do {                                  \
+    int s_ = (call);                    \
+    if (s_ != STST_OK) return s_;       \
+  } while (0)
+
+extern thread_local cudaError_t stst_last_cuda;
+
+// ---- matrix kinds assembled on the device (band storage n x (2p+1), row-major) ----------------
+enum MatKind { MK_M = 0, MK_L = 1, MK_J = 2, MK_K = 3, MK_K2 = 4, MK_KA = 5, MK_K2S = 6 };
+// MK_KA = K - K^T (time advection, W + W^* = i KA); MK_K2S = K2 + K2^T.
+
+struct DirInfo {
+  int p, n_el, nq, m, n;  // degree, elements, quad points / element, full size, reduced size
+  double len;              // T for time, 1 for space
+  int off;                 // first kept full index (1 for time and space)
+  int Q() const { return n_el * nq; }
+};
+
+struct BandMat {
+  double *d = nullptr;  // n x (2p+1)
+  int n = 0, p = 0;
+};
+
+// ---- sum-factorised mat-vec plan --------------------------------------------------------------
+#define PASS_MAXIN 16
+#define PASS_MAXAPP 24
+#define PASS_MAXOUT 12
+
+struct PassParams {
+  int mode;                  // 0 = time, l >= 1 spatial direction
+  int p;                     // half bandwidth of this mode's matrices
+  int n_in, n_app, n_out;
+  int n_mode_out, n_mode_in, row_off;  // output / input extent along the mode; input index = j + row_off - p + k
+  long long inner, outer;    // tensor = (outer, n_mode, inner) complex elements
+  const void *in[PASS_MAXIN];
+  void *out[PASS_MAXOUT];
+  const double *mat[PASS_MAXAPP];    // FP64 band matrices (n_mode_out rows x (2p+1))
+  const float *mat32[PASS_MAXAPP];   // FP32 copies
+  int app_in[PASS_MAXAPP];
+  int app_imag[PASS_MAXAPP];         // multiply by i
+  float coef32[PASS_MAXAPP][PASS_MAXOUT];
+  double coef[PASS_MAXAPP][PASS_MAXOUT];
+  // epilogue (final pass only, n_out == 1)
+  int epi;                    // 0 store, 1 out = b - v
+  const void *b;
+  const void *dotvec;         // if non-null: partial sums of Re(conj(dotvec) . out) per CTA
+  double *dot_partials;
+  const void *dot2vec;        // second partial: ||out||^2 when dot2vec == out sentinel (see kernel)
+  double *dot2_partials;
+  const int *done;            // if non-null and *done: skip
+};
+
+struct Plan {
+  std::vector<PassParams> passes;
+  int n_levels = 0;
+};
+
+// ---- PCG control block (device) ---------------------------------------------------------------
+struct PcgCtl {
+  double ff, rr, rho, pq, alpha, beta, rz_old, tol2;
+  int it, maxit, done, status;
+  int flexible, pad;
+};
+
+// ---- handle -------------------------------------------------------------------------------------
+struct stst_problem {
+  int magic;
+  int d;
+  DirInfo dir[STST_MAXD + 1];
+  double T, nu;
+  int prec_mode;
+  cudaStream_t stream;
+  int own_stream;                  // stream created by the handle (caller passed NULL)
+  long long N_s, N_dof;
+  int n_t() const { return dir[0].n; }
+
+  // 1D matrices: per direction, list indexed by matrix id (0 M, 1 L, 2 J, then weighted ones)
+  std::vector<BandMat> mats[STST_MAXD + 1];
+  std::vector<float *> mats32[STST_MAXD + 1];
+  // time: KA = K - K^T (id 2 in mats[0]: 0 L? see capi: time ids 0 L, 1 M, 2 KA)
+  BandMat tfull[3];  // full-basis time L, M, KA (rows 1..p of the full matrices used by the lifting)
+  float *tfull32[3];
+  // quadrature and basis tables per direction
+  double *qpts[STST_MAXD + 1];
+  double *qwts[STST_MAXD + 1];
+  double *tab[STST_MAXD + 1];     // Q x (p+1) x 3 : value, d1, d2 of functions e..e+p (full index) at each point
+  double *mchol[STST_MAXD + 1];   // banded Cholesky of the reduced mass, n x (p+1)
+
+  // potential
+  int pot_rank;
+  std::vector<double *> pot_bufs;  // device buffers of weights (owned)
+
+  // FD
+  int fd_ready;
+  int eig_src[STST_MAXD + 1];
+  double *U[STST_MAXD + 1];
+  float *U32[STST_MAXD + 1];
+  __nv_bfloat16 *Ubf[STST_MAXD + 1];
+  double *lam[STST_MAXD + 1];
+  double *oa_work;                 // refinement workspace
+  void *Hg;                        // FP64 factors: n_t x p x N_s complex
+  double *Hd;                      // FP64 inverse diagonals n_t x N_s
+  void *Hg32;                      // FP32 factors
+  float *Hd32;
+  int *flags;                      // device status flags (NOT_HPD, ...)
+
+  // plans
+  Plan sys_plan, lift_plan;
+  std::vector<void *> pool;        // intermediate tensors of the plans (FP64 sized)
+
+  // workspaces (N_dof complex FP64 each)
+  double *w_x, *w_r, *w_z, *w_zold, *w_p, *w_q, *w_f, *w_t1, *w_t2;
+  float *v_d, *v_r, *v_z, *v_p, *v_q;  // FP32 inner-solver vectors (N_dof complex each)
+  PcgCtl *ctl2;                        // inner-solver control block
+  double *partials;                // 4 x MAXPART
+  PcgCtl *ctl;
+  PcgCtl *ctl_host;                // pinned
+  double *proj_work;               // rhs / projection workspace
+  size_t proj_work_bytes;
+
+  // PCG graph
+  cudaGraphExec_t pcg_exec;
+  int pcg_graph_valid;
+  int pcg_graph_flexible;
+  cudaGraphExec_t ir_exec;
+  int ir_graph_valid;
+
+  // tracing
+  int prof_on;
+  Profiler *prof;
+};
+
+// Installs the handle's profiler for the duration of an API call and flushes it on exit.
+struct ApiScope {
+  stst_problem *h;
+  explicit ApiScope(stst_problem *hh) : h(hh) { g_prof = (h && h->prof_on) ? h->prof : nullptr; }
+  ~ApiScope() {
+    if (g_prof) prof_flush(g_prof);
+    g_prof = nullptr;
+  }
+};
+
+#define STST_MAGIC 0x57575354
+#define STST_MAXPART 65536
+
+// ---- kernels / launchers (defined in the .cu files) ------------------------------------------
+int launch_assemble_band(int kind, int p, int n_el, double len, int nq, int off, int n_rows, int n_cols,
+                         const double *weight, double *out, cudaStream_t s);
+int launch_quadrature(int p, int n_el, double len, int nq, double *pts, double *wts, double *tab, cudaStream_t s);
+int launch_mass_cholesky(const BandMat &M, double *chol, int *flags, cudaStream_t s);
+int launch_to_f32(const double *src, float *dst, long long n, cudaStream_t s);
+int launch_weight_product(const double *a, const double *b, double *out, int n, cudaStream_t s);
+
+int run_plan(const Plan &plan, const void *x, void *y, int precision, int epi, const void *b, const void *dotvec,
+             double *dot_partials, const int *done, cudaStream_t s, const void *dot2vec = nullptr,
+             double *dot2_partials = nullptr);
+int fd_setup(stst_problem *h);
+// dotvec: FP64 vector (double2) when the output is FP64, FP32 (float2) when out32 is given.
+int fd_apply(stst_problem *h, const double *r, double *s, int precision, const void *dotvec, double *dot_partials,
+             const int *done, void *f32_scratch_a, void *f32_scratch_b, float *out32 = nullptr,
+             const float *in32 = nullptr);
+int rhs_compute(stst_problem *h, const double *f_qp, const double *u0_qp, double *rhs, double *c0);
+
+int pcg_run(stst_problem *h, const double *rhs, double *x, double tol, int maxit, int *iters, double *relres);
+int ir_run(stst_problem *h, const double *rhs, double *x, double tol, int maxit, double inner_tol,
+           int inner_maxit, int *iters, int *outer, double *relres);
+
+int grid_for(long long n, int block);

@@ -1,0 +1,232 @@
+"""Parity of the CUDA library (through its C ABI) with the FP64 CPU oracle.
+
+Tolerances: FP64 path 1e-12 relative (operators) and 1e-10 (PCG iterates,
+the same algorithm in the same order); FP32 preconditioner 1e-5 relative on
+P-hat^{-1} r; solutions of the mixed path within 1e-8 of the FP64 oracle's.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2311_18461_gb300 as S
+from inputs import harmonic_potential, bump_potential, wavepacket_factors, wavepacket_params, random_complex
+from oracle import fd as ofd, pcg as opcg, rhs as orhs, matrices as omat
+from tests._common import (rel_err, oracle_disc, sample_potential, sample_initial, sample_forcing, to_dev, to_np)
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    # (n_el, p, potential)
+    ([32, 32], 2, None),
+    ([7, 9], [1, 3], None),
+    ([9, 11, 7], [2, 3, 2], None),
+    ([9, 11, 7], [2, 3, 3], "harmonic"),
+    ([5, 6, 5, 7], [2, 2, 3, 2], None),
+    ([5, 6, 5, 4], [3, 2, 2, 2], "bump"),
+    ([3, 1], [1, 2], None),
+]
+
+
+def _pot(kind, d):
+    if kind is None:
+        return None
+    return harmonic_potential(d) if kind == "harmonic" else bump_potential(d)
+
+
+def _problem(n_el, p, kind, prec=S.STST_PREC_FP64, T=1.0, nu=1.0):
+    d = len(n_el) - 1
+    pl = [p] * (d + 1) if isinstance(p, int) else list(p)
+    prob = S.Problem(d, n_el, pl, T=T, nu=nu, prec_mode=prec)
+    V = _pot(kind, d)
+    if V is not None:
+        prob.set_potential(sample_potential(prob, V), len(V))
+    disc = oracle_disc(n_el, pl, T=T, nu=nu, potential=V)
+    return prob, disc
+
+
+def _band_to_dense(band, n, p):
+    A = np.zeros((n, n))
+    for i in range(n):
+        for k in range(2 * p + 1):
+            j = i - p + k
+            if 0 <= j < n:
+                A[i, j] = band[i * (2 * p + 1) + k]
+    return A
+
+
+@pytest.mark.parametrize("p,n_el,length,bc", [(2, 5, 1.0, 2), (3, 9, 2.0, 1), (4, 6, 0.7, 0), (1, 4, 1.3, 1),
+                                              (8, 3, 1.0, 2)])
+def test_assemble_1d(p, n_el, length, bc):
+    m = n_el + p
+    n = m - bc
+    bufs = [torch.zeros(n * (2 * p + 1), dtype=torch.float64, device="cuda") for _ in range(5)]
+    assert S.stst_assemble_1d(p, n_el, length, bc, None, *bufs) == n
+    torch.cuda.synchronize()
+    F = omat.assemble_1d(p, n_el, length)
+    sl = {0: slice(0, m), 1: slice(1, m), 2: slice(1, m - 1)}[bc]
+    for key, b in zip(["M", "L", "J", "K", "K2"], bufs):
+        ref = F[key][sl, sl]
+        got = _band_to_dense(to_np(b), n, p)
+        assert rel_err(got, ref) < 1e-13, key
+
+
+def test_quadrature_points():
+    prob, disc = _problem([4, 6, 5], [2, 3, 4], None, T=1.7)
+    for l in range(prob.d + 1):
+        np.testing.assert_allclose(to_np(prob.quad_points(l)), disc.quad(l)[0], rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("n_el,p,kind", CASES)
+def test_apply_sys(n_el, p, kind):
+    prob, disc = _problem(n_el, p, kind, T=1.3, nu=0.8)
+    x = random_complex(prob.n_dof, 11)
+    y = to_np(prob.apply_sys(to_dev(x)))
+    ref = disc.apply(x)
+    assert rel_err(y, ref) < 1e-12
+
+
+@pytest.mark.parametrize("n_el,p,kind", CASES)
+def test_apply_prec_fp64(n_el, p, kind):
+    prob, disc = _problem(n_el, p, kind, T=0.9, nu=1.1)
+    assert prob.build_fd() == 0
+    r = random_complex(prob.n_dof, 12)
+    s = to_np(prob.apply_prec(to_dev(r)))
+    ref = ofd.FastDiagonalization(disc).apply(r)
+    assert rel_err(s, ref) < 1e-11
+
+
+@pytest.mark.parametrize("n_el,p", [([9, 11, 7], [2, 3, 2]), ([5, 6, 5, 7], [2, 2, 3, 2]), ([32, 32], 2)])
+def test_apply_prec_fp32(n_el, p):
+    prob, disc = _problem(n_el, p, None, prec=S.STST_PREC_FP32)
+    prob.build_fd()
+    r = random_complex(prob.n_dof, 13)
+    s = to_np(prob.apply_prec(to_dev(r)))
+    ref = ofd.FastDiagonalization(disc).apply(r)
+    assert rel_err(s, ref) < 1e-5
+
+
+@pytest.mark.parametrize("n_el,p,kind", [([8, 9], [2, 3], None), ([6, 7, 5], [2, 2, 3], "harmonic"),
+                                         ([4, 5, 4, 3], 2, "bump")])
+def test_rhs_lifting_and_forcing(n_el, p, kind):
+    prob, disc = _problem(n_el, p, kind, T=0.8, nu=1.2)
+    d = prob.d
+    wp = wavepacket_factors(wavepacket_params(np.random.default_rng(3), d))
+    f = lambda t, *xs: np.exp(1j * (2 * t + xs[0])) * (1 + 0.5 * sum(x ** 2 for x in xs))
+    b_gpu, c_gpu = prob.rhs(sample_forcing(prob, f), sample_initial(prob, wp), want_c0=True)
+    from inputs import product_fn
+    b_ref, c_ref = orhs.rhs_initial(disc, f, product_fn(wp))
+    assert rel_err(to_np(c_gpu), c_ref.ravel()) < 1e-12
+    assert rel_err(to_np(b_gpu), b_ref) < 1e-12
+
+
+@pytest.mark.parametrize("n_el,p,kind", CASES[:6])
+def test_pcg_fp64_matches_oracle_iterates(n_el, p, kind):
+    prob, disc = _problem(n_el, p, kind)
+    prob.build_fd()
+    b = random_complex(prob.n_dof, 21)
+    x, st, it, rr = prob.pcg(to_dev(b), tol=1e-10, maxit=200)
+    F = ofd.FastDiagonalization(disc)
+    xo, ito, rro, _ = opcg.pcg(disc.apply, F.apply, b, tol=1e-10, maxit=200)
+    assert st == 0 and rr <= 1e-10
+    assert abs(it - ito) <= 1
+    assert rel_err(to_np(x), xo) < 1e-9
+    # residual of the GPU solution measured by the oracle
+    res = np.linalg.norm(b - disc.apply(to_np(x))) / np.linalg.norm(b)
+    assert res < 1e-9
+
+
+@pytest.mark.parametrize("n_el,p,kind", [([9, 11, 7], [2, 3, 2], "harmonic"), ([5, 6, 5, 7], [2, 2, 3, 2], None)])
+def test_pcg_fp32_preconditioner_solution(n_el, p, kind):
+    prob, disc = _problem(n_el, p, kind, prec=S.STST_PREC_FP32)
+    prob.build_fd()
+    b = random_complex(prob.n_dof, 22)
+    x, st, it, rr = prob.pcg(to_dev(b), tol=1e-12, maxit=200)
+    xo, _, _, _ = opcg.pcg(disc.apply, ofd.FastDiagonalization(disc).apply, b, tol=1e-12, maxit=200)
+    assert st == 0
+    assert rel_err(to_np(x), xo) < 1e-8
+
+
+@pytest.mark.parametrize("n_el,p,kind", [([9, 11, 7], [2, 3, 2], "harmonic"), ([5, 6, 5, 7], [2, 2, 3, 2], None),
+                                         ([32, 32], 2, None)])
+def test_iterative_refinement_solution(n_el, p, kind):
+    """FP64 residual/update around FP32 inner PCG: final solution within 1e-8 of the FP64 oracle's."""
+    prob, disc = _problem(n_el, p, kind, prec=S.STST_PREC_FP32)
+    prob.build_fd()
+    b = random_complex(prob.n_dof, 23)
+    x, st, it, outer, rr = prob.ir(to_dev(b), tol=1e-10, maxit=80, inner_tol=1e-4, inner_maxit=100)
+    xo, _, _, _ = opcg.pcg(disc.apply, ofd.FastDiagonalization(disc).apply, b, tol=1e-13, maxit=300)
+    assert st == 0 and rr <= 1e-10
+    assert rel_err(to_np(x), xo) < 1e-8
+    res = np.linalg.norm(b - disc.apply(to_np(x))) / np.linalg.norm(b)
+    assert res < 1e-9
+
+
+def test_c1_workload_end_to_end():
+    """1D+t, p=2, 32x32, u = exp(i pi^2 t) sin(pi x): rhs by lifting, PCG to 1e-10, against the oracle."""
+    from inputs import CONFIGS, initial_factors, product_fn
+    cfg = CONFIGS["c1"]
+    prob, disc = _problem(cfg["n_el"], cfg["p"], None)
+    u0 = initial_factors(cfg)
+    b, c0 = prob.rhs(None, sample_initial(prob, u0), want_c0=True)
+    b_ref, c_ref = orhs.rhs_initial(disc, None, product_fn(u0))
+    # the lifted rhs is a difference of terms about 1e4 times larger than the result (nu^2 J_l c with
+    # J ~ h^-3): FP64 rounding in a different summation order shows at ~1e-12 relative to max|rhs|
+    assert rel_err(to_np(b), b_ref) < 1e-11
+    prob.build_fd()
+    x, st, it, rr = prob.pcg(b, tol=cfg["tol"], maxit=200)
+    xo, ito, _, _ = opcg.pcg(disc.apply, ofd.FastDiagonalization(disc).apply, b_ref, tol=cfg["tol"])
+    assert st == 0 and abs(it - ito) <= 1
+    assert rel_err(to_np(x), xo) < 1e-9
+
+
+# ---------------------------------------------------------------------------------------- edge cases
+def test_degenerate_sizes():
+    # one spatial unknown, one time unknown
+    prob, disc = _problem([1, 1], [1, 2], None)
+    assert prob.n_dof == 1
+    prob.build_fd()
+    x = random_complex(1, 1)
+    assert rel_err(to_np(prob.apply_sys(to_dev(x))), disc.apply(x)) < 1e-13
+    xs, st, it, rr = prob.pcg(to_dev(x), tol=1e-12)
+    assert st == 0 and it <= 1
+
+
+def test_max_space_size_and_degree():
+    prob, disc = _problem([3, 126], [2, 4], None)  # n_1 = 128
+    prob.build_fd()
+    r = random_complex(prob.n_dof, 5)
+    assert rel_err(to_np(prob.apply_prec(to_dev(r))), ofd.FastDiagonalization(disc).apply(r)) < 1e-10
+    prob8, disc8 = _problem([3, 4], [1, 8], None)
+    prob8.build_fd()
+    r = random_complex(prob8.n_dof, 6)
+    assert rel_err(to_np(prob8.apply_prec(to_dev(r))), ofd.FastDiagonalization(disc8).apply(r)) < 1e-10
+
+
+def test_status_codes():
+    with pytest.raises(S.StstError):
+        S.Problem(2, [4, 4, 4], [2, 1, 2])  # p_s = 1 violates C^1 in space
+    with pytest.raises(S.StstError):
+        S.Problem(1, [4, 200], [2, 2])       # n_s > 128
+    with pytest.raises(S.StstError):
+        S.Problem(0, [4], [2])
+    prob, _ = _problem([4, 5], 2, None)
+    r = prob.vec()
+    with pytest.raises(S.StstError) as e:
+        prob.apply_prec(r)                   # before build_fd
+    assert e.value.status == -5
+    with pytest.raises(S.StstError):
+        S._lib._chk(S.lib().stst_apply_sys(None, r.data_ptr(), r.data_ptr()), "x")
+    prob.build_fd()
+    b = to_dev(random_complex(prob.n_dof, 9))
+    x, st, it, rr = prob.pcg(b, tol=0.0, maxit=3)
+    assert st == 1 and it == 3
+    x, st, it, rr = prob.pcg(b, tol=1e-8, maxit=0)
+    assert st == 1 and it == 0 and np.abs(to_np(x)).max() == 0
+    bn = b.clone()
+    bn[0] = complex(float("nan"), 0)
+    x, st, it, rr = prob.pcg(bn, tol=1e-8, maxit=10)
+    assert st in (1, 2)
+    # zero right-hand side: converged immediately with x = 0
+    x, st, it, rr = prob.pcg(prob.vec(), tol=1e-8, maxit=10)
+    assert st == 0 and it == 0
