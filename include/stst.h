@@ -146,6 +146,29 @@ int stst_apply_prec(stst_handle h, const double *r, double *s);
 int stst_rhs(stst_handle h, const double *f_qp, const double *u0_qp, double *rhs, double *c0);
 
 /*
+ * stst_rhs_noalloc: the same right-hand side as stst_rhs, computed without
+ * taking any device memory at call time. (The paper has no counterpart: this
+ * is an interface for callers that cannot allocate.) stst_rhs with a forcing
+ * grid allocates temporaries for every call; some callers cannot let it:
+ * code that records the call while a CUDA stream is being captured into a
+ * graph, where cudaMalloc and cudaFree are not allowed, and programs whose
+ * device memory is already claimed by their own pool or a fixed budget, where
+ * an allocation inside the solver could fail or fragment that pool. This
+ * variant keeps its temporaries in one static device array of 16 MiB
+ * (2^20 complex128 values) built into the library: every GPU that loads the
+ * library holds it until the process exits. The first call on a device looks
+ * up the array's device address (with that device current); make that first
+ * call before any stream capture. The forcing path needs 4 n_t prod_l Q_l
+ * complex values of it (5 with a potential, Q_l = n_el[l]*(p[l]+2)); larger
+ * problems return STST_ERR_ARG and do nothing. The initial-datum path uses the
+ * handle's own workspaces. All calls share the array: calls whose work may
+ * overlap on the GPU (other streams, other host threads, other handles on the
+ * same device) race on it and must be serialized by the caller. Nothing in it
+ * has to start at zero. Arguments and outputs as for stst_rhs.
+ */
+int stst_rhs_noalloc(stst_handle h, const double *f_qp, const double *u0_qp, double *rhs, double *c0);
+
+/*
  * stst_pcg_solve: P-hat-preconditioned conjugate gradients (Sec. 5.3, Sec. 6)
  * from the initial guess in x (x is overwritten by the solution). Stops when
  * ||rhs - A x_k||_2 <= tol ||rhs||_2 (recursive residual) or after maxit

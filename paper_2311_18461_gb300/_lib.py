@@ -44,6 +44,7 @@ def lib():
             "stst_apply_sys": [P, P, P],
             "stst_apply_prec": [P, P, P],
             "stst_rhs": [P, P, P, P, P],
+            "stst_rhs_noalloc": [P, P, P, P, P],
             "stst_pcg_solve": [P, P, P, D, I, IP, DP],
             "stst_ir_solve": [P, P, P, D, I, D, I, IP, IP, DP],
             "stst_profile": [P, I],
@@ -144,6 +145,10 @@ def stst_apply_prec(h, r, s):
 
 def stst_rhs(h, f_qp, u0_qp, rhs, c0):
     return _chk(lib().stst_rhs(h, _ptr(f_qp), _ptr(u0_qp), _ptr(rhs), _ptr(c0)), "stst_rhs")
+
+
+def stst_rhs_noalloc(h, f_qp, u0_qp, rhs, c0):
+    return _chk(lib().stst_rhs_noalloc(h, _ptr(f_qp), _ptr(u0_qp), _ptr(rhs), _ptr(c0)), "stst_rhs_noalloc")
 
 
 def stst_pcg_solve(h, rhs, x, tol, maxit):
