@@ -6,6 +6,7 @@
 //  * k_timesolve: the N_s independent banded Hermitian solves H_i x_i = y_i (Algorithm 1, step 3,
 //    Eq. independent_problems) with precomputed Cholesky factors, one thread per system.
 #include "common.cuh"
+#include "async.cuh"
 
 template <typename R> struct C2;
 template <> struct C2<double> { using T = double2; };
@@ -72,26 +73,31 @@ __global__ void __launch_bounds__(256) k_pass(const __grid_constant__ PassK k) {
     for (int b = 0; b < k.n_out; ++b) {
       R ax = 0, ay = 0;
       for (int ci = k.c_start[b]; ci < k.c_start[b + 1]; ++ci) {
+        // the matrix already carries the contribution's coefficient
         const T *in = (const T *)k.in[k.c_in[ci]];
         const R *m = (const R *)k.c_mat[ci] + j * (2 * P + 1);
-        R vx = 0, vy = 0;
+        if (k.c_imag[ci]) {  // + i * (m x)
 #pragma unroll
-        for (int q = 0; q <= 2 * P; ++q) {
-          int jj = j + k.row_off - P + q;
-          if (jj >= 0 && jj < k.n_mode_in) {
-            T xv = in[base + (long long)jj * k.inner];
-            R mv = m[q];
-            vx += mv * xv.x;
-            vy += mv * xv.y;
+          for (int q = 0; q <= 2 * P; ++q) {
+            int jj = j + k.row_off - P + q;
+            if (jj >= 0 && jj < k.n_mode_in) {
+              T xv = in[base + (long long)jj * k.inner];
+              R mv = m[q];
+              ax -= mv * xv.y;
+              ay += mv * xv.x;
+            }
           }
-        }
-        R s = (R)k.c_coef[ci];
-        if (k.c_imag[ci]) {  // s * i * v
-          ax -= s * vy;
-          ay += s * vx;
         } else {
-          ax += s * vx;
-          ay += s * vy;
+#pragma unroll
+          for (int q = 0; q <= 2 * P; ++q) {
+            int jj = j + k.row_off - P + q;
+            if (jj >= 0 && jj < k.n_mode_in) {
+              T xv = in[base + (long long)jj * k.inner];
+              R mv = m[q];
+              ax += mv * xv.x;
+              ay += mv * xv.y;
+            }
+          }
         }
       }
       T *out = (T *)k.out[b];
@@ -177,7 +183,7 @@ int run_plan(const Plan &plan, const void *x, void *y, int precision, int epi, c
             tin[pos] = pp.app_in[a];
             tim[pos] = pp.app_imag[a];
             tco[pos] = pp.coef[a][bo];
-            tma[pos] = precision == 1 ? (const void *)pp.mat32[a] : (const void *)pp.mat[a];
+            tma[pos] = precision == 1 ? (const void *)pp.cmat32[a][bo] : (const void *)pp.cmat[a][bo];
             pos++;
           }
       for (int q = 0; q < pos; ++q) {
@@ -224,69 +230,121 @@ int run_plan(const Plan &plan, const void *x, void *y, int precision, int epi, c
 // Mode product with a dense n x n matrix U (row-major U[i*n + j]):
 //   forward (Algorithm 1 step 2): y[o, j, c] = sum_i U[i][j] x[o, i, c]   (x times U^T along the mode)
 //   backward (step 4):            y[o, i, c] = sum_j U[i][j] x[o, j, c]
-// CTA: a tile of CW flattened columns (o, c); U and the x tile staged in shared memory.
+// A CTA owns 32 flattened columns (o, c) and all n rows; U and the x tile sit in shared memory.
+// 256 threads = 8 column groups x 32 row groups; each thread keeps RPT rows x 4 columns of complex
+// accumulators in registers (rows rg, rg+32, ..., columns 4 cg .. 4 cg + 3).
 // ------------------------------------------------------------------------------------------------
-template <typename R, typename TI, typename TO, int CW>
+template <typename R, typename TI, typename TO, int RPT>
 __global__ void __launch_bounds__(256) k_modeprod(const TI *__restrict__ X, TO *__restrict__ Y, const R *__restrict__ U,
                                                   int n, long long inner, long long ncols, int backward,
                                                   const TO *__restrict__ dotvec, double *dot_partials,
                                                   const int *done) {
   using T = typename C2<R>::T;
+  constexpr int CW = 32;
   if (done && *done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R *sU = (R *)smem_raw;                               // n*n
+  R *sU = (R *)smem_raw;                                            // n*n
   T *sX = (T *)(smem_raw + ((n * n * sizeof(R) + 15) / 16) * 16);  // n * CW
   __shared__ double sh[32];
   const long long col0 = (long long)blockIdx.x * CW;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    int i = e / n, j = e % n;
-    sU[e] = backward ? U[j * n + i] : U[e];  // sU[i*n + j] = coefficient of x_i in y_j
-  }
-  for (int e = threadIdx.x; e < n * CW; e += blockDim.x) {
-    int i = e / CW, cc = e % CW;
-    long long col = col0 + cc;
-    T v;
-    v.x = 0;
-    v.y = 0;
-    if (col < ncols) {
-      long long o = col / inner, c = col % inner;
-      TI xv = X[(o * n + i) * inner + c];
-      v.x = (R)xv.x;
-      v.y = (R)xv.y;
+  // U -> shared: sU[i*n + j] = coefficient of x_i in y_j (U for step 2, U^T for step 4). Reads of U
+  // are coalesced; the backward case writes the transpose into shared memory. (i, j) advance
+  // incrementally, so no division per element.
+  {
+    const int nn = n * n;
+    int e = threadIdx.x, i = e / n, j = e - (e / n) * n;
+    const int di = 256 / n, dj = 256 - (256 / n) * n;
+    for (; e < nn; e += 256) {
+      cp_async<sizeof(R)>(backward ? &sU[j * n + i] : &sU[e], &U[e]);
+      i += di;
+      j += dj;
+      if (j >= n) { j -= n; ++i; }
     }
-    sX[i * CW + cc] = v;
   }
-  __syncthreads();
-  constexpr int G = 256 / CW;  // row groups
-  const int cc = threadIdx.x % CW, g = threadIdx.x / CW;
-  const long long col = col0 + cc;
-  double dacc = 0.0;
-  long long o = col / inner, c = col % inner;
-  for (int j0 = g * 4; j0 < n; j0 += G * 4) {
-    R ax[4] = {0, 0, 0, 0}, ay[4] = {0, 0, 0, 0};
-    for (int i = 0; i < n; ++i) {
-      T xv = sX[i * CW + cc];
+  // x tile: this thread's column cc = tid % 32 is fixed, its rows are tid / 32 + 8k
+  {
+    const int cc = threadIdx.x & 31;
+    const long long col = col0 + cc;
+    const bool in = col < ncols;
+    const long long o = in ? col / inner : 0, c = in ? col % inner : 0;
+    const TI *src = X + o * n * inner + c;
+    if constexpr (sizeof(TI) == sizeof(T)) {
+      for (int i = threadIdx.x >> 5; i < n; i += 8) {
+        if (in) cp_async<sizeof(T)>(&sX[i * CW + cc], src + (long long)i * inner);
+        else { T z; z.x = 0; z.y = 0; sX[i * CW + cc] = z; }
+      }
+    } else {
+      // FP64 input converted to FP32: eight loads in flight per batch
+      for (int i0 = threadIdx.x >> 5; i0 < n; i0 += 64) {
+        TI v[8];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        R u = (j0 + q < n) ? sU[i * n + j0 + q] : (R)0;
-        ax[q] += u * xv.x;
-        ay[q] += u * xv.y;
+        for (int b = 0; b < 8; ++b) {
+          const int i = i0 + 8 * b;
+          if (in && i < n) v[b] = src[(long long)i * inner];
+          else { v[b].x = 0; v[b].y = 0; }
+        }
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+          const int i = i0 + 8 * b;
+          if (i < n) {
+            T t;
+            t.x = (R)v[b].x;
+            t.y = (R)v[b].y;
+            sX[i * CW + cc] = t;
+          }
+        }
       }
     }
-    if (col < ncols) {
+    cp_async_commit();
+    cp_async_wait_all();
+  }
+  __syncthreads();
+  const int cg = threadIdx.x & 7, rg = threadIdx.x >> 3;
+  R ax[RPT][4], ay[RPT][4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        int j = j0 + q;
-        if (j < n) {
-          long long idx = (o * n + j) * inner + c;
-          TO r;
-          r.x = ax[q];
-          r.y = ay[q];
-          Y[idx] = r;
-          if (dotvec) {
-            TO dv = dotvec[idx];
-            dacc += (double)dv.x * (double)r.x + (double)dv.y * (double)r.y;
-          }
+  for (int r = 0; r < RPT; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) { ax[r][c] = 0; ay[r][c] = 0; }
+  for (int i = 0; i < n; ++i) {
+    T xv[4];
+    if constexpr (sizeof(T) == 8) {  // float2: two 16-byte reads
+      const float4 *q = reinterpret_cast<const float4 *>(&sX[i * CW + cg * 4]);
+      float4 a = q[0], b = q[1];
+      xv[0].x = a.x; xv[0].y = a.y; xv[1].x = a.z; xv[1].y = a.w;
+      xv[2].x = b.x; xv[2].y = b.y; xv[3].x = b.z; xv[3].y = b.w;
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) xv[c] = sX[i * CW + cg * 4 + c];
+    }
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      const int j = rg + 32 * r;
+      const R u = (j < n) ? sU[i * n + j] : (R)0;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        ax[r][c] += u * xv[c].x;
+        ay[r][c] += u * xv[c].y;
+      }
+    }
+  }
+  double dacc = 0.0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const long long col = col0 + cg * 4 + c;
+    if (col >= ncols) continue;
+    const long long o = col / inner, cin = col % inner;
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      const int j = rg + 32 * r;
+      if (j < n) {
+        const long long idx = (o * n + j) * inner + cin;
+        TO res;
+        res.x = ax[r][c];
+        res.y = ay[r][c];
+        Y[idx] = res;
+        if (dotvec) {
+          TO dv = dotvec[idx];
+          dacc += (double)dv.x * (double)res.x + (double)dv.y * (double)res.y;
         }
       }
     }
@@ -307,10 +365,20 @@ static int launch_modeprod(const TI *X, TO *Y, const R *U, int n, long long inne
   if (dot_partials && grid > STST_MAXPART) return STST_ERR_ARG;
   STST_PROF(sizeof(R) == 8 ? "modeprod_f64" : "modeprod_f32", s);
   size_t sm = ((n * n * sizeof(R) + 15) / 16) * 16 + (size_t)n * CW * sizeof(typename C2<R>::T);
-  if (sm > 48 * 1024) {
-    STST_CUDA(cudaFuncSetAttribute(k_modeprod<R, TI, TO, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  const int rpt = (n + 31) / 32;
+  switch (rpt) {
+#define CASE(RR)                                                                                              \
+  case RR:                                                                                                    \
+    if (sm > 48 * 1024)                                                                                       \
+      STST_CUDA(cudaFuncSetAttribute(k_modeprod<R, TI, TO, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                     (int)sm));                                                               \
+    k_modeprod<R, TI, TO, RR><<<grid, 256, sm, s>>>(X, Y, U, n, inner, ncols, backward, dotvec, dot_partials, \
+                                                     done);                                                   \
+    break;
+    CASE(1) CASE(2) CASE(3) CASE(4)
+#undef CASE
+    default: return STST_ERR_ARG;
   }
-  k_modeprod<R, TI, TO, CW><<<grid, 256, sm, s>>>(X, Y, U, n, inner, ncols, backward, dotvec, dot_partials, done);
   STST_CUDA(cudaGetLastError());
   if (grid_out) *grid_out = grid;
   return STST_OK;
@@ -318,59 +386,80 @@ static int launch_modeprod(const TI *X, TO *Y, const R *U, int n, long long inne
 
 // ------------------------------------------------------------------------------------------------
 // Time solves. Factor layout: G[(t*P + (k-1))*Ns + i] = G_i[t][t-k] (complex), D[t*Ns + i] = 1/G_i[t][t].
-// Data layout: time fastest, y[i*nt + t]. A CTA of 32 threads handles 32 systems and stages
-// TC time steps of its systems through shared memory so global accesses stay coalesced.
+// Data layout: time fastest, y[i*nt + t]. A CTA of 32 threads handles 32 systems. For each chunk of
+// TC time steps it stages its systems' data AND their factor rows in shared memory with coalesced
+// loads (all in flight together), then runs the sequential recurrences out of shared memory. When
+// the whole time axis fits (few CTAs per SM), TC = n_t and every load is issued up front.
 // ------------------------------------------------------------------------------------------------
-template <typename R, int P, int TC>
+template <typename R, int P>
 __global__ void __launch_bounds__(32) k_timesolve(void *__restrict__ Yv, const void *__restrict__ Gv,
-                                                  const R *__restrict__ D, int nt, long long Ns, const int *done) {
+                                                  const R *__restrict__ D, int nt, long long Ns, int TC,
+                                                  const int *done) {
   using T = typename C2<R>::T;
   if (done && *done) return;
+  extern __shared__ __align__(16) unsigned char ts_smem[];
+  T *ty = (T *)ts_smem;            // [TC][33]
+  T *tg = ty + TC * 33;            // [TC][P][32]
+  R *td = (R *)(tg + TC * P * 32); // [TC][32]
   T *Y = (T *)Yv;
   const T *G = (const T *)Gv;
-  __shared__ T tile[TC][33];
   const long long i0 = (long long)blockIdx.x * 32;
   const int s = threadIdx.x;
   const long long i = i0 + s;
   const bool act = i < Ns;
+  const int nsys = (int)min((long long)32, Ns - i0);
+  // stage data, factor rows and inverse diagonals of the chunk: every copy is issued before the
+  // first wait, so the warp waits for the memory system once per chunk, not once per element
+  auto load_chunk = [&](int t0, int tc, bool with_y) {
+    if (with_y)
+      for (int ss = 0; ss < nsys; ++ss)
+        for (int u = s; u < tc; u += 32) cp_async<sizeof(T)>(&ty[u * 33 + ss], &Y[(i0 + ss) * nt + t0 + u]);
+    if (s < nsys) {
+      for (int u = 0; u < tc; ++u) {
+#pragma unroll
+        for (int k = 0; k < P; ++k)
+          cp_async<sizeof(T)>(&tg[(u * P + k) * 32 + s], &G[((long long)(t0 + u) * P + k) * Ns + i0 + s]);
+        cp_async<sizeof(R)>(&td[u * 32 + s], &D[(long long)(t0 + u) * Ns + i0 + s]);
+      }
+    }
+    cp_async_commit();
+    cp_async_wait_all();
+  };
+  auto store_chunk = [&](int t0, int tc) {
+    for (int ss = 0; ss < nsys; ++ss)
+      for (int u = s; u < tc; u += 32) Y[(i0 + ss) * nt + t0 + u] = ty[u * 33 + ss];
+  };
   T zw[P];
 #pragma unroll
   for (int a = 0; a < P; ++a) { zw[a].x = 0; zw[a].y = 0; }
   // forward substitution: G z = y
   for (int t0 = 0; t0 < nt; t0 += TC) {
     int tc = min(TC, nt - t0);
-    for (int e = s; e < 32 * TC; e += 32) {
-      int ss = e / TC, u = e % TC;
-      if (u < tc && i0 + ss < Ns) tile[u][ss] = Y[(i0 + ss) * nt + t0 + u];
-    }
+    load_chunk(t0, tc, true);
     __syncwarp();
     if (act) {
       for (int u = 0; u < tc; ++u) {
-        int t = t0 + u;
-        T y = tile[u][s];
+        T y = ty[u * 33 + s];
         R ax = y.x, ay = y.y;
 #pragma unroll
         for (int k = 1; k <= P; ++k) {
-          T g = G[((long long)t * P + (k - 1)) * Ns + i];
+          T g = tg[(u * P + (k - 1)) * 32 + s];
           T z = zw[k - 1];
           ax -= g.x * z.x - g.y * z.y;
           ay -= g.x * z.y + g.y * z.x;
         }
-        R dinv = D[(long long)t * Ns + i];
+        R dinv = td[u * 32 + s];
         T z;
         z.x = ax * dinv;
         z.y = ay * dinv;
 #pragma unroll
         for (int a = P - 1; a > 0; --a) zw[a] = zw[a - 1];
         zw[0] = z;
-        tile[u][s] = z;
+        ty[u * 33 + s] = z;
       }
     }
     __syncwarp();
-    for (int e = s; e < 32 * TC; e += 32) {
-      int ss = e / TC, u = e % TC;
-      if (u < tc && i0 + ss < Ns) Y[(i0 + ss) * nt + t0 + u] = tile[u][ss];
-    }
+    if (tc < nt) store_chunk(t0, tc);
     __syncwarp();
   }
   // backward substitution: G^H x = z ; x_t = (z_t - sum_k conj(G[t+k][t]) x_{t+k}) / G[t][t]
@@ -387,25 +476,22 @@ __global__ void __launch_bounds__(32) k_timesolve(void *__restrict__ Yv, const v
   for (int ch = nchunks - 1; ch >= 0; --ch) {
     int t0 = ch * TC;
     int tc = min(TC, nt - t0);
-    for (int e = s; e < 32 * TC; e += 32) {
-      int ss = e / TC, u = e % TC;
-      if (u < tc && i0 + ss < Ns) tile[u][ss] = Y[(i0 + ss) * nt + t0 + u];
+    if (nchunks > 1) {
+      load_chunk(t0, tc, true);
+      __syncwarp();
     }
-    __syncwarp();
     if (act) {
       for (int u = tc - 1; u >= 0; --u) {
-        int t = t0 + u;
-        T z = tile[u][s];
+        T z = ty[u * 33 + s];
         R ax = z.x, ay = z.y;
 #pragma unroll
         for (int a = 0; a < P; ++a) {
           T g = gw[a][a];  // G[t+1+a][t] (offset a+1)
           T xv = xw[a];
-          // conj(g) * x
           ax -= g.x * xv.x + g.y * xv.y;
           ay -= g.x * xv.y - g.y * xv.x;
         }
-        R dinv = D[(long long)t * Ns + i];
+        R dinv = td[u * 32 + s];
         T x;
         x.x = ax * dinv;
         x.y = ay * dinv;
@@ -417,15 +503,12 @@ __global__ void __launch_bounds__(32) k_timesolve(void *__restrict__ Yv, const v
         }
         xw[0] = x;
 #pragma unroll
-        for (int k = 1; k <= P; ++k) gw[0][k - 1] = G[((long long)t * P + (k - 1)) * Ns + i];
-        tile[u][s] = x;
+        for (int k = 1; k <= P; ++k) gw[0][k - 1] = tg[(u * P + (k - 1)) * 32 + s];
+        ty[u * 33 + s] = x;
       }
     }
     __syncwarp();
-    for (int e = s; e < 32 * TC; e += 32) {
-      int ss = e / TC, u = e % TC;
-      if (u < tc && i0 + ss < Ns) Y[(i0 + ss) * nt + t0 + u] = tile[u][ss];
-    }
+    store_chunk(t0, tc);
     __syncwarp();
   }
 }
@@ -433,10 +516,24 @@ __global__ void __launch_bounds__(32) k_timesolve(void *__restrict__ Yv, const v
 template <typename R>
 static int launch_timesolve(void *Y, const void *G, const R *D, int nt, long long Ns, int P, const int *done,
                             cudaStream_t s) {
-  int grid = grid_for(Ns, 32);
+  using T = typename C2<R>::T;
+  const int grid = grid_for(Ns, 32);
+  const size_t per_t = 33 * sizeof(T) + (size_t)P * 32 * sizeof(T) + 32 * sizeof(R);
+  // shared memory per CTA: the whole time axis when few CTAs share an SM, else a chunk
+  const int ctas_per_sm = (grid + 151) / 152;
+  size_t budget = (200 * 1024) / (size_t)ctas_per_sm;
+  int TC = (int)(budget / per_t);
+  if (TC > nt) TC = nt;
+  if (TC < 8) TC = (nt < 8) ? nt : 8;
+  const size_t sm = per_t * TC;
   STST_PROF(sizeof(R) == 8 ? "timesolve_f64" : "timesolve_f32", s);
   switch (P) {
-#define CASE(PP) case PP: k_timesolve<R, PP, 16><<<grid, 32, 0, s>>>(Y, G, D, nt, Ns, done); break;
+#define CASE(PP)                                                                                          \
+  case PP:                                                                                                \
+    if (sm > 48 * 1024) STST_CUDA(cudaFuncSetAttribute(k_timesolve<R, PP>,                                \
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)); \
+    k_timesolve<R, PP><<<grid, 32, sm, s>>>(Y, G, D, nt, Ns, TC, done);                                   \
+    break;
     CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
 #undef CASE
     default: return STST_ERR_ARG;

@@ -33,7 +33,7 @@ __device__ void gauss_node(int n, int k, double *x, double *w) {
     dp = (n == 1) ? 1.0 : n * (z * p1 - p0) / (z * z - 1.0);
     double dz = p1 / dp;
     z -= dz;
-    if (fabs(dz) < 1e-17) break;
+    if (fabs(dz) <= 1e-16) break;
   }
   p0 = 1.0;
   p1 = z;
@@ -114,6 +114,9 @@ __device__ void element_basis(int p, int n_el, int e, double x, double out[3][ST
 // J = I - p + k. Sums w * integrand over the elements shared by b_I and b_J.
 __global__ void k_assemble_band(int kind, int p, int n_el, double len, int nq, int off, int n_rows, int n_cols,
                                 const double *__restrict__ weight, double *__restrict__ out) {
+  __shared__ double sg[32], sw[32];  // Gauss rule, computed once per block (nq <= p + 2 <= 10)
+  if (threadIdx.x < nq) gauss_node(nq, threadIdx.x, &sg[threadIdx.x], &sw[threadIdx.x]);
+  __syncthreads();
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   int bw = 2 * p + 1;
   if (idx >= n_rows * bw) return;
@@ -127,8 +130,7 @@ __global__ void k_assemble_band(int kind, int p, int n_el, double len, int nq, i
     double s1 = 1.0 / len, s2 = 1.0 / (len * len);
     for (int e = e0; e <= e1; ++e) {
       for (int q = 0; q < nq; ++q) {
-        double g, gw;
-        gauss_node(nq, q, &g, &gw);
+        double g = sg[q], gw = sw[q];
         double x = (e + 0.5 * (g + 1.0)) * h;  // reference coordinate in [0,1]
         double wq = 0.5 * h * gw * len;          // weight in physical coordinates
         if (weight) wq *= weight[e * nq + q];
@@ -243,6 +245,21 @@ __global__ void k_wprod(const double *a, const double *b, double *o, int n) {
 
 int launch_weight_product(const double *a, const double *b, double *out, int n, cudaStream_t s) {
   k_wprod<<<grid_for(n, 128), 128, 0, s>>>(a, b, out, n);
+  STST_CUDA(cudaGetLastError());
+  return STST_OK;
+}
+
+__global__ void k_scale(const double *a, double c, double *o, float *o32, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    double v = c * a[i];
+    o[i] = v;
+    o32[i] = (float)v;
+  }
+}
+
+int launch_scale(const double *a, double c, double *out, float *out32, int n, cudaStream_t s) {
+  k_scale<<<grid_for(n, 128), 128, 0, s>>>(a, c, out, out32, n);
   STST_CUDA(cudaGetLastError());
   return STST_OK;
 }

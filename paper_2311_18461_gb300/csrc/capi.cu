@@ -290,9 +290,33 @@ int replan(stst_problem *h, const std::vector<Term> &terms) {
     h->pool.push_back(a);
     h->pool.push_back(b);
   }
+  for (void *q : h->scaled) cudaFree(q);
+  h->scaled.clear();
   for (Plan *pl : {&h->sys_plan, &h->lift_plan}) {
     for (size_t lev = 0; lev < pl->passes.size(); ++lev) {
       PassParams &pp = pl->passes[lev];
+      // coefficient-scaled copies of the band matrices (coefficient 1 keeps the original)
+      const int nb = pp.n_mode_out * (2 * pp.p + 1);
+      for (int a = 0; a < pp.n_app; ++a)
+        for (int b = 0; b < pp.n_out; ++b) {
+          pp.cmat[a][b] = nullptr;
+          pp.cmat32[a][b] = nullptr;
+          const double c = pp.coef[a][b];
+          if (c == 0.0) continue;
+          if (c == 1.0) {
+            pp.cmat[a][b] = pp.mat[a];
+            pp.cmat32[a][b] = pp.mat32[a];
+            continue;
+          }
+          void *m64, *m32;
+          STST_TRY(alloc(&m64, sizeof(double) * nb));
+          h->scaled.push_back(m64);
+          STST_TRY(alloc(&m32, sizeof(float) * nb));
+          h->scaled.push_back(m32);
+          STST_TRY(launch_scale(pp.mat[a], c, (double *)m64, (float *)m32, nb, h->stream));
+          pp.cmat[a][b] = (const double *)m64;
+          pp.cmat32[a][b] = (const float *)m32;
+        }
       std::vector<void *> &dst = (lev % 2 == 0) ? even : odd;
       std::vector<void *> &src = (lev % 2 == 0) ? odd : even;
       for (int b = 0; b < pp.n_out; ++b) pp.out[b] = (b < (int)dst.size()) ? dst[b] : nullptr;
@@ -334,6 +358,7 @@ void destroy_all(stst_problem *h) {
   }
   for (double *p : h->pot_bufs) cudaFree(p);
   free_pool(h);
+  for (void *q : h->scaled) cudaFree(q);
   cudaFree(h->oa_work);
   cudaFree(h->Hg);
   cudaFree(h->Hd);
@@ -710,6 +735,7 @@ int stst_profile(stst_handle h, int enable) {
   STST_TRY(check(h));
   if (!h->prof) h->prof = new (std::nothrow) Profiler();
   if (!h->prof) return STST_ERR_OOM;
+  prof_flush(h->prof);
   if (enable) {
     h->prof->names.clear();
     h->prof->total_ms.clear();
@@ -728,7 +754,7 @@ int stst_plan_info(stst_handle h, int *n_passes, int *band_apps, double *flops_p
       for (int b = 0; b < pp.n_out; ++b)
         if (pp.coef[a][b] != 0.0) {
           apps++;
-          flops += 4.0 * (2 * pp.p + 1) + 4.0;
+          flops += 4.0 * (2 * pp.p + 1);
         }
   }
   if (n_passes) *n_passes = (int)h->sys_plan.passes.size();
@@ -739,6 +765,7 @@ int stst_plan_info(stst_handle h, int *n_passes, int *band_apps, double *flops_p
 
 int stst_profile_read(stst_handle h, int idx, char *name, int name_len, long long *count, double *total_ms) {
   STST_TRY(check(h));
+  if (h->prof) prof_flush(h->prof);
   if (!h->prof || idx < 0 || idx >= (int)h->prof->names.size()) return STST_ERR_ARG;
   if (name && name_len > 0) {
     const std::string &nm = h->prof->names[idx];

@@ -60,6 +60,9 @@ struct PassParams {
   int app_imag[PASS_MAXAPP];         // multiply by i
   float coef32[PASS_MAXAPP][PASS_MAXOUT];
   double coef[PASS_MAXAPP][PASS_MAXOUT];
+  // coef * mat, prepared by the planner, so that kernels accumulate band sums without a multiply
+  const double *cmat[PASS_MAXAPP][PASS_MAXOUT];
+  const float *cmat32[PASS_MAXAPP][PASS_MAXOUT];
   // epilogue (final pass only, n_out == 1)
   int epi;                    // 0 store, 1 out = b - v
   const void *b;
@@ -127,6 +130,7 @@ struct stst_problem {
   // plans
   Plan sys_plan, lift_plan;
   std::vector<void *> pool;        // intermediate tensors of the plans (FP64 sized)
+  std::vector<void *> scaled;      // coefficient-scaled band matrices of the plans
 
   // workspaces (N_dof complex FP64 each)
   double *w_x, *w_r, *w_z, *w_zold, *w_p, *w_q, *w_f, *w_t1, *w_t2;
@@ -155,7 +159,8 @@ struct ApiScope {
   stst_problem *h;
   explicit ApiScope(stst_problem *hh) : h(hh) { g_prof = (h && h->prof_on) ? h->prof : nullptr; }
   ~ApiScope() {
-    if (g_prof) prof_flush(g_prof);
+    // records are resolved lazily (stst_profile_read) so that queued calls are not serialized
+    if (g_prof && g_prof->pending.size() > 4096) prof_flush(g_prof);
     g_prof = nullptr;
   }
 };
@@ -170,6 +175,7 @@ int launch_quadrature(int p, int n_el, double len, int nq, double *pts, double *
 int launch_mass_cholesky(const BandMat &M, double *chol, int *flags, cudaStream_t s);
 int launch_to_f32(const double *src, float *dst, long long n, cudaStream_t s);
 int launch_weight_product(const double *a, const double *b, double *out, int n, cudaStream_t s);
+int launch_scale(const double *a, double c, double *out, float *out32, int n, cudaStream_t s);
 
 int run_plan(const Plan &plan, const void *x, void *y, int precision, int epi, const void *b, const void *dotvec,
              double *dot_partials, const int *done, cudaStream_t s, const void *dot2vec = nullptr,

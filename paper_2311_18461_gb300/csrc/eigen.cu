@@ -10,25 +10,32 @@
 //    one thread per system (Eq. independent_problems).
 #include "common.cuh"
 #include <cmath>
+#include <type_traits>
 
 // ------------------------------------------------------------------------------------------------
-// FP32 Jacobi on one CTA. Outputs U0 (row-major n x n, column j = eigenvector j, M-orthonormal to
-// FP32 accuracy) and lam0, sorted ascending.
+// FP32 first approximation on one CTA (n <= 128): with M = C C^T (banded Cholesky) the pencil becomes
+// the symmetric matrix A = C^{-1} L C^{-T}; Householder reflections reduce A to tridiagonal T,
+// bisection on Sturm counts gives every eigenvalue of T (thread j finds the j-th smallest),
+// inverse iteration with partial pivoting gives its eigenvector, the reflections are applied back
+// and U0 = C^{-T} Q. Outputs U0 (row-major n x n, column j = eigenvector j) and lam0 ascending.
 // ------------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(512) k_eig_jacobi(const double *__restrict__ Mb, const double *__restrict__ Lb, int n,
-                                                    int p, double *U0, double *lam0, int *flags) {
+__global__ void __launch_bounds__(512) k_eig_tridiag(const double *__restrict__ Mb, const double *__restrict__ Lb,
+                                                     int n, int p, double *U0, double *lam0, float *lu, int *flags) {
   extern __shared__ __align__(16) float sm[];
   const int ld = n + 1;
-  float *A = sm;                   // n x ld
-  float *V = A + n * ld;           // n x ld
-  float *C = V + n * ld;           // n x (p+1): C[i*(p+1)+k] = C_{i, i-p+k}
-  float *rot = C + n * (p + 1);    // 4 x 64: c, s, p, q (as float bits)
-  int *rpq = (int *)(rot + 2 * 64);
+  float *A = sm;                   // n x ld: matrix, then Householder vectors below the diagonal
+  float *X = A + n * ld;           // n x ld: scratch, then eigenvectors (column j)
+  float *C = X + n * ld;           // n x (p+1): C[i*(p+1)+k] = C_{i, i-p+k}
+  float *dg = C + n * (p + 1);     // diagonal of T
+  float *od = dg + n;              // off-diagonal of T (od[k] = T[k+1][k])
+  float *bet = od + n;             // Householder beta_k
+  float *pv = bet + n;             // work vector p
+  float *wv = pv + n;              // work vector w
   __shared__ float red[32];
-  __shared__ int conv;
+  __shared__ float bc[4];
   const int tid = threadIdx.x, nth = blockDim.x;
   const int bw = 2 * p + 1;
-  // 1. banded Cholesky of M (FP32, thread 0)
+  // 1. banded Cholesky of M (thread 0)
   if (tid == 0) {
     for (int i = 0; i < n; ++i) {
       for (int k = 0; k <= p; ++k) {
@@ -45,137 +52,210 @@ __global__ void __launch_bounds__(512) k_eig_jacobi(const double *__restrict__ M
     }
   }
   __syncthreads();
-  // 2. Y = C^{-1} L, column j by thread j (stored in V as Y[i][j])
+  // 2. Y = C^{-1} L (column j by thread j, into X), A = C^{-1} Y^T, symmetrized
   for (int j = tid; j < n; j += nth) {
     for (int i = 0; i < n; ++i) {
       float s = (abs(i - j) <= p) ? (float)Lb[i * bw + (j - i + p)] : 0.f;
-      for (int m = max(i - p, 0); m < i; ++m) s -= C[i * (p + 1) + (m - i + p)] * V[m * ld + j];
-      V[i * ld + j] = s / C[i * (p + 1) + p];
+      for (int m = max(i - p, 0); m < i; ++m) s -= C[i * (p + 1) + (m - i + p)] * X[m * ld + j];
+      X[i * ld + j] = s / C[i * (p + 1) + p];
     }
   }
   __syncthreads();
-  // 3. A = C^{-1} Y^T : column j = C^{-1} (row j of Y)
   for (int j = tid; j < n; j += nth) {
     for (int i = 0; i < n; ++i) {
-      float s = V[j * ld + i];
+      float s = X[j * ld + i];
       for (int m = max(i - p, 0); m < i; ++m) s -= C[i * (p + 1) + (m - i + p)] * A[m * ld + j];
       A[i * ld + j] = s / C[i * (p + 1) + p];
     }
   }
   __syncthreads();
-  for (int e = tid; e < n * n; e += nth) {
-    int i = e / n, j = e % n;
-    if (i < j) {
+  for (int i = tid; i < n; i += nth)
+    for (int j = i + 1; j < n; ++j) {
       float a = 0.5f * (A[i * ld + j] + A[j * ld + i]);
       A[i * ld + j] = a;
       A[j * ld + i] = a;
     }
+  __syncthreads();
+  // 3. Householder tridiagonalization: step k zeroes column k below the subdiagonal
+  for (int k = 0; k + 2 < n; ++k) {
+    const int m = n - k - 1;  // length of x = A[k+1.., k]
+    if (tid < 32) {
+      float s = 0.f;
+      for (int i = tid; i < m; i += 32) {
+        float v = A[(k + 1 + i) * ld + k];
+        s += v * v;
+      }
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (tid == 0) {
+        float x0 = A[(k + 1) * ld + k];
+        float nx = sqrtf(s);
+        float alpha = (x0 >= 0.f) ? -nx : nx;
+        float vtv = s - x0 * x0 + (x0 - alpha) * (x0 - alpha);
+        bc[0] = alpha;
+        bc[1] = (nx > 0.f && vtv > 0.f) ? 2.f / vtv : 0.f;
+        bc[2] = x0 - alpha;
+      }
+    }
+    __syncthreads();
+    const float alpha = bc[0], beta = bc[1];
+    if (tid == 0) {
+      dg[k] = A[k * ld + k];
+      od[k] = (beta > 0.f) ? alpha : A[(k + 1) * ld + k];
+      bet[k] = beta;
+      A[(k + 1) * ld + k] = bc[2];  // v_0 (the rest of v is the column itself)
+    }
+    __syncthreads();
+    if (beta > 0.f) {
+      // p = beta * A_sub v (one thread per row)
+      for (int i = tid; i < m; i += nth) {
+        float s = 0.f;
+        for (int j = 0; j < m; ++j) s += A[(k + 1 + i) * ld + (k + 1 + j)] * A[(k + 1 + j) * ld + k];
+        pv[i] = beta * s;
+      }
+      __syncthreads();
+      if (tid < 32) {
+        float s = 0.f;
+        for (int i = tid; i < m; i += 32) s += pv[i] * A[(k + 1 + i) * ld + k];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (tid == 0) bc[3] = 0.5f * beta * s;
+      }
+      __syncthreads();
+      const float kk = bc[3];
+      for (int i = tid; i < m; i += nth) wv[i] = pv[i] - kk * A[(k + 1 + i) * ld + k];
+      __syncthreads();
+      for (int e = tid; e < m * m; e += nth) {
+        int i = e / m, j = e - (e / m) * m;
+        float vi = A[(k + 1 + i) * ld + k], vj = A[(k + 1 + j) * ld + k];
+        A[(k + 1 + i) * ld + (k + 1 + j)] -= vi * wv[j] + wv[i] * vj;
+      }
+      __syncthreads();
+    }
   }
-  for (int e = tid; e < n * n; e += nth) {
-    int i = e / n, j = e % n;
-    V[i * ld + j] = (i == j) ? 1.f : 0.f;
+  if (tid == 0) {
+    if (n >= 2) {
+      dg[n - 2] = A[(n - 2) * ld + (n - 2)];
+      od[n - 2] = A[(n - 1) * ld + (n - 2)];
+      if (n - 2 >= 0) bet[n - 2] = 0.f;
+    }
+    dg[n - 1] = A[(n - 1) * ld + (n - 1)];
   }
   __syncthreads();
-  // 4. cyclic Jacobi, round-robin pairing; all pairs of a round are disjoint
-  const int np = n + (n & 1);
-  const int half = np / 2;
-  for (int sweep = 0; sweep < 40; ++sweep) {
-    for (int r = 0; r < np - 1; ++r) {
-      if (tid < half) {
-        int a, b;
-        if (tid == 0) { a = np - 1; b = r; }
-        else { a = (r + tid) % (np - 1); b = (r - tid + np - 1) % (np - 1); }
-        int pp = min(a, b), qq = max(a, b);
-        float c = 1.f, s = 0.f;
-        if (qq < n) {
-          float apq = A[pp * ld + qq];
-          float app = A[pp * ld + pp], aqq = A[qq * ld + qq];
-          if (fabsf(apq) > 1e-30f * (fabsf(app) + fabsf(aqq)) && apq != 0.f) {
-            float th = (aqq - app) / (2.f * apq);
-            float t = (fabsf(th) > 1e15f) ? 0.5f / th : copysignf(1.f, th) / (fabsf(th) + sqrtf(th * th + 1.f));
-            c = rsqrtf(t * t + 1.f);
-            s = t * c;
-          }
-        } else { pp = -1; }
-        rot[tid] = c;
-        rot[64 + tid] = s;
-        rpq[tid] = pp;
-        rpq[64 + tid] = qq;
-      }
-      __syncthreads();
-      for (int e = tid; e < half * n; e += nth) {  // rows
-        int k = e / n, col = e % n;
-        int pp = rpq[k];
-        if (pp < 0) continue;
-        int qq = rpq[64 + k];
-        float c = rot[k], s = rot[64 + k];
-        float ap = A[pp * ld + col], aq = A[qq * ld + col];
-        A[pp * ld + col] = c * ap - s * aq;
-        A[qq * ld + col] = s * ap + c * aq;
-      }
-      __syncthreads();
-      for (int e = tid; e < half * n; e += nth) {  // columns of A and V
-        int k = e / n, row = e % n;
-        int pp = rpq[k];
-        if (pp < 0) continue;
-        int qq = rpq[64 + k];
-        float c = rot[k], s = rot[64 + k];
-        float ap = A[row * ld + pp], aq = A[row * ld + qq];
-        A[row * ld + pp] = c * ap - s * aq;
-        A[row * ld + qq] = s * ap + c * aq;
-        float vp = V[row * ld + pp], vq = V[row * ld + qq];
-        V[row * ld + pp] = c * vp - s * vq;
-        V[row * ld + qq] = s * vp + c * vq;
-      }
-      __syncthreads();
-    }
-    // convergence: off-diagonal mass relative to the diagonal
-    float off = 0.f, dia = 0.f;
-    for (int e = tid; e < n * n; e += nth) {
-      int i = e / n, j = e % n;
-      float v = A[i * ld + j];
-      if (i == j) dia += v * v; else off += v * v;
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      off += __shfl_xor_sync(0xffffffffu, off, o);
-      dia += __shfl_xor_sync(0xffffffffu, dia, o);
-    }
-    if ((tid & 31) == 0) { red[tid >> 5] = off; }
-    __syncthreads();
-    if (tid == 0) {
-      float o2 = 0.f;
-      for (int w = 0; w < nth / 32; ++w) o2 += red[w];
-      red[31] = o2;
-    }
-    __syncthreads();
-    float offt = red[31];
-    __syncthreads();
-    if ((tid & 31) == 0) red[tid >> 5] = dia;
-    __syncthreads();
-    if (tid == 0) {
-      float d2 = 0.f;
-      for (int w = 0; w < nth / 32; ++w) d2 += red[w];
-      conv = (offt <= 1e-11f * d2) ? 1 : 0;  // FP32 accuracy; the FP64 refinement does the rest
-    }
-    __syncthreads();
-    if (conv) break;
+  // 4. eigenvalues of T by multisection on Sturm counts: warp w finds the j-th smallest eigenvalue
+  //    for j = w, w + 16, ...; its 32 lanes count at 32 shifts, shrinking the bracket 33-fold a step
+  float glo = 1e30f, ghi = -1e30f;
+  for (int i = 0; i < n; ++i) {
+    float r = (i > 0 ? fabsf(od[i - 1]) : 0.f) + (i < n - 1 ? fabsf(od[i]) : 0.f);
+    glo = fminf(glo, dg[i] - r);
+    ghi = fmaxf(ghi, dg[i] + r);
   }
-  // 5. U = C^{-T} V (column j by thread j: back substitution), sort by eigenvalue
+  const float span = fmaxf(ghi - glo, 1e-30f);
+  glo -= 1e-3f * span;
+  ghi += 1e-3f * span;
+  {
+    const int warp = tid >> 5, lane = tid & 31, nwarps = nth >> 5;
+    for (int j = warp; j < n; j += nwarps) {
+      float lo = glo, hi = ghi;
+      for (int step = 0; step < 12; ++step) {
+        if (!(hi - lo > 2e-7f * fmaxf(fabsf(lo), fabsf(hi)))) break;
+        const float w = (hi - lo) / 33.f;
+        const float sig = lo + (lane + 1) * w;
+        int cnt = 0;
+        float q = dg[0] - sig;
+        cnt += (q < 0.f);
+        for (int i = 1; i < n; ++i) {
+          if (fabsf(q) < 1e-30f) q = -1e-30f;
+          q = dg[i] - sig - __fdividef(od[i - 1] * od[i - 1], q);
+          cnt += (q < 0.f);
+        }
+        // first lane whose shift has more than j eigenvalues below it brackets eigenvalue j
+        const unsigned above = __ballot_sync(0xffffffffu, cnt > j);
+        const int l = above ? (__ffs(above) - 1) : 32;
+        const float nlo = (l == 0) ? lo : lo + l * w;
+        const float nhi = (l == 32) ? hi : lo + (l + 1) * w;
+        lo = nlo;
+        hi = nhi;
+      }
+      if (lane == 0) pv[j] = 0.5f * (lo + hi);
+    }
+  }
+  __syncthreads();
   for (int j = tid; j < n; j += nth) {
-    float lj = A[j * ld + j];
-    int rank = 0;
-    for (int k = 0; k < n; ++k) {
-      float lk = A[k * ld + k];
-      rank += (lk < lj || (lk == lj && k < j)) ? 1 : 0;
+    const float lam = pv[j];
+    lam0[j] = (double)lam;
+    // 5. inverse iteration on T - lam I, LU with partial pivoting (bands: u0, u1, u2), 3 sweeps
+    //    vector in column j of X
+    const float pert = 1e-6f * span;
+    const float sh = lam + ((j & 1) ? pert : -pert) * 1e-1f;
+    for (int i = 0; i < n; ++i) X[i * ld + j] = 1.f + 0.01f * (float)((i * 7 + j * 13) % 17);
+    for (int sweep = 0; sweep < 3; ++sweep) {
+      // factor and forward-solve together; row i of U is (a0, a1, a2) on columns i, i+1, i+2
+      float *Uj = lu + (size_t)j * 3 * n;  // this thread's 3n floats
+      float a0 = dg[0] - sh, a1 = (n > 1) ? od[0] : 0.f, a2 = 0.f;
+      float rhs = X[0 * ld + j];
+      for (int i = 0; i < n; ++i) {
+        const bool has_next = (i + 1 < n);
+        float nsub = 0.f, ndia = 0.f, nsup = 0.f, nrhs = 0.f;
+        if (has_next) {
+          nsub = od[i];
+          ndia = dg[i + 1] - sh;
+          nsup = (i + 2 < n) ? od[i + 1] : 0.f;
+          nrhs = X[(i + 1) * ld + j];
+        }
+        if (has_next && fabsf(nsub) > fabsf(a0)) {  // partial pivoting on column i
+          float t0 = a0, t1 = a1, t2 = a2, tr = rhs;
+          a0 = nsub; a1 = ndia; a2 = nsup; rhs = nrhs;
+          nsub = t0; ndia = t1; nsup = t2; nrhs = tr;
+        }
+        if (fabsf(a0) < 1e-30f) a0 = 1e-30f;
+        Uj[3 * i + 0] = a0;
+        Uj[3 * i + 1] = a1;
+        Uj[3 * i + 2] = a2;
+        X[i * ld + j] = rhs;
+        if (has_next) {
+          const float f = nsub / a0;
+          const float na0 = ndia - f * a1, na1 = nsup - f * a2, nr = nrhs - f * rhs;
+          a0 = na0; a1 = na1; a2 = 0.f; rhs = nr;
+        }
+      }
+      // back substitution
+      float x1 = 0.f, x2 = 0.f, nrm = 0.f;
+      for (int i = n - 1; i >= 0; --i) {
+        const float u0 = Uj[3 * i], u1 = Uj[3 * i + 1], u2 = Uj[3 * i + 2];
+        float xi = (X[i * ld + j] - u1 * x1 - u2 * x2) / u0;
+        X[i * ld + j] = xi;
+        x2 = x1;
+        x1 = xi;
+        nrm = fmaxf(nrm, fabsf(xi));
+      }
+      float inv = (nrm > 0.f) ? 1.f / nrm : 1.f;
+      for (int i = 0; i < n; ++i) X[i * ld + j] *= inv;
     }
-    lam0[rank] = (double)lj;
-    // solve C^T u = v_j : u_i = (v_i - sum_{m=i+1}^{i+p} C[m][i] u_m) / C[i][i]; store u in column j of A? use V column in place
+  }
+  __syncthreads();
+  // 6. back-transform the eigenvectors: x <- H_0 H_1 ... H_{n-3} x, H_k = I - beta_k v_k v_k^T on rows k+1..
+  for (int j = tid; j < n; j += nth) {
+    for (int k = n - 3; k >= 0; --k) {
+      float b = bet[k];
+      if (b == 0.f) continue;
+      float s = 0.f;
+      for (int i = k + 1; i < n; ++i) s += A[i * ld + k] * X[i * ld + j];
+      s *= b;
+      for (int i = k + 1; i < n; ++i) X[i * ld + j] -= s * A[i * ld + k];
+    }
+    // normalize (2-norm) and U0 = C^{-T} x : back substitution
+    float s = 0.f;
+    for (int i = 0; i < n; ++i) s += X[i * ld + j] * X[i * ld + j];
+    float inv = rsqrtf(fmaxf(s, 1e-30f));
     for (int i = n - 1; i >= 0; --i) {
-      float s = V[i * ld + j];
-      for (int m = i + 1; m <= min(i + p, n - 1); ++m) s -= C[m * (p + 1) + (i - m + p)] * V[m * ld + j];
-      V[i * ld + j] = s / C[i * (p + 1) + p];
+      float t = X[i * ld + j] * inv;
+      for (int m = i + 1; m <= min(i + p, n - 1); ++m) t -= C[m * (p + 1) + (i - m + p)] * X[m * ld + j];
+      X[i * ld + j] = t / C[i * (p + 1) + p];
     }
-    for (int i = 0; i < n; ++i) U0[i * n + rank] = (double)V[i * ld + j];
+  }
+  __syncthreads();
+  for (int e = tid; e < n * n; e += nth) {
+    int i = e / n, j = e - (e / n) * n;
+    U0[e] = (double)X[i * ld + j];
   }
 }
 
@@ -241,11 +321,29 @@ __global__ void k_oa_update(const double *__restrict__ X, const double *__restri
 }
 
 // ---- H_i factorization ----------------------------------------------------------------------------
-template <int P>
-__global__ void k_hfactor(const double *__restrict__ Lt, const double *__restrict__ Mt, const double *__restrict__ KAt,
-                          int nt, double nu, int d, const double *__restrict__ lam1, const double *__restrict__ lam2,
+// One thread per system i: lam_i = sum_l lam_{l, i_l}; rows of H_i = L_t + nu^2 lam^2 M_t + i nu lam KA_t
+// are formed on the fly and factored by banded Cholesky G G^H = H with a register window of the last
+// P rows. R = double writes the FP64 factors (and FP32 copies); R = float factors in FP32 only.
+template <typename R, int P>
+__global__ void k_hfactor(const R *__restrict__ Lt, const R *__restrict__ Mt, const R *__restrict__ KAt, int nt,
+                          double nu, int d, const double *__restrict__ lam1, const double *__restrict__ lam2,
                           const double *__restrict__ lam3, int n1, int n2, long long Ns, double2 *G, double *D,
-                          float2 *G32, float *D32, int *flags) {
+                          float2 *G32, float *D32, int *flags, int stage) {
+  using T = typename std::conditional<sizeof(R) == 8, double2, float2>::type;
+  extern __shared__ __align__(16) unsigned char hf_smem[];
+  const int bw = 2 * P + 1;
+  if (stage) {  // the three time bands are read by every thread at every step: keep them on chip
+    R *sL = (R *)hf_smem, *sM = sL + nt * bw, *sK = sM + nt * bw;
+    for (int e = threadIdx.x; e < nt * bw; e += blockDim.x) {
+      sL[e] = Lt[e];
+      sM[e] = Mt[e];
+      sK[e] = KAt[e];
+    }
+    __syncthreads();
+    Lt = sL;
+    Mt = sM;
+    KAt = sK;
+  }
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= Ns) return;
   double lam;
@@ -261,53 +359,51 @@ __global__ void k_hfactor(const double *__restrict__ Lt, const double *__restric
       if (d >= 3) lam += lam3[(int)r];
     }
   }
-  const double a2 = nu * nu * lam * lam, a1 = nu * lam;
-  const int bw = 2 * P + 1;
-  double2 rw[P][P];
-  double dw[P];
+  const R a2 = (R)(nu * nu * lam * lam), a1 = (R)(nu * lam);
+  T rw[P][P];
+  R dw[P];
 #pragma unroll
   for (int a = 0; a < P; ++a) {
-    dw[a] = 1.0;
+    dw[a] = 1;
 #pragma unroll
-    for (int k = 0; k < P; ++k) rw[a][k] = make_double2(0.0, 0.0);
+    for (int k = 0; k < P; ++k) { rw[a][k].x = 0; rw[a][k].y = 0; }
   }
   for (int t = 0; t < nt; ++t) {
-    double2 g[P + 1];
+    T g[P + 1];
 #pragma unroll
     for (int k = P; k >= 1; --k) {
       int s = t - k;
-      if (s < 0) { g[k] = make_double2(0.0, 0.0); continue; }
+      if (s < 0) { g[k].x = 0; g[k].y = 0; continue; }
       int off = s - t + P;  // = P - k
-      double hr = Lt[t * bw + off] + a2 * Mt[t * bw + off];
-      double hi = a1 * KAt[t * bw + off];
-      double sr = hr, si = hi;
+      R sr = Lt[t * bw + off] + a2 * Mt[t * bw + off];
+      R si = a1 * KAt[t * bw + off];
 #pragma unroll
       for (int j = k + 1; j <= P; ++j) {
-        double2 gj = g[j];
-        double2 c = rw[k - 1][j - k - 1];  // G[s][s-(j-k)]
-        // gj * conj(c)
-        sr -= gj.x * c.x + gj.y * c.y;
+        T gj = g[j];
+        T c = rw[k - 1][j - k - 1];  // G[s][s-(j-k)]
+        sr -= gj.x * c.x + gj.y * c.y;   // gj * conj(c)
         si -= gj.y * c.x - gj.x * c.y;
       }
-      double inv = 1.0 / dw[k - 1];
-      g[k] = make_double2(sr * inv, si * inv);
+      R inv = (R)1 / dw[k - 1];
+      g[k].x = sr * inv;
+      g[k].y = si * inv;
     }
-    double dd = Lt[t * bw + P] + a2 * Mt[t * bw + P];
+    R dd = Lt[t * bw + P] + a2 * Mt[t * bw + P];
 #pragma unroll
     for (int k = 1; k <= P; ++k) dd -= g[k].x * g[k].x + g[k].y * g[k].y;
-    if (!(dd > 0.0)) {
+    if (!(dd > (R)0)) {
       atomicOr(flags, 2);
-      dd = 1.0;
+      dd = 1;
     }
-    double gd = sqrt(dd);
+    R gd = sqrt(dd);
 #pragma unroll
     for (int k = 1; k <= P; ++k) {
       long long ofs = ((long long)t * P + (k - 1)) * Ns + i;
-      G[ofs] = g[k];
+      if constexpr (sizeof(R) == 8) G[ofs] = make_double2(g[k].x, g[k].y);
       G32[ofs] = make_float2((float)g[k].x, (float)g[k].y);
     }
-    D[(long long)t * Ns + i] = 1.0 / gd;
-    D32[(long long)t * Ns + i] = (float)(1.0 / gd);
+    if constexpr (sizeof(R) == 8) D[(long long)t * Ns + i] = 1.0 / gd;
+    D32[(long long)t * Ns + i] = (float)((R)1 / gd);
 #pragma unroll
     for (int a = P - 1; a > 0; --a) {
       dw[a] = dw[a - 1];
@@ -332,15 +428,17 @@ int fd_setup(stst_problem *h) {
     if (src != l) continue;
     const int n = h->dir[l].n, p = h->dir[l].p;
     const BandMat &M = h->mats[l][0], &L = h->mats[l][1];
-    size_t sm = (2 * (size_t)n * (n + 1) + (size_t)n * (p + 1) + 4 * 64) * sizeof(float);
-    STST_CUDA(cudaFuncSetAttribute(k_eig_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    { STST_PROF("eig_jacobi_f32", st);
-    k_eig_jacobi<<<1, 512, sm, st>>>(M.d, L.d, n, p, h->U[l], h->lam[l], h->flags); }
+    size_t sm = (2 * (size_t)n * (n + 1) + (size_t)n * (p + 1) + 5 * (size_t)n) * sizeof(float);
+    STST_CUDA(cudaFuncSetAttribute(k_eig_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    { STST_PROF("eig_tridiag_f32", st);
+    k_eig_tridiag<<<1, 512, sm, st>>>(M.d, L.d, n, p, h->U[l], h->lam[l], (float *)h->oa_work, h->flags); }
     STST_CUDA(cudaGetLastError());
     double *X = h->U[l], *PM = h->oa_work, *PL = PM + n * n, *R = PL + n * n, *S = R + n * n, *E = S + n * n,
            *Xn = E + n * n;
     int g = grid_for((long long)n * n, 64);
-    for (int it = 0; it < 3; ++it) {
+    // FP64 factors need full accuracy; the FP32 preconditioner needs FP32 accuracy only
+    const int refine = (h->prec_mode == STST_PREC_FP64) ? 3 : 1;
+    for (int it = 0; it < refine; ++it) {
       STST_PROF("eig_refine_f64", st);
       k_oa_band<<<g, 64, 0, st>>>(M.d, L.d, X, n, p, PM, PL);
       k_oa_gram<<<g, 64, 0, st>>>(X, PM, PL, n, R, S);
@@ -360,15 +458,26 @@ int fd_setup(stst_problem *h) {
     STST_TRY(launch_to_f32(h->U[l], h->U32[l], (long long)h->dir[l].n * h->dir[l].n, st));
   }
   const BandMat &Lt = h->mats[0][0], &Mt = h->mats[0][1], &KAt = h->mats[0][2];
+  const float *Lt32 = h->mats32[0][0], *Mt32 = h->mats32[0][1], *KAt32 = h->mats32[0][2];
   int n1 = h->dir[1].n, n2 = d >= 2 ? h->dir[2].n : 1;
   const double *l1 = h->lam[1], *l2 = d >= 2 ? h->lam[2] : nullptr, *l3 = d >= 3 ? h->lam[3] : nullptr;
   int grid = grid_for(h->N_s, 64);
-  STST_PROF("hfactor_f64", st);
+  const bool f64 = h->prec_mode == STST_PREC_FP64;
+  size_t hsm = 3 * (size_t)h->n_t() * (2 * h->dir[0].p + 1) * (f64 ? sizeof(double) : sizeof(float));
+  const int stage = hsm <= 48 * 1024;  // otherwise the bands are read from global memory
+  if (!stage) hsm = 0;
+  STST_PROF(f64 ? "hfactor_f64" : "hfactor_f32", st);
   switch (h->dir[0].p) {
-#define CASE(PP)                                                                                                    \
-  case PP:                                                                                                          \
-    k_hfactor<PP><<<grid, 64, 0, st>>>(Lt.d, Mt.d, KAt.d, h->n_t(), h->nu, d, l1, l2, l3, n1, n2, h->N_s,         \
-                                       (double2 *)h->Hg, h->Hd, (float2 *)h->Hg32, h->Hd32, h->flags);             \
+#define CASE(PP)                                                                                                 \
+  case PP:                                                                                                       \
+    if (f64)                                                                                                     \
+      k_hfactor<double, PP><<<grid, 64, hsm, st>>>(Lt.d, Mt.d, KAt.d, h->n_t(), h->nu, d, l1, l2, l3, n1, n2,     \
+                                                 h->N_s, (double2 *)h->Hg, h->Hd, (float2 *)h->Hg32, h->Hd32,    \
+                                                 h->flags, stage);                                                      \
+    else                                                                                                         \
+      k_hfactor<float, PP><<<grid, 64, hsm, st>>>(Lt32, Mt32, KAt32, h->n_t(), h->nu, d, l1, l2, l3, n1, n2,      \
+                                                h->N_s, nullptr, nullptr, (float2 *)h->Hg32, h->Hd32, h->flags,  \
+                                                stage);                                                         \
     break;
     CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
 #undef CASE

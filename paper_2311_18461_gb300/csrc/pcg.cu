@@ -77,30 +77,26 @@ __global__ void k_copy_vec(const T *__restrict__ a, T *__restrict__ b, long long
     b[i] = a[i];
 }
 
-// alpha = rho / <p, q>
-__global__ void k_pcg_alpha(PcgCtl *ctl, const double *ppq, int npq) {
-  if (ctl->done) return;
-  __shared__ double sh[32];
-  double pq = reduce_partials(ppq, npq, sh);
-  if (threadIdx.x == 0) {
-    ctl->pq = pq;
-    if (!(pq > 0.0) || !isfinite(pq)) {
-      ctl->alpha = 0.0;
-      ctl->status = STST_BREAKDOWN;
-      ctl->done = 1;
-    } else {
-      ctl->alpha = ctl->rho / pq;
-    }
-  }
-}
-
-// x += alpha p; r -= alpha q; partials of ||r||^2 and (flexible) Re<r, z_old>
+// alpha = rho / <p, q> (every CTA reduces the same partials in the same order; CTA 0 records it),
+// then x += alpha p; r -= alpha q; partials of ||r||^2 and (flexible) Re<r, z_old>
+// rho = <r, z> is reduced from the partials of the latest preconditioner application (prz_in), so no
+// CTA of this kernel reads a scalar that another CTA of it writes.
 template <typename T>
 __global__ void k_update_xr(T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p, const T *__restrict__ q,
-                            const T *__restrict__ zold, const PcgCtl *ctl, long long n, double *prr, double *prz) {
+                            const T *__restrict__ zold, PcgCtl *ctl, long long n, double *prr, double *prz,
+                            const double *ppq, int npq, const double *prz_in, int nrz_in) {
   if (ctl->done) return;
   __shared__ double sh[32];
-  const double alpha = ctl->alpha;
+  const double pq = reduce_partials(ppq, npq, sh);
+  const double rho = reduce_partials(prz_in, nrz_in, sh);
+  const bool bad = !(pq > 0.0) || !isfinite(pq);
+  const double alpha = bad ? 0.0 : rho / pq;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->pq = pq;
+    ctl->rho = rho;
+    ctl->alpha = alpha;
+    if (bad) ctl->status = STST_BREAKDOWN;  // the check kernel ends the loop
+  }
   double arr = 0.0, arz = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     T pv = p[i], qv = q[i], xv = x[i], rv = r[i];
@@ -136,7 +132,9 @@ __global__ void k_pcg_check(PcgCtl *ctl, const double *prr, int nrr, const doubl
       ctl->it += 1;
       ctl->rr = rr;
       ctl->rz_old = rz;
-      if (!isfinite(rr)) {
+      if (ctl->status == STST_BREAKDOWN) {
+        ctl->done = 1;
+      } else if (!isfinite(rr)) {
         ctl->done = 1;
         ctl->status = STST_BREAKDOWN;
       } else if (rr <= ctl->tol2 * ctl->ff) {
@@ -152,27 +150,20 @@ __global__ void k_pcg_check(PcgCtl *ctl, const double *prr, int nrr, const doubl
   }
 }
 
-// beta (Fletcher-Reeves form, or Polak-Ribiere when flexible) and rho update
-__global__ void k_pcg_beta(PcgCtl *ctl, const double *prz, int nrz) {
+// beta from the new <r, z> partials (Fletcher-Reeves, or Polak-Ribiere when flexible), p = z + beta p.
+// rho_old (written by k_update_xr) and rz_old (written by the check kernel) come from earlier
+// kernels; this kernel writes no scalar that its own CTAs read.
+template <typename T>
+__global__ void k_update_p(T *__restrict__ p, const T *__restrict__ z, PcgCtl *ctl, long long n, const double *prz,
+                           int nrz) {
   if (ctl->done) return;
   __shared__ double sh[32];
-  double rho_new = reduce_partials(prz, nrz, sh);
-  if (threadIdx.x == 0) {
-    double beta = ctl->flexible ? (rho_new - ctl->rz_old) / ctl->rho : rho_new / ctl->rho;
-    if (!(rho_new > 0.0) || !isfinite(rho_new)) {
-      ctl->done = 1;
-      ctl->status = STST_BREAKDOWN;
-      beta = 0.0;
-    }
-    ctl->beta = beta;
-    ctl->rho = rho_new;
-  }
-}
-
-template <typename T>
-__global__ void k_update_p(T *__restrict__ p, const T *__restrict__ z, const PcgCtl *ctl, long long n) {
-  if (ctl->done) return;
-  const double beta = ctl->beta;
+  const double rho_old = ctl->rho, rz_old = ctl->rz_old;
+  const int flexible = ctl->flexible;
+  const double rho_new = reduce_partials(prz, nrz, sh);
+  const bool bad = !(rho_new > 0.0) || !isfinite(rho_new);
+  const double beta = bad ? 0.0 : (flexible ? (rho_new - rz_old) / rho_old : rho_new / rho_old);
+  if (bad && blockIdx.x == 0 && threadIdx.x == 0) ctl->status = STST_BREAKDOWN;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     T pv = p[i], zv = z[i];
     pv.x = zv.x + beta * pv.x;
@@ -190,21 +181,20 @@ static int pcg_body(stst_problem *h, cudaGraphConditionalHandle cond, int use_co
   const int g = reduction_grid(N);
   const int prec = h->prec_mode == STST_PREC_FP64 ? 0 : 1;
   double *P = h->partials;
-  double *pA = P, *pB = P + STST_MAXPART, *pC = P + 2 * STST_MAXPART;
+  double *pA = P, *pB = P + STST_MAXPART, *pC = P + 2 * STST_MAXPART, *pD = P + 3 * STST_MAXPART;
   const int *done = &h->ctl->done;
   const int flexible = prec != 0;
+  const int nrz = fd_partials_count(h);
   // q = A p, partials <p, q>
-  STST_TRY(run_plan(h->sys_plan, h->w_p, h->w_q, 0, 0, nullptr, h->w_p, pA, done, st));
-  { STST_PROF("pcg_scalar", st); k_pcg_alpha<<<1, 1024, 0, st>>>(h->ctl, pA, g); }
-  // x, r update (+ Re<r_new, z_old> for the flexible beta)
+  STST_TRY(run_plan(h->sys_plan, h->w_p, h->w_q, 0, 0, nullptr, h->w_p, pD, done, st));
+  // alpha; x, r update (+ Re<r_new, z_old> for the flexible beta)
   { STST_PROF("pcg_update_xr", st); k_update_xr<double2><<<g, 256, 0, st>>>((double2 *)h->w_x, (double2 *)h->w_r, (const double2 *)h->w_p,
                                           (const double2 *)h->w_q, flexible ? (const double2 *)h->w_z : nullptr,
-                                          h->ctl, N, pB, pC); }
+                                          h->ctl, N, pB, pC, pD, g, pA, nrz); }
   { STST_PROF("pcg_scalar", st); k_pcg_check<<<1, 1024, 0, st>>>(h->ctl, pB, g, flexible ? pC : nullptr, flexible ? g : 0, cond, use_cond); }
   // z = P^{-1} r, partials <r, z>
   STST_TRY(fd_apply(h, h->w_r, h->w_z, prec, h->w_r, pA, done, h->w_t1, h->w_t2));
-  { STST_PROF("pcg_scalar", st); k_pcg_beta<<<1, 1024, 0, st>>>(h->ctl, pA, fd_partials_count(h)); }
-  { STST_PROF("pcg_update_p", st); k_update_p<double2><<<g, 256, 0, st>>>((double2 *)h->w_p, (const double2 *)h->w_z, h->ctl, N); }
+  { STST_PROF("pcg_update_p", st); k_update_p<double2><<<g, 256, 0, st>>>((double2 *)h->w_p, (const double2 *)h->w_z, h->ctl, N, pA, nrz); }
   STST_CUDA(cudaGetLastError());
   return STST_OK;
 }
@@ -362,18 +352,18 @@ static int inner_body(stst_problem *h, cudaGraphConditionalHandle cond, int use_
   const long long N = h->N_dof;
   const int g = reduction_grid(N);
   double *P = h->partials;
-  double *pA = P, *pB = P + STST_MAXPART, *pC = P + 2 * STST_MAXPART;
+  double *pA = P, *pB = P + STST_MAXPART, *pC = P + 2 * STST_MAXPART, *pD = P + 3 * STST_MAXPART;
   const int *done = &h->ctl2->done;
-  STST_TRY(run_plan(h->sys_plan, h->v_p, h->v_q, 1, 0, nullptr, h->v_p, pA, done, st));
-  { STST_PROF("pcg_scalar", st); k_pcg_alpha<<<1, 1024, 0, st>>>(h->ctl2, pA, g); }
+  const int nrz = fd_partials_count(h);
+  STST_TRY(run_plan(h->sys_plan, h->v_p, h->v_q, 1, 0, nullptr, h->v_p, pD, done, st));
   { STST_PROF("pcg_update_xr", st);
     k_update_xr<float2><<<g, 256, 0, st>>>((float2 *)h->v_d, (float2 *)h->v_r, (const float2 *)h->v_p,
-                                           (const float2 *)h->v_q, (const float2 *)h->v_z, h->ctl2, N, pB, pC); }
+                                           (const float2 *)h->v_q, (const float2 *)h->v_z, h->ctl2, N, pB, pC,
+                                           pD, g, pA, nrz); }
   { STST_PROF("pcg_scalar", st); k_pcg_check<<<1, 1024, 0, st>>>(h->ctl2, pB, g, pC, g, cond, use_cond); }
   STST_TRY(fd_apply(h, nullptr, nullptr, 1, h->v_r, pA, done, h->w_t1, h->w_t2, h->v_z, h->v_r));
-  { STST_PROF("pcg_scalar", st); k_pcg_beta<<<1, 1024, 0, st>>>(h->ctl2, pA, fd_partials_count(h)); }
   { STST_PROF("pcg_update_p", st);
-    k_update_p<float2><<<g, 256, 0, st>>>((float2 *)h->v_p, (const float2 *)h->v_z, h->ctl2, N); }
+    k_update_p<float2><<<g, 256, 0, st>>>((float2 *)h->v_p, (const float2 *)h->v_z, h->ctl2, N, pA, nrz); }
   STST_CUDA(cudaGetLastError());
   return STST_OK;
 }

@@ -103,7 +103,9 @@ def test_apply_prec_fp32(n_el, p):
     r = random_complex(prob.n_dof, 13)
     s = to_np(prob.apply_prec(to_dev(r)))
     ref = ofd.FastDiagonalization(disc).apply(r)
-    assert rel_err(s, ref) < 1e-5
+    # FP32 (u = 6e-8): the mode products accumulate n_l <= 128 terms (n u ~ 1e-5 at worst) and the
+    # banded solves lose kappa(H_i) ~ 1e2 (u kappa ~ 1e-5): the FD apply is good to a few 1e-5
+    assert rel_err(s, ref) < 5e-5
 
 
 @pytest.mark.parametrize("n_el,p,kind", [([8, 9], [2, 3], None), ([6, 7, 5], [2, 2, 3], "harmonic"),
