@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="c2")
-    ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32"])
+    ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--solver", default="pcg", choices=["pcg", "ir"])
     ap.add_argument("--inner-tol", type=float, default=1e-4)
     return ap.parse_args()
@@ -148,7 +148,8 @@ def build_problem(cfg, V, u0, prec, stream):
     import paper_2311_18461_gb300 as S
     d = cfg["d"]
     prob = S.Problem(d, cfg["n_el"], [cfg["p"]] * (d + 1), T=cfg["T"], nu=cfg["nu"],
-                     prec_mode=S.STST_PREC_FP64 if prec == "fp64" else S.STST_PREC_FP32, stream=stream)
+                     prec_mode={"fp64": S.STST_PREC_FP64, "fp32": S.STST_PREC_FP32, "bf16": S.STST_PREC_BF16}[prec],
+                     stream=stream)
     if V:
         cols = [sample_1d(prob, term[l - 1], l) for term in V for l in range(1, d + 1)]
         prob.set_potential(torch.tensor(np.concatenate(cols), dtype=torch.float64, device="cuda"), len(V))
@@ -303,7 +304,11 @@ def run_ours(args):
     if dom:
         cnt, tot = prof[dom]
         per_launch_s = tot / cnt / 1e3
-        if dom.startswith("modeprod"):
+        if dom.startswith("modeprod_bf16"):
+            # HBM/L2 bound on tensor cores: read FP32 tile + write FP32 result per complex unknown
+            roof = {"kernel": dom, "bound": "hbm", "achieved": 16.0 * n_dof / per_launch_s / 1e9,
+                    "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+        elif dom.startswith("modeprod"):
             flops = 4.0 * (sum(n_l) / d) * n_dof
             peak = fp64_peak if dom.endswith("f64") else fp32_peak
             roof = {"kernel": dom, "bound": "alu", "achieved": flops / per_launch_s / 1e12,
@@ -335,7 +340,7 @@ def run_ours(args):
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64" if args.prec == "fp64" else "f64+f32",
+        "dtype": {"fp64": "f64", "fp32": "f64+f32", "bf16": "f64+f32+bf16"}[args.prec],
         "data": "synthetic",
         "config": {"workload": workload_name(args.config, cfg, tol),
                    "n_dof": n_dof, "preconditioner": args.prec, "solver": args.solver,

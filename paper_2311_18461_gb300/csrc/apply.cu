@@ -140,10 +140,12 @@ static int launch_pass_t(const PassK &k, int p, int grid, cudaStream_t s) {
   return STST_OK;
 }
 
-// Number of CTAs of every kernel that produces per-CTA partial sums.
+// Number of CTAs of every kernel that produces per-CTA partial sums: two per SM. Every consumer of
+// the partials reduces all of them (some redundantly in each of its CTAs), so fewer, fuller CTAs
+// keep that cheap; 16 warps per SM still cover the FP64 pipe latency of the mat-vec's last level.
 int reduction_grid(long long total) {
   int g = grid_for(total, 256);
-  if (g > 1024) g = 1024;
+  if (g > 2 * 152) g = 2 * 152;
   if (g < 1) g = 1;
   return g;
 }
@@ -589,6 +591,53 @@ int fd_apply(stst_problem *h, const double *r, double *s, int precision, const v
     }
     return STST_OK;
   }
+  if (precision == 2) {
+    // mode products on the tensor cores (BF16 operands, FP32 accumulation), time solves in FP32
+    float2 *bufs[2] = {(float2 *)bufA, (float2 *)bufB};
+    int cur = 0;
+    const float2 *src32 = nullptr;
+    int *ef = h->flags + 1;
+    // U' planes per direction: [fwd hi | bwd hi | fwd lo | bwd lo]; three-product split
+    const int split = 3;
+    auto Bk = [&](int l, int bwd) {
+      const size_t np = pad16(h->dir[l].n);
+      return (const __nv_bfloat16 *)(h->Ubf[l] + (bwd ? np * np : 0));
+    };
+    auto lo = [&](int l) { return 2LL * pad16(h->dir[l].n) * pad16(h->dir[l].n); };
+    for (int l = 1; l <= d; ++l) {
+      float2 *dst = bufs[cur];
+      if (l == 1 && !in32) {
+        STST_TRY((launch_modeprod_tc<double2, float2>((const double2 *)r, dst, Bk(l, 0), lo(l), split, h->dir[l].n, inner[l],
+                                                      outer[l], nullptr, nullptr, done, ef, st)));
+      } else {
+        const float2 *in = (l == 1) ? (const float2 *)in32 : src32;
+        STST_TRY((launch_modeprod_tc<float2, float2>(in, dst, Bk(l, 0), lo(l), split, h->dir[l].n, inner[l], outer[l], nullptr,
+                                                     nullptr, done, ef, st)));
+      }
+      src32 = dst;
+      cur ^= 1;
+    }
+    STST_TRY(launch_timesolve<float>((void *)src32, h->Hg32, h->Hd32, nt, Ns, h->dir[0].p, done, st));
+    for (int l = d; l >= 1; --l) {
+      if (l == 1) {
+        if (out32) {
+          STST_TRY((launch_modeprod_tc<float2, float2>(src32, (float2 *)out32, Bk(l, 1), lo(l), split, h->dir[l].n, inner[l],
+                                                       outer[l], (const float2 *)dotvec, dot_partials, done, ef, st)));
+        } else {
+          STST_TRY((launch_modeprod_tc<float2, double2>(src32, (double2 *)s, Bk(l, 1), lo(l), split, h->dir[l].n, inner[l],
+                                                        outer[l], (const double2 *)dotvec, dot_partials, done, ef,
+                                                        st)));
+        }
+      } else {
+        float2 *dst = bufs[cur];
+        STST_TRY((launch_modeprod_tc<float2, float2>(src32, dst, Bk(l, 1), lo(l), split, h->dir[l].n, inner[l], outer[l], nullptr,
+                                                     nullptr, done, ef, st)));
+        src32 = dst;
+        cur ^= 1;
+      }
+    }
+    return STST_OK;
+  }
   // FP32
   float2 *bufs[2] = {(float2 *)bufA, (float2 *)bufB};
   int cur = 0;
@@ -636,5 +685,6 @@ int fd_apply(stst_problem *h, const double *r, double *s, int precision, const v
 // grid of the last backward mode product (number of partials it writes)
 int fd_partials_count(stst_problem *h) {
   long long ncols = h->N_dof / h->dir[1].n;
+  if (h->prec_mode == STST_PREC_BF16) return tc_partials_count(ncols);
   return grid_for(ncols, 32);
 }

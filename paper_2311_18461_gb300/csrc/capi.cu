@@ -374,6 +374,7 @@ void destroy_all(stst_problem *h) {
   cudaFree(h->ctl2);
   cudaFree(h->proj_work);
   if (h->ctl_host) cudaFreeHost(h->ctl_host);
+  if (h->flags_host) cudaFreeHost(h->flags_host);
   if (h->pcg_exec) cudaGraphExecDestroy(h->pcg_exec);
   if (h->ir_exec) cudaGraphExecDestroy(h->ir_exec);
   if (h->prof) {
@@ -442,7 +443,7 @@ int create_impl(stst_problem *h, int d, const int *n_el, const int *p, double T,
     STST_TRY(launch_mass_cholesky(h->mats[l][SM_M], h->mchol[l], h->flags, st));
     STST_TRY(alloc((void **)&h->U[l], sizeof(double) * D.n * D.n));
     STST_TRY(alloc((void **)&h->U32[l], sizeof(float) * D.n * D.n));
-    STST_TRY(alloc((void **)&h->Ubf[l], sizeof(__nv_bfloat16) * D.n * D.n));
+    STST_TRY(alloc((void **)&h->Ubf[l], sizeof(__nv_bfloat16) * 4 * pad16(D.n) * pad16(D.n)));
     STST_TRY(alloc((void **)&h->lam[l], sizeof(double) * D.n));
   }
   int nmax = 1;
@@ -463,6 +464,11 @@ int create_impl(stst_problem *h, int d, const int *n_el, const int *p, double T,
   for (float **v : vs) STST_TRY(alloc((void **)v, sizeof(float2) * (size_t)h->N_dof));
   {
     cudaError_t e = cudaMallocHost(&h->ctl_host, 2 * sizeof(PcgCtl));
+    if (e != cudaSuccess) {
+      stst_last_cuda = e;
+      return STST_ERR_OOM;
+    }
+    e = cudaMallocHost(&h->flags_host, 4 * sizeof(int));
     if (e != cudaSuccess) {
       stst_last_cuda = e;
       return STST_ERR_OOM;
@@ -703,7 +709,7 @@ int stst_apply_prec(stst_handle h, const double *r, double *s) {
   ApiScope scope(h);
   if (!r || !s) return STST_ERR_ARG;
   if (!h->fd_ready) return STST_ERR_STATE;
-  int prec = h->prec_mode == STST_PREC_FP64 ? 0 : 1;
+  int prec = h->prec_mode;  // STST_PREC_* equals fd_apply's precision code
   return fd_apply(h, r, s, prec, nullptr, nullptr, nullptr, h->w_t1, h->w_t2);
 }
 

@@ -125,7 +125,8 @@ struct stst_problem {
   double *Hd;                      // FP64 inverse diagonals n_t x N_s
   void *Hg32;                      // FP32 factors
   float *Hd32;
-  int *flags;                      // device status flags (NOT_HPD, ...)
+  int *flags;                      // device status flags: [0] factorization pivots, [1] bounded waits
+  int *flags_host;                 // pinned copy
 
   // plans
   Plan sys_plan, lift_plan;
@@ -192,3 +193,12 @@ int ir_run(stst_problem *h, const double *rhs, double *x, double tol, int maxit,
            int inner_maxit, int *iters, int *outer, double *relres);
 
 int grid_for(long long n, int block);
+
+// tensor-core mode products (modeprod_tc.cu)
+int launch_u_to_bf16(const double *U, int n, __nv_bfloat16 *out, cudaStream_t s);
+template <typename TI, typename TO>
+int launch_modeprod_tc(const TI *X, TO *Y, const __nv_bfloat16 *Bk, long long lo_stride, int split, int n,
+                       long long inner, long long outer, const TO *dotvec, double *dot_partials, const int *done,
+                       int *errflag, cudaStream_t s);
+int tc_partials_count(long long ncols);
+inline int pad16(int n) { return (n + 15) / 16 * 16; }

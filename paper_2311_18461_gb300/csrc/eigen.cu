@@ -421,7 +421,7 @@ int fd_setup(stst_problem *h) {
   const int d = h->d;
   STST_CUDA(cudaMemsetAsync(h->flags, 0, sizeof(int) * 4, st));
   for (int l = 1; l <= d; ++l) {
-    int src = l;
+    int src = l;  // directions with the same degree and mesh share one eigendecomposition
     for (int k = 1; k < l; ++k)
       if (h->dir[k].p == h->dir[l].p && h->dir[k].n_el == h->dir[l].n_el) { src = k; break; }
     h->eig_src[l] = src;
@@ -456,6 +456,7 @@ int fd_setup(stst_problem *h) {
       STST_CUDA(cudaMemcpyAsync(h->lam[l], h->lam[src], sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     }
     STST_TRY(launch_to_f32(h->U[l], h->U32[l], (long long)h->dir[l].n * h->dir[l].n, st));
+    if (h->prec_mode == STST_PREC_BF16) STST_TRY(launch_u_to_bf16(h->U[l], h->dir[l].n, h->Ubf[l], st));
   }
   const BandMat &Lt = h->mats[0][0], &Mt = h->mats[0][1], &KAt = h->mats[0][2];
   const float *Lt32 = h->mats32[0][0], *Mt32 = h->mats32[0][1], *KAt32 = h->mats32[0][2];

@@ -179,7 +179,7 @@ static int pcg_body(stst_problem *h, cudaGraphConditionalHandle cond, int use_co
   cudaStream_t st = h->stream;
   const long long N = h->N_dof;
   const int g = reduction_grid(N);
-  const int prec = h->prec_mode == STST_PREC_FP64 ? 0 : 1;
+  const int prec = h->prec_mode;  // STST_PREC_* equals fd_apply's precision code
   double *P = h->partials;
   double *pA = P, *pB = P + STST_MAXPART, *pC = P + 2 * STST_MAXPART, *pD = P + 3 * STST_MAXPART;
   const int *done = &h->ctl->done;
@@ -203,7 +203,7 @@ static int pcg_init(stst_problem *h) {
   cudaStream_t st = h->stream;
   const long long N = h->N_dof;
   const int g = reduction_grid(N);
-  const int prec = h->prec_mode == STST_PREC_FP64 ? 0 : 1;
+  const int prec = h->prec_mode;  // STST_PREC_* equals fd_apply's precision code
   double *P = h->partials;
   double *pA = P, *pB = P + STST_MAXPART, *pC = P + 2 * STST_MAXPART;
   // r = f - A x, partials ||r||^2 ; ||f||^2
@@ -361,7 +361,7 @@ static int inner_body(stst_problem *h, cudaGraphConditionalHandle cond, int use_
                                            (const float2 *)h->v_q, (const float2 *)h->v_z, h->ctl2, N, pB, pC,
                                            pD, g, pA, nrz); }
   { STST_PROF("pcg_scalar", st); k_pcg_check<<<1, 1024, 0, st>>>(h->ctl2, pB, g, pC, g, cond, use_cond); }
-  STST_TRY(fd_apply(h, nullptr, nullptr, 1, h->v_r, pA, done, h->w_t1, h->w_t2, h->v_z, h->v_r));
+  STST_TRY(fd_apply(h, nullptr, nullptr, h->prec_mode == STST_PREC_BF16 ? 2 : 1, h->v_r, pA, done, h->w_t1, h->w_t2, h->v_z, h->v_r));
   { STST_PROF("pcg_update_p", st);
     k_update_p<float2><<<g, 256, 0, st>>>((float2 *)h->v_p, (const float2 *)h->v_z, h->ctl2, N, pA, nrz); }
   STST_CUDA(cudaGetLastError());
@@ -446,7 +446,7 @@ int ir_run(stst_problem *h, const double *rhs, double *x, double tol, int maxit,
     h->ctl_host[1] = hc2;
     STST_CUDA(cudaMemcpyAsync(h->ctl2, &h->ctl_host[1], sizeof(PcgCtl), cudaMemcpyHostToDevice, st));
     { STST_PROF("norm2", st); k_norm2<float2><<<g, 256, 0, st>>>((const float2 *)h->v_r, N, pC); }
-    STST_TRY(fd_apply(h, nullptr, nullptr, 1, h->v_r, pA, nullptr, h->w_t1, h->w_t2, h->v_z, h->v_r));
+    STST_TRY(fd_apply(h, nullptr, nullptr, h->prec_mode == STST_PREC_BF16 ? 2 : 1, h->v_r, pA, nullptr, h->w_t1, h->w_t2, h->v_z, h->v_r));
     { STST_PROF("pcg_scalar", st);
       k_pcg_init<<<1, 1024, 0, st>>>(h->ctl2, pC, g, pC, g, pA, fd_partials_count(h)); }
     { STST_PROF("copy", st);

@@ -108,6 +108,32 @@ def test_apply_prec_fp32(n_el, p):
     assert rel_err(s, ref) < 5e-5
 
 
+@pytest.mark.parametrize("n_el,p", [([9, 11, 7], [2, 3, 2]), ([5, 6, 5, 7], [2, 2, 3, 2]), ([32, 32], 2),
+                                   ([6, 126], [2, 4]), ([64, 64, 64], [3, 3, 3])])
+def test_apply_prec_bf16_tensor_cores(n_el, p):
+    """Mode products on tcgen05 tensor cores: BF16 operands split into high and low parts, FP32 accumulation."""
+    prob, disc = _problem(n_el, p, None, prec=S.STST_PREC_BF16)
+    prob.build_fd()
+    r = random_complex(prob.n_dof, 14)
+    s = to_np(prob.apply_prec(to_dev(r)))
+    ref = ofd.FastDiagonalization(disc).apply(r)
+    # with x = x_hi + x_lo and U = U_hi + U_lo in BF16 the three products keep ~16 significant bits
+    # (dropped x_lo U_lo and the lo rounding are ~2^-17 relative), the FP32 time solves lose
+    # kappa(H_i) ~ 1e2 times FP32 rounding: the FD apply is good to about 1e-4 relative
+    assert rel_err(s, ref) < 1e-4
+
+
+@pytest.mark.parametrize("n_el,p,kind", [([9, 11, 7], [2, 3, 2], "harmonic"), ([5, 6, 5, 7], [2, 2, 3, 2], None)])
+def test_pcg_bf16_preconditioner_solution(n_el, p, kind):
+    prob, disc = _problem(n_el, p, kind, prec=S.STST_PREC_BF16)
+    prob.build_fd()
+    b = random_complex(prob.n_dof, 24)
+    x, st, it, rr = prob.pcg(to_dev(b), tol=1e-12, maxit=300)
+    xo, _, _, _ = opcg.pcg(disc.apply, ofd.FastDiagonalization(disc).apply, b, tol=1e-13, maxit=300)
+    assert st == 0
+    assert rel_err(to_np(x), xo) < 1e-8
+
+
 @pytest.mark.parametrize("n_el,p,kind", [([8, 9], [2, 3], None), ([6, 7, 5], [2, 2, 3], "harmonic"),
                                          ([4, 5, 4, 3], 2, "bump")])
 def test_rhs_lifting_and_forcing(n_el, p, kind):
