@@ -263,3 +263,19 @@ int launch_scale(const double *a, double c, double *out, float *out32, int n, cu
   STST_CUDA(cudaGetLastError());
   return STST_OK;
 }
+
+__global__ void k_band_axpby(const double *a, double ca, const double *b, double cb, double *o, float *o32, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    double v = ca * a[i] + cb * b[i];
+    o[i] = v;
+    o32[i] = (float)v;
+  }
+}
+
+int launch_band_axpby(const double *a, double ca, const double *b, double cb, double *out, float *out32, int n,
+                      cudaStream_t s) {
+  k_band_axpby<<<grid_for(n, 128), 128, 0, s>>>(a, ca, b, cb, out, out32, n);
+  STST_CUDA(cudaGetLastError());
+  return STST_OK;
+}

@@ -249,6 +249,52 @@ std::vector<Term> base_terms(const stst_problem *h) {
   return T;
 }
 
+// c1 * mats[l][i1] + c2 * mats[l][i2] as a new band matrix of direction l; returns its id
+int add_combo(stst_problem *h, int l, int i1, double c1, int i2, double c2) {
+  const DirInfo &D = h->dir[l];
+  BandMat B;
+  B.n = D.n;
+  B.p = D.p;
+  const int nb = B.n * (2 * B.p + 1);
+  STST_TRY(alloc((void **)&B.d, sizeof(double) * nb));
+  float *f32;
+  STST_TRY(alloc((void **)&f32, sizeof(float) * nb));
+  STST_TRY(launch_band_axpby(h->mats[l][i1].d, c1, h->mats[l][i2].d, c2, B.d, f32, nb, h->stream));
+  h->mats[l].push_back(B);
+  h->mats32[l].push_back(f32);
+  return (int)h->mats[l].size() - 1;
+}
+
+// Kronecker terms that differ in the matrix of a single spatial mode are combined:
+// c1 (.. x A x ..) + c2 (.. x B x ..) = (.. x (c1 A + c2 B) x ..). Fewer terms mean fewer band
+// applications in every level of the sum-factorised mat-vec. Time matrices are never combined
+// (the imaginary advection term and the lifting's unrestricted time columns stay separate).
+std::vector<Term> combine_terms(stst_problem *h, std::vector<Term> t) {
+  const int d = h->d;
+  for (bool found = true; found;) {
+    found = false;
+    for (size_t i = 0; i < t.size() && !found; ++i)
+      for (size_t j = i + 1; j < t.size() && !found; ++j) {
+        int diff = -1, ndiff = 0;
+        for (int l = 0; l <= d; ++l)
+          if (t[i].m[l] != t[j].m[l]) {
+            diff = l;
+            ndiff++;
+          }
+        if (ndiff != 1 || diff == 0) continue;
+        const int id = add_combo(h, diff, t[i].m[diff], t[i].coef, t[j].m[diff], t[j].coef);
+        if (id < 0) return t;
+        Term m = t[i];
+        m.coef = 1.0;
+        m.m[diff] = id;
+        t[i] = m;
+        t.erase(t.begin() + j);
+        found = true;
+      }
+  }
+  return t;
+}
+
 std::vector<Term> merge_terms(const std::vector<Term> &in) {
   std::vector<Term> out;
   for (const Term &t : in) {
@@ -686,7 +732,7 @@ int stst_set_potential(stst_handle h, int rank, const double *v_qp) {
     }
     h->pot_rank = rank;
   }
-  STST_TRY(replan(h, merge_terms(terms)));
+  STST_TRY(replan(h, combine_terms(h, merge_terms(terms))));
   STST_CUDA(cudaStreamSynchronize(st));
   return STST_OK;
 }

@@ -177,6 +177,8 @@ int launch_mass_cholesky(const BandMat &M, double *chol, int *flags, cudaStream_
 int launch_to_f32(const double *src, float *dst, long long n, cudaStream_t s);
 int launch_weight_product(const double *a, const double *b, double *out, int n, cudaStream_t s);
 int launch_scale(const double *a, double c, double *out, float *out32, int n, cudaStream_t s);
+int launch_band_axpby(const double *a, double ca, const double *b, double cb, double *out, float *out32, int n,
+                      cudaStream_t s);
 
 int run_plan(const Plan &plan, const void *x, void *y, int precision, int epi, const void *b, const void *dotvec,
              double *dot_partials, const int *done, cudaStream_t s, const void *dot2vec = nullptr,
