@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--solver", default="pcg", choices=["pcg", "ir"])
     ap.add_argument("--inner-tol", type=float, default=1e-4)
+    ap.add_argument("--batch", type=int, default=128, help="number of problems of the c4 workload")
     return ap.parse_args()
 
 
@@ -172,6 +173,104 @@ def workload_name(name, cfg, tol):
     u0 = "sin(pi x) initial datum" if cfg["u0"] == "sine" else "windowed Gaussian wavepacket u0"
     return (f"{name}: {d}D+t p={cfg['p']} {space} x {cfg['n_el'][0]} elements, {pot}, {u0}, complex128, "
             f"tol {tol:g}")
+
+
+def run_batch(args):
+    """Batched workload: 128 heterogeneous 2D+t problems solved by one graph launch per step."""
+    import numpy as np
+    import torch
+    import paper_2311_18461_gb300 as S
+    from inputs import c4_instances
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    torch.cuda.set_device(local)
+    n_inst = args.batch
+    specs = c4_instances(n_inst)
+    prec = {"fp64": S.STST_PREC_FP64, "fp32": S.STST_PREC_FP32, "bf16": S.STST_PREC_BF16}[args.prec]
+    probs, rhs, xs = [], [], []
+    for sp in specs:
+        prob = S.Problem(2, sp["n_el"], [sp["p"]] * 3, prec_mode=prec)
+        cols = [sample_1d(prob, term[l - 1], l) for term in sp["potential_terms"] for l in (1, 2)]
+        prob.set_potential(torch.tensor(np.concatenate(cols), dtype=torch.float64, device="cuda"),
+                           len(sp["potential_terms"]))
+        g1, g2 = (prob.quad_points(l).cpu().numpy() for l in (1, 2))
+        U = np.asarray(sp["u0_factors"][1](g2)).reshape(-1, 1) * np.asarray(sp["u0_factors"][0](g1)).reshape(1, -1)
+        b = prob.rhs(None, torch.tensor(np.ascontiguousarray(U).ravel(), dtype=torch.complex128, device="cuda"))
+        probs.append(prob)
+        rhs.append(b)
+        xs.append(prob.vec())
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    batch = S.stst_batch_create([p.h for p in probs], rhs, xs, stream)
+    tol = 1e-8
+    n_dof = sum(p.n_dof for p in probs)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def step():
+        for x in xs:
+            x.zero_()
+        return S.stst_batch_solve(batch, n_inst, tol, 200)
+
+    for _ in range(max(args.warmup, 3)):
+        status, iters, relres, sts = step()
+    assert status == 0, f"batch failed: {sts}"
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        status, iters, relres, sts = step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    # end to end: right-hand sides from pinned host memory in, solutions out, every step
+    b_host = [b.cpu().pin_memory() for b in rhs]
+    x_host = [torch.empty_like(h).pin_memory() for h in b_host]
+    e2e = []
+    for k in range(args.steps + 1):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        with torch.cuda.stream(stream):
+            for bd, bh in zip(rhs, b_host):
+                bd.copy_(bh, non_blocking=True)
+        step()
+        with torch.cuda.stream(stream):
+            for xd, xh in zip(xs, x_host):
+                xh.copy_(xd, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if k > 0:
+            e2e.append(e0.elapsed_time(e1))
+    clocks = sampler.stop()
+    ms = statistics.mean(times)
+    out = {
+        "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f64+f32", "bf16": "f64+f32+bf16"}[args.prec],
+        "data": "synthetic",
+        "config": {"workload": f"c4: {n_inst} 2D+t problems, n_el in {{16..96}}^2 x {{16..96}}, p in {{2,3,4}}, "
+                               f"random separable potentials (rank <= 3), wavepackets, seeds 4+i, tol {tol:g}",
+                   "n_dof_total": n_dof, "step": "one graph launch: setup + PCG of every problem",
+                   "pcg_iterations": {"min": min(iters), "median": statistics.median(iters), "max": max(iters)},
+                   "l2": "flushed (512 MB write) before each step", "parallelism": f"replicas x{world}"},
+        "dofs_per_s": n_dof / (ms / 1e3),
+        "clocks": clocks,
+        "e2e": {"value": statistics.mean(e2e) / 1e3, "unit": "s", "h2d_bytes_per_step": 16 * n_dof,
+                "d2h_bytes_per_step": 16 * n_dof},
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    S.stst_batch_destroy(batch)
+    for p in probs:
+        p.close()
 
 
 def run_ours(args):
@@ -440,7 +539,10 @@ def main():
     else:
         from paper_2311_18461_gb300 import build
         build.build()
-        run_ours(args)
+        if args.config == "c4":
+            run_batch(args)
+        else:
+            run_ours(args)
 
 
 if __name__ == "__main__":

@@ -190,6 +190,26 @@ int stst_ir_solve(stst_handle h, const double *rhs, double *x, double tol, int m
                   int inner_maxit, int *iters, int *outer, double *relres);
 
 /*
+ * Batched solves (an extension; the paper solves one problem at a time).
+ * stst_batch_create: builds ONE CUDA graph that solves `count` independent problems, each given by
+ * its own handle (any sizes, degrees, potentials, precision modes), its right-hand side rhs[i] and
+ * its solution array x[i] (device pointers, fixed at creation; x[i] holds the initial guess on
+ * input). Each problem is a separate branch of the graph: preconditioner setup as in
+ * stst_build_fd, then PCG as in stst_pcg_solve with its loop as a conditional WHILE node; the
+ * branches share nothing, so the GPU runs them concurrently. Handles must be distinct and must not
+ * be used by other calls while a batch solve runs. stream: NULL creates a stream for the batch.
+ * Allocates; the handles keep their own workspaces.
+ * stst_batch_solve: one graph launch solving every problem to ||rhs - A x|| <= tol ||rhs|| within
+ * maxit iterations; waits for completion. iters, relres, status (host arrays of length count, may be
+ * NULL) receive each problem's outcome; the return value is STST_OK or the first non-OK status.
+ */
+typedef struct stst_batch_s *stst_batch;
+int stst_batch_create(stst_batch *b, int count, const stst_handle *handles, const double *const *rhs,
+                      double *const *x, void *stream);
+int stst_batch_solve(stst_batch b, double tol, int maxit, int *iters, double *relres, int *status);
+int stst_batch_destroy(stst_batch b);
+
+/*
  * stst_profile: enable (1) or disable (0) per-kernel timing for the handle's
  * calls. Enabling clears previous records. While enabled every kernel launch
  * of a call is bracketed by CUDA events on the handle's stream and the call

@@ -9,11 +9,13 @@ library needs the built extension and raises if it is missing.
 from ._lib import (StstError, lib, library_path, stst_create, stst_destroy, stst_strerror, stst_sizes,
                    stst_quadrature_points, stst_assemble_1d, stst_set_potential, stst_build_fd, stst_apply_sys,
                    stst_apply_prec, stst_rhs, stst_rhs_noalloc, stst_pcg_solve, stst_ir_solve, stst_profile,
-                   stst_profile_read, stst_plan_info, Problem,
+                   stst_profile_read, stst_plan_info, stst_batch_create, stst_batch_solve,
+                   stst_batch_destroy, Problem,
                    STST_PREC_FP64, STST_PREC_FP32, STST_PREC_BF16)
 
 __all__ = ["StstError", "lib", "library_path", "stst_create", "stst_destroy", "stst_strerror", "stst_sizes",
            "stst_quadrature_points", "stst_assemble_1d", "stst_set_potential", "stst_build_fd", "stst_apply_sys",
            "stst_apply_prec", "stst_rhs", "stst_rhs_noalloc", "stst_pcg_solve", "stst_ir_solve", "stst_profile",
-           "stst_profile_read", "stst_plan_info", "Problem",
+           "stst_profile_read", "stst_plan_info", "stst_batch_create", "stst_batch_solve",
+           "stst_batch_destroy", "Problem",
            "STST_PREC_FP64", "STST_PREC_FP32", "STST_PREC_BF16"]

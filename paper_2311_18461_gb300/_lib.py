@@ -48,6 +48,9 @@ def lib():
             "stst_pcg_solve": [P, P, P, D, I, IP, DP],
             "stst_ir_solve": [P, P, P, D, I, D, I, IP, IP, DP],
             "stst_profile": [P, I],
+            "stst_batch_create": [ctypes.POINTER(P), I, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), P],
+            "stst_batch_solve": [P, D, I, IP, DP, IP],
+            "stst_batch_destroy": [P],
             "stst_plan_info": [P, IP, IP, DP],
             "stst_profile_read": [P, I, ctypes.c_char_p, I, ctypes.POINTER(LL), DP],
         }
@@ -170,6 +173,28 @@ def stst_ir_solve(h, rhs, x, tol, maxit, inner_tol, inner_maxit):
 
 def stst_profile(h, enable):
     return _chk(lib().stst_profile(h, int(enable)), "stst_profile")
+
+
+def stst_batch_create(handles, rhs, x, stream=None):
+    n = len(handles)
+    hs = (ctypes.c_void_p * n)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    rs = (ctypes.c_void_p * n)(*[_ptr(t) for t in rhs])
+    xs = (ctypes.c_void_p * n)(*[_ptr(t) for t in x])
+    b = ctypes.c_void_p()
+    _chk(lib().stst_batch_create(ctypes.byref(b), n, hs, rs, xs, _stream_ptr(stream)), "stst_batch_create")
+    return b
+
+
+def stst_batch_solve(b, count, tol, maxit):
+    it = (ctypes.c_int * count)()
+    rr = (ctypes.c_double * count)()
+    st = (ctypes.c_int * count)()
+    s = _chk(lib().stst_batch_solve(b, float(tol), int(maxit), it, rr, st), "stst_batch_solve")
+    return s, list(it), list(rr), list(st)
+
+
+def stst_batch_destroy(b):
+    return _chk(lib().stst_batch_destroy(b), "stst_batch_destroy")
 
 
 def stst_plan_info(h):

@@ -42,9 +42,9 @@ struct BandMat {
 };
 
 // ---- sum-factorised mat-vec plan --------------------------------------------------------------
-#define PASS_MAXIN 16
-#define PASS_MAXAPP 24
-#define PASS_MAXOUT 12
+#define PASS_MAXIN 24
+#define PASS_MAXAPP 48
+#define PASS_MAXOUT 24
 
 struct PassParams {
   int mode;                  // 0 = time, l >= 1 spatial direction
@@ -184,6 +184,10 @@ int run_plan(const Plan &plan, const void *x, void *y, int precision, int epi, c
              double *dot_partials, const int *done, cudaStream_t s, const void *dot2vec = nullptr,
              double *dot2_partials = nullptr);
 int fd_setup(stst_problem *h);
+int fd_setup_launch(stst_problem *h);
+int pcg_init(stst_problem *h);
+int pcg_body(stst_problem *h, cudaGraphConditionalHandle cond, int use_cond);
+int reduction_grid(long long total);
 // dotvec: FP64 vector (double2) when the output is FP64, FP32 (float2) when out32 is given.
 int fd_apply(stst_problem *h, const double *r, double *s, int precision, const void *dotvec, double *dot_partials,
              const int *done, void *f32_scratch_a, void *f32_scratch_b, float *out32 = nullptr,

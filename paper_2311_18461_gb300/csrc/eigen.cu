@@ -179,56 +179,74 @@ __global__ void __launch_bounds__(512) k_eig_tridiag(const double *__restrict__ 
     }
   }
   __syncthreads();
+  // 5. eigenvectors by inverse iteration on T - lam I (LU with partial pivoting, 3 sweeps).
+  //    Eigenvalues closer than 1e-5 * span to their predecessor form a cluster (the boundary outlier
+  //    modes of the B-spline pencils come in nearly degenerate symmetric / antisymmetric pairs); the
+  //    cluster's first thread computes all its vectors in turn and orthogonalizes each sweep against
+  //    the vectors already found, so the cluster's subspace is spanned rather than one vector twice.
+  const float ctol = 1e-5f * span;
   for (int j = tid; j < n; j += nth) {
-    const float lam = pv[j];
-    lam0[j] = (double)lam;
-    // 5. inverse iteration on T - lam I, LU with partial pivoting (bands: u0, u1, u2), 3 sweeps
-    //    vector in column j of X
-    const float pert = 1e-6f * span;
-    const float sh = lam + ((j & 1) ? pert : -pert) * 1e-1f;
-    for (int i = 0; i < n; ++i) X[i * ld + j] = 1.f + 0.01f * (float)((i * 7 + j * 13) % 17);
-    for (int sweep = 0; sweep < 3; ++sweep) {
-      // factor and forward-solve together; row i of U is (a0, a1, a2) on columns i, i+1, i+2
-      float *Uj = lu + (size_t)j * 3 * n;  // this thread's 3n floats
-      float a0 = dg[0] - sh, a1 = (n > 1) ? od[0] : 0.f, a2 = 0.f;
-      float rhs = X[0 * ld + j];
-      for (int i = 0; i < n; ++i) {
-        const bool has_next = (i + 1 < n);
-        float nsub = 0.f, ndia = 0.f, nsup = 0.f, nrhs = 0.f;
-        if (has_next) {
-          nsub = od[i];
-          ndia = dg[i + 1] - sh;
-          nsup = (i + 2 < n) ? od[i + 1] : 0.f;
-          nrhs = X[(i + 1) * ld + j];
+    lam0[j] = (double)pv[j];
+    if (j > 0 && pv[j] - pv[j - 1] <= ctol) continue;  // not the first of its cluster
+    int e = j + 1;
+    while (e < n && pv[e] - pv[e - 1] <= ctol) ++e;
+    float *Uj = lu + (size_t)j * 3 * n;  // this thread's 3n floats of LU storage
+    for (int a = j; a < e; ++a) {
+      const float lam = pv[a];
+      const float sh = lam + ((a & 1) ? 1e-7f : -1e-7f) * span;
+      for (int i = 0; i < n; ++i) X[i * ld + a] = 1.f + 0.01f * (float)((i * 7 + a * 13) % 17);
+      for (int sweep = 0; sweep < 3; ++sweep) {
+        // factor and forward-solve together; row i of U is (a0, a1, a2) on columns i, i+1, i+2
+        float a0 = dg[0] - sh, a1 = (n > 1) ? od[0] : 0.f, a2 = 0.f;
+        float rhs = X[0 * ld + a];
+        for (int i = 0; i < n; ++i) {
+          const bool has_next = (i + 1 < n);
+          float nsub = 0.f, ndia = 0.f, nsup = 0.f, nrhs = 0.f;
+          if (has_next) {
+            nsub = od[i];
+            ndia = dg[i + 1] - sh;
+            nsup = (i + 2 < n) ? od[i + 1] : 0.f;
+            nrhs = X[(i + 1) * ld + a];
+          }
+          if (has_next && fabsf(nsub) > fabsf(a0)) {  // partial pivoting on column i
+            float t0 = a0, t1 = a1, t2 = a2, tr = rhs;
+            a0 = nsub; a1 = ndia; a2 = nsup; rhs = nrhs;
+            nsub = t0; ndia = t1; nsup = t2; nrhs = tr;
+          }
+          if (fabsf(a0) < 1e-30f) a0 = 1e-30f;
+          Uj[3 * i + 0] = a0;
+          Uj[3 * i + 1] = a1;
+          Uj[3 * i + 2] = a2;
+          X[i * ld + a] = rhs;
+          if (has_next) {
+            const float f = nsub / a0;
+            const float na0 = ndia - f * a1, na1 = nsup - f * a2, nr = nrhs - f * rhs;
+            a0 = na0; a1 = na1; a2 = 0.f; rhs = nr;
+          }
         }
-        if (has_next && fabsf(nsub) > fabsf(a0)) {  // partial pivoting on column i
-          float t0 = a0, t1 = a1, t2 = a2, tr = rhs;
-          a0 = nsub; a1 = ndia; a2 = nsup; rhs = nrhs;
-          nsub = t0; ndia = t1; nsup = t2; nrhs = tr;
+        float x1 = 0.f, x2 = 0.f;
+        for (int i = n - 1; i >= 0; --i) {
+          const float u0 = Uj[3 * i], u1 = Uj[3 * i + 1], u2 = Uj[3 * i + 2];
+          const float xi = (X[i * ld + a] - u1 * x1 - u2 * x2) / u0;
+          X[i * ld + a] = xi;
+          x2 = x1;
+          x1 = xi;
         }
-        if (fabsf(a0) < 1e-30f) a0 = 1e-30f;
-        Uj[3 * i + 0] = a0;
-        Uj[3 * i + 1] = a1;
-        Uj[3 * i + 2] = a2;
-        X[i * ld + j] = rhs;
-        if (has_next) {
-          const float f = nsub / a0;
-          const float na0 = ndia - f * a1, na1 = nsup - f * a2, nr = nrhs - f * rhs;
-          a0 = na0; a1 = na1; a2 = 0.f; rhs = nr;
+        // normalize (2-norm, scaled first against overflow), then orthogonalize against the cluster
+        float mx = 0.f;
+        for (int i = 0; i < n; ++i) mx = fmaxf(mx, fabsf(X[i * ld + a]));
+        const float sc = mx > 0.f ? 1.f / mx : 1.f;
+        for (int i = 0; i < n; ++i) X[i * ld + a] *= sc;
+        for (int b2 = j; b2 < a; ++b2) {
+          float dot = 0.f;
+          for (int i = 0; i < n; ++i) dot += X[i * ld + a] * X[i * ld + b2];
+          for (int i = 0; i < n; ++i) X[i * ld + a] -= dot * X[i * ld + b2];
         }
+        float nr2 = 0.f;
+        for (int i = 0; i < n; ++i) nr2 += X[i * ld + a] * X[i * ld + a];
+        const float inv = nr2 > 0.f ? rsqrtf(nr2) : 1.f;
+        for (int i = 0; i < n; ++i) X[i * ld + a] *= inv;
       }
-      // back substitution
-      float x1 = 0.f, x2 = 0.f, nrm = 0.f;
-      for (int i = n - 1; i >= 0; --i) {
-        const float u0 = Uj[3 * i], u1 = Uj[3 * i + 1], u2 = Uj[3 * i + 2];
-        float xi = (X[i * ld + j] - u1 * x1 - u2 * x2) / u0;
-        X[i * ld + j] = xi;
-        x2 = x1;
-        x1 = xi;
-        nrm = fmaxf(nrm, fabsf(xi));
-      }
-      float inv = (nrm > 0.f) ? 1.f / nrm : 1.f;
-      for (int i = 0; i < n; ++i) X[i * ld + j] *= inv;
     }
   }
   __syncthreads();
@@ -295,7 +313,11 @@ __global__ void k_oa_gram(const double *__restrict__ X, const double *__restrict
   S[e] = s;
 }
 
-// lam_j = S_jj / (1 - R_jj); E_kj = (S_kj + lam_j R_kj) / (lam_j - lam_k) (k != j, separated), R_kj / 2 otherwise.
+// lam_j = S_jj / (1 - R_jj); E_kj = (S_kj + lam_j R_kj) / (lam_j - lam_k) for well separated pairs,
+// R_kj / 2 otherwise. Pairs closer than 1e-3 relative are treated as a cluster: dividing the O(eps)
+// error of an FP32 starting vector by a tiny gap would amplify it; such clusters are only
+// orthonormalized here and diagonalized exactly afterwards (k_oa_cluster).
+#define OA_CLUSTER_GAP 1e-3
 __global__ void k_oa_E(const double *__restrict__ R, const double *__restrict__ S, int n, double *E, double *lam) {
   int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n * n) return;
@@ -304,10 +326,109 @@ __global__ void k_oa_E(const double *__restrict__ R, const double *__restrict__ 
   double lk = S[k * n + k] / (1.0 - R[k * n + k]);
   double v;
   double gap = fabs(lj - lk);
-  if (k == j || !(gap > 1e-10 * (fabs(lj) + fabs(lk)))) v = 0.5 * R[e];
+  if (k == j || !(gap > OA_CLUSTER_GAP * fmax(fabs(lj), fabs(lk)))) v = 0.5 * R[e];
   else v = (S[e] + lj * R[e]) / (lj - lk);
   E[e] = v;
   if (k == j) lam[j] = lj;
+}
+
+// Exact diagonalization inside clusters of close eigenvalues (one CTA): for each run of columns whose
+// eigenvalues are within OA_CLUSTER_GAP (relative), cyclic Jacobi rotations on the block X_c^T L X_c.
+// The columns are already M-orthonormal and rotations keep them so. Y = L X_c is updated alongside.
+__global__ void k_oa_cluster(const double *__restrict__ Lb, int n, int p, double *X, double *lam, double *Y) {
+  __shared__ int cs, ce;
+  __shared__ double red[32];
+  __shared__ double rot[2];
+  const int tid = threadIdx.x, bw = 2 * p + 1;
+  int start = 0;
+  while (true) {
+    if (tid == 0) {
+      int s0 = start;
+      while (s0 + 1 < n && !(fabs(lam[s0 + 1] - lam[s0]) <= OA_CLUSTER_GAP * fmax(fabs(lam[s0]), fabs(lam[s0 + 1]))))
+        ++s0;
+      int e0 = s0 + 1;
+      while (e0 < n && fabs(lam[e0] - lam[e0 - 1]) <= OA_CLUSTER_GAP * fmax(fabs(lam[e0]), fabs(lam[e0 - 1]))) ++e0;
+      cs = s0;
+      ce = (s0 + 1 < n) ? e0 : n;
+    }
+    __syncthreads();
+    const int c0 = cs, c1 = ce;
+    __syncthreads();
+    if (c1 - c0 < 2) break;
+    // Y[:, c] = L X[:, c] for the cluster's columns
+    for (int e = tid; e < n * (c1 - c0); e += blockDim.x) {
+      const int i = e / (c1 - c0), c = c0 + e % (c1 - c0);
+      double acc = 0.0;
+      for (int k = 0; k < bw; ++k) {
+        const int m = i - p + k;
+        if (m >= 0 && m < n) acc += Lb[i * bw + k] * X[m * n + c];
+      }
+      Y[i * n + c] = acc;
+    }
+    __syncthreads();
+    for (int sweep = 0; sweep < 8; ++sweep) {
+      for (int a = c0; a < c1; ++a)
+        for (int b = a + 1; b < c1; ++b) {
+          // block entries S_aa, S_bb, S_ab
+          double saa = 0.0, sbb = 0.0, sab = 0.0;
+          for (int i = tid; i < n; i += blockDim.x) {
+            saa += X[i * n + a] * Y[i * n + a];
+            sbb += X[i * n + b] * Y[i * n + b];
+            sab += X[i * n + a] * Y[i * n + b];
+          }
+          double vals[3] = {saa, sbb, sab};
+          for (int q = 0; q < 3; ++q) {
+            double v = vals[q];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if ((tid & 31) == 0) red[(tid >> 5) + 8 * q] = v;
+          }
+          __syncthreads();
+          if (tid == 0) {
+            double A = 0, B = 0, C = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+              A += red[w];
+              B += red[w + 8];
+              C += red[w + 16];
+            }
+            double c = 1.0, sn = 0.0;
+            if (C != 0.0) {
+              const double th = (B - A) / (2.0 * C);
+              const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+              c = 1.0 / sqrt(t * t + 1.0);
+              sn = t * c;
+            }
+            rot[0] = c;
+            rot[1] = sn;
+          }
+          __syncthreads();
+          const double c = rot[0], sn = rot[1];
+          for (int i = tid; i < n; i += blockDim.x) {
+            const double xa = X[i * n + a], xb = X[i * n + b], ya = Y[i * n + a], yb = Y[i * n + b];
+            X[i * n + a] = c * xa - sn * xb;
+            X[i * n + b] = sn * xa + c * xb;
+            Y[i * n + a] = c * ya - sn * yb;
+            Y[i * n + b] = sn * ya + c * yb;
+          }
+          __syncthreads();
+        }
+    }
+    // eigenvalues of the rotated columns: lam_c = x_c^T L x_c
+    for (int c = c0; c < c1; ++c) {
+      double v = 0.0;
+      for (int i = tid; i < n; i += blockDim.x) v += X[i * n + c] * Y[i * n + c];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if ((tid & 31) == 0) red[tid >> 5] = v;
+      __syncthreads();
+      if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        lam[c] = t;
+      }
+      __syncthreads();
+    }
+    start = c1;
+    if (start >= n - 1) break;
+  }
 }
 
 // Xn = X + X E
@@ -416,7 +537,8 @@ __global__ void k_hfactor(const R *__restrict__ Lt, const R *__restrict__ Mt, co
   }
 }
 
-int fd_setup(stst_problem *h) {
+// Launches the whole setup on the handle's stream without waiting (capturable into a graph).
+int fd_setup_launch(stst_problem *h) {
   cudaStream_t st = h->stream;
   const int d = h->d;
   STST_CUDA(cudaMemsetAsync(h->flags, 0, sizeof(int) * 4, st));
@@ -446,6 +568,7 @@ int fd_setup(stst_problem *h) {
       k_oa_update<<<g, 64, 0, st>>>(X, E, n, Xn);
       STST_CUDA(cudaMemcpyAsync(X, Xn, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, st));
     }
+    { STST_PROF("eig_cluster_f64", st); k_oa_cluster<<<1, 256, 0, st>>>(L.d, n, p, X, h->lam[l], PL); }
     STST_CUDA(cudaGetLastError());
   }
   for (int l = 1; l <= d; ++l) {
@@ -485,9 +608,14 @@ int fd_setup(stst_problem *h) {
     default: return STST_ERR_ARG;
   }
   STST_CUDA(cudaGetLastError());
+  return STST_OK;
+}
+
+int fd_setup(stst_problem *h) {
+  STST_TRY(fd_setup_launch(h));
   int hflags[4];
-  STST_CUDA(cudaMemcpyAsync(hflags, h->flags, sizeof(hflags), cudaMemcpyDeviceToHost, st));
-  STST_CUDA(cudaStreamSynchronize(st));
+  STST_CUDA(cudaMemcpyAsync(hflags, h->flags, sizeof(hflags), cudaMemcpyDeviceToHost, h->stream));
+  STST_CUDA(cudaStreamSynchronize(h->stream));
   if (hflags[0] & 3) return STST_NOT_HPD;
   h->fd_ready = 1;
   return STST_OK;

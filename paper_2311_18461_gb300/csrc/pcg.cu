@@ -8,7 +8,6 @@
 // condition, so the loop always ends after at most maxit bodies and the host waits once.
 #include "common.cuh"
 
-int reduction_grid(long long total);
 int fd_partials_count(stst_problem *h);
 
 enum { PART_A = 0, PART_B = 1, PART_C = 2, PART_D = 3 };
@@ -175,7 +174,7 @@ __global__ void k_update_p(T *__restrict__ p, const T *__restrict__ z, PcgCtl *c
 // ------------------------------------------------------------------------------------------------
 // FP64 PCG
 // ------------------------------------------------------------------------------------------------
-static int pcg_body(stst_problem *h, cudaGraphConditionalHandle cond, int use_cond) {
+int pcg_body(stst_problem *h, cudaGraphConditionalHandle cond, int use_cond) {
   cudaStream_t st = h->stream;
   const long long N = h->N_dof;
   const int g = reduction_grid(N);
@@ -199,7 +198,7 @@ static int pcg_body(stst_problem *h, cudaGraphConditionalHandle cond, int use_co
   return STST_OK;
 }
 
-static int pcg_init(stst_problem *h) {
+int pcg_init(stst_problem *h) {
   cudaStream_t st = h->stream;
   const long long N = h->N_dof;
   const int g = reduction_grid(N);

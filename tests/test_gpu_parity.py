@@ -258,3 +258,25 @@ def test_status_codes():
     # zero right-hand side: converged immediately with x = 0
     x, st, it, rr = prob.pcg(prob.vec(), tol=1e-8, maxit=10)
     assert st == 0 and it == 0
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_apply_prec_size_sweep(p):
+    """Every spatial size from 1 to 100 unknowns: the eigen setup must handle the nearly degenerate
+    pairs of boundary outlier eigenvalues of the B-spline pencils (all three precisions)."""
+    bad = []
+    for n_el in list(range(1, 40)) + list(range(40, 100, 7)):
+        if n_el + p - 2 < 1:
+            continue
+        disc = oracle_disc([3, n_el], [2, p])
+        ref_fd = ofd.FastDiagonalization(disc)
+        r = random_complex(disc.N_dof, 15)
+        ref = ref_fd.apply(r)
+        for prec, tol in [(S.STST_PREC_FP64, 1e-10), (S.STST_PREC_FP32, 5e-5), (S.STST_PREC_BF16, 1e-4)]:
+            prob = S.Problem(1, [3, n_el], [2, p], prec_mode=prec)
+            assert prob.build_fd() == 0
+            err = rel_err(to_np(prob.apply_prec(to_dev(r))), ref)
+            if err > tol:
+                bad.append((n_el, prec, err))
+            prob.close()
+    assert not bad, bad
