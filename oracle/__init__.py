@@ -19,6 +19,8 @@ Modules, each citing the passage of the paper it restates:
   pcg       -- preconditioned conjugate gradients (Sec. 5.3, Sec. 6)
   rhs       -- load vector F(S B_i) and liftings of initial / boundary data (Sec. 2.2, Sec. 4.3)
   norms     -- L2 and V-norm errors (Sec. 2.1, Theorem 2)
+  warmstart -- network, loss, gradient, Adam and randomized snapshot basis of the learned warm start
+               (not in the paper: its PCG starts from zero, Sec. 6)
 
 Parity status: every function here is pinned by a `-m "not gpu"` test against
 closed forms, the paper's printed numbers, invariants or brute force, except
@@ -26,4 +28,7 @@ the separable-potential terms, whose Kronecker expansion is pinned only by
 brute-force quadrature of the same sesquilinear form (the paper has no
 potential), and the inexact-preconditioner (flexible) CG variant, which the
 paper does not define: parity unpinned beyond the exact-preconditioner case.
+The warm-start module has no counterpart in the paper; its functions are pinned against finite
+differences, closed forms and the SVD, but whether a trained warm start helps is judged only by PCG
+iterations and final error against the cold start.
 """

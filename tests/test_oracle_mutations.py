@@ -52,3 +52,48 @@ def test_lambda_instead_of_lambda_squared_is_caught():
     ref = np.linalg.solve(P, r)
     F.H = lambda li, F=F: disc.Lt + disc.nu ** 2 * li * disc.Mt + disc.nu * li * disc.Wsym
     assert np.abs(F.apply(r) - ref).max() > 1e-3 * np.abs(ref).max()
+
+
+def _mutated_loss_grad(old, new):
+    """A copy of the oracle's gradient with one planted textual change."""
+    import inspect
+    from oracle import warmstart
+    src = inspect.getsource(warmstart.loss_grad)
+    assert old in src
+    ns = dict(vars(warmstart))
+    exec(src.replace(old, new), ns)
+    return ns["loss_grad"]
+
+
+def _fd_mismatch(grad_fn):
+    from oracle import warmstart as W
+    rng = np.random.default_rng(0)
+    sizes = [3, 5, 4, 2]
+    theta = rng.standard_normal(W.n_params(sizes)) * 0.7
+    X = rng.standard_normal((7, 3))
+    T = rng.standard_normal((7, 2))
+    w = rng.uniform(0.2, 2.0, size=7)
+    _, g = grad_fn(theta, sizes, X, T, w)
+    gfd = np.zeros_like(theta)
+    for i in range(len(theta)):
+        tp, tm = theta.copy(), theta.copy()
+        tp[i] += 1e-6
+        tm[i] -= 1e-6
+        gfd[i] = (W.loss(tp, sizes, X, T, w) - W.loss(tm, sizes, X, T, w)) / 2e-6
+    return np.abs(g - gfd).max() / np.abs(gfd).max()
+
+
+def test_dropped_tanh_derivative_is_caught():
+    assert _fd_mismatch(_mutated_loss_grad("dh * (1.0 - hs[l] ** 2)", "dh")) > 1e-2
+
+
+def test_bias_gradient_taken_as_a_mean_is_caught():
+    assert _fd_mismatch(_mutated_loss_grad("dz.sum(axis=0)", "dz.mean(axis=0)")) > 1e-2
+
+
+def test_flipped_residual_sign_is_caught():
+    assert _fd_mismatch(_mutated_loss_grad("dz = 2.0 * w[:, None] * R / B", "dz = -2.0 * w[:, None] * R / B")) > 1e-2
+
+
+def test_missing_sample_weights_are_caught():
+    assert _fd_mismatch(_mutated_loss_grad("dz = 2.0 * w[:, None] * R / B", "dz = 2.0 * R / B")) > 1e-2
