@@ -231,6 +231,89 @@ int stst_profile(stst_handle h, int enable);
 int stst_plan_info(stst_handle h, int *n_passes, int *band_apps, double *flops_per_dof);
 int stst_profile_read(stst_handle h, int idx, char *name, int name_len, long long *count, double *total_ms);
 
+/* ======================================================================================
+ * Learned warm start. The paper has no learned component: these calls are an extension.
+ * A network maps a problem's data parameters to coordinates c in a basis Q of the solution
+ * space; x0 = Q^T c starts PCG (stst_pcg_solve_guarded), which stays the judge of the result.
+ * All arrays are device memory owned by the caller unless stated; calls are ordered on the
+ * given stream (the network's own stream for stst_ws_*).
+ * ====================================================================================== */
+
+/*
+ * stst_ws_create: a fully connected network sizes[0] -> sizes[1] -> ... -> sizes[n_layers]
+ * (1 <= n_layers <= 8) with tanh after every layer but the last. Parameters are packed layer by
+ * layer: W_l (sizes[l+1] x sizes[l], row-major) then b_l (sizes[l+1]). Weights are kept as an
+ * FP32 master copy (with the Adam moments) and as a BF16 copy that every product reads; biases
+ * are read in FP32; products accumulate in FP32. Weights start as N(0, 1/sizes[l]) drawn from a
+ * counter-based generator seeded by `seed`, biases at 0. max_batch bounds the batch of every
+ * later call. stream: the stream of every later call on this network (NULL: the legacy default
+ * stream). Allocates all workspace here.
+ * Errors: STST_ERR_ARG for bad sizes, STST_ERR_OOM.
+ */
+typedef struct stst_ws_s *stst_ws;
+int stst_ws_create(stst_ws *w, int n_layers, const int *sizes, int max_batch, unsigned long long seed,
+                   void *stream);
+int stst_ws_destroy(stst_ws w);
+/* number of parameters (host output) */
+int stst_ws_num_params(stst_ws w, long long *n);
+/* the effective parameters (weights as the BF16 copy widened to FP32, biases FP32) -> params
+ * (device, n floats); synchronizes. stst_ws_set_params: params (device) become the master copy,
+ * the BF16 copy is rounded from it, the Adam state is reset; synchronizes. */
+int stst_ws_get_params(stst_ws w, float *params);
+int stst_ws_set_params(stst_ws w, const float *params);
+/* Y (batch x sizes[n_layers], row-major) = s (.) network(X) + beta Y for X (batch x sizes[0], row-major),
+ * s the output scale (all ones unless set); beta = 0 does not read Y. 1 <= batch <= max_batch; batches of
+ * at most 8 rows run one warp per weight row. Stream-ordered, no synchronization. */
+int stst_ws_forward(stst_ws w, const float *X, int batch, float *Y, float beta);
+/* Per-output scale s used by stst_ws_forward only (training sees the unscaled outputs); scale: sizes[n_layers]
+ * floats (host or device), NULL removes it. Synchronizes. */
+int stst_ws_set_output_scale(stst_ws w, const float *scale);
+/*
+ * Loss L = (1/batch) sum_n w_n ||network(X_n) - T_n||^2 over the batch and its gradient with
+ * respect to the effective parameters (backpropagation through the BF16 weights).
+ * X: rows x sizes[0], T: rows x sizes[n_layers] (row-major), weight: per-row w_n (NULL: all 1).
+ * idx (device int array of length batch, may be NULL): the batch is rows idx[0..batch-1] of X, T
+ * and weight; NULL: the first batch rows. grad (device, n_params floats, may be NULL) receives the
+ * gradient; loss (host, may be NULL) receives L, and when given the call synchronizes.
+ */
+int stst_ws_grad(stst_ws w, const float *X, const float *T, const float *weight, const int *idx, int batch,
+                 float *grad, double *loss);
+/* The same loss and gradient, then one Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected,
+ * learning rate lr) on the master copy and a fresh BF16 copy. */
+int stst_ws_train_step(stst_ws w, const float *X, const float *T, const float *weight, const int *idx, int batch,
+                       float lr, double *loss);
+
+/*
+ * stst_pod_basis: rows of Q (K x m, row-major, FP32) = an orthonormal basis of the dominant row
+ * space of the snapshot matrix Y (n x m, row-major, FP64; each row one solution viewed as m reals,
+ * e.g. m = 2 N_dof for complex128 vectors). Randomized subspace iteration (Halko, Martinsson and
+ * Tropp 2011, Alg. 4.4): Q = orth(Omega^T Y), then power_its times Q = orth((Q Y^T) Y) with the
+ * intermediate orthonormalized too. orth = CholeskyQR2 with the Gram matrices accumulated in FP64.
+ * Omega (n x K, row-major, FP32) is the caller's Gaussian test matrix. Requires 1 <= K <= min(n, m),
+ * K <= 4096, m < 2^31, 0 <= power_its <= 8. Allocates stream-ordered temporaries ((K + 2 K) x max
+ * of m, n floats and (slices + 2) K^2 doubles) and synchronizes. STST_NOT_HPD when a Gram matrix
+ * is numerically singular (the snapshots span fewer than K directions).
+ */
+int stst_pod_basis(const double *Y, int n, long long m, const float *Omega, int K, int power_its, float *Q,
+                   void *stream);
+/* C (n x K, row-major, FP32) = Y Q^T: coordinates of the snapshot rows in the basis. Products in FP32,
+ * sums in FP32 over at most 32 terms and then in FP64. Stream-ordered, no allocation. */
+int stst_pod_project(const double *Y, int n, long long m, const float *Q, int K, float *C, void *stream);
+/* X (n x m, row-major, FP64) = alpha C Q + beta X (C: n x K row-major FP32; beta = 0 does not read X),
+ * accumulated like stst_pod_project. When phase (device, n doubles) is given, m must be even and row r
+ * (m/2 complex values) is then multiplied by e^{i phase[r]}. Stream-ordered, no allocation. */
+int stst_pod_expand(const float *Q, int K, long long m, const float *C, int n, float alpha, float beta,
+                    const double *phase, double *X, void *stream);
+
+/*
+ * stst_pcg_solve_guarded: stst_pcg_solve from the initial guess in x, after a device-side check:
+ * if ||rhs - A x|| >= ||rhs|| or is not finite, x is set to 0 first (the cold start of Sec. 6).
+ * used_warm (host, may be NULL) = 1 when the given guess was kept. Same outputs and errors as
+ * stst_pcg_solve.
+ */
+int stst_pcg_solve_guarded(stst_handle h, const double *rhs, double *x, double tol, int maxit, int *iters,
+                           double *relres, int *used_warm);
+
 #ifdef __cplusplus
 }
 #endif

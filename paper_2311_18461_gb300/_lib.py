@@ -53,6 +53,19 @@ def lib():
             "stst_batch_destroy": [P],
             "stst_plan_info": [P, IP, IP, DP],
             "stst_profile_read": [P, I, ctypes.c_char_p, I, ctypes.POINTER(LL), DP],
+            "stst_ws_create": [ctypes.POINTER(P), I, IP, I, ctypes.c_ulonglong, P],
+            "stst_ws_destroy": [P],
+            "stst_ws_num_params": [P, ctypes.POINTER(LL)],
+            "stst_ws_get_params": [P, P],
+            "stst_ws_set_params": [P, P],
+            "stst_ws_forward": [P, P, I, P, ctypes.c_float],
+            "stst_ws_set_output_scale": [P, P],
+            "stst_ws_grad": [P, P, P, P, P, I, P, DP],
+            "stst_ws_train_step": [P, P, P, P, P, I, ctypes.c_float, DP],
+            "stst_pod_basis": [P, I, LL, P, I, I, P, P],
+            "stst_pod_project": [P, I, LL, P, I, P, P],
+            "stst_pod_expand": [P, I, LL, P, I, ctypes.c_float, ctypes.c_float, P, P, P],
+            "stst_pcg_solve_guarded": [P, P, P, D, I, IP, DP, IP],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -220,6 +233,80 @@ def stst_profile_read(h):
     return out
 
 
+def stst_ws_create(sizes, max_batch, seed=0, stream=None):
+    """Network sizes[0] -> ... -> sizes[-1] (tanh between layers); returns the handle."""
+    n_layers = len(sizes) - 1
+    arr = (ctypes.c_int * len(sizes))(*[int(v) for v in sizes])
+    w = ctypes.c_void_p()
+    _chk(lib().stst_ws_create(ctypes.byref(w), n_layers, arr, int(max_batch), int(seed), _stream_ptr(stream)),
+         "stst_ws_create")
+    return w
+
+
+def stst_ws_destroy(w):
+    return _chk(lib().stst_ws_destroy(w), "stst_ws_destroy")
+
+
+def stst_ws_num_params(w):
+    n = ctypes.c_longlong()
+    _chk(lib().stst_ws_num_params(w, ctypes.byref(n)), "stst_ws_num_params")
+    return n.value
+
+
+def stst_ws_get_params(w, params):
+    return _chk(lib().stst_ws_get_params(w, _ptr(params)), "stst_ws_get_params")
+
+
+def stst_ws_set_params(w, params):
+    return _chk(lib().stst_ws_set_params(w, _ptr(params)), "stst_ws_set_params")
+
+
+def stst_ws_forward(w, X, batch, Y, beta=0.0):
+    return _chk(lib().stst_ws_forward(w, _ptr(X), int(batch), _ptr(Y), float(beta)), "stst_ws_forward")
+
+
+def stst_ws_set_output_scale(w, scale):
+    return _chk(lib().stst_ws_set_output_scale(w, _ptr(scale)), "stst_ws_set_output_scale")
+
+
+def stst_ws_grad(w, X, T, weight, idx, batch, grad, want_loss=True):
+    loss = ctypes.c_double()
+    _chk(lib().stst_ws_grad(w, _ptr(X), _ptr(T), _ptr(weight), _ptr(idx), int(batch), _ptr(grad),
+                            ctypes.byref(loss) if want_loss else None), "stst_ws_grad")
+    return loss.value if want_loss else None
+
+
+def stst_ws_train_step(w, X, T, weight, idx, batch, lr, want_loss=False):
+    loss = ctypes.c_double()
+    _chk(lib().stst_ws_train_step(w, _ptr(X), _ptr(T), _ptr(weight), _ptr(idx), int(batch), float(lr),
+                                  ctypes.byref(loss) if want_loss else None), "stst_ws_train_step")
+    return loss.value if want_loss else None
+
+
+def stst_pod_basis(Y, n, m, Omega, K, power_its, Q, stream=None):
+    return _chk(lib().stst_pod_basis(_ptr(Y), int(n), int(m), _ptr(Omega), int(K), int(power_its), _ptr(Q),
+                                     _stream_ptr(stream)), "stst_pod_basis")
+
+
+def stst_pod_project(Y, n, m, Q, K, C, stream=None):
+    return _chk(lib().stst_pod_project(_ptr(Y), int(n), int(m), _ptr(Q), int(K), _ptr(C), _stream_ptr(stream)),
+                "stst_pod_project")
+
+
+def stst_pod_expand(Q, K, m, C, n, alpha, beta, phase, X, stream=None):
+    return _chk(lib().stst_pod_expand(_ptr(Q), int(K), int(m), _ptr(C), int(n), float(alpha), float(beta),
+                                      _ptr(phase), _ptr(X), _stream_ptr(stream)), "stst_pod_expand")
+
+
+def stst_pcg_solve_guarded(h, rhs, x, tol, maxit):
+    it = ctypes.c_int()
+    rr = ctypes.c_double()
+    used = ctypes.c_int()
+    s = _chk(lib().stst_pcg_solve_guarded(h, _ptr(rhs), _ptr(x), float(tol), int(maxit), ctypes.byref(it),
+                                          ctypes.byref(rr), ctypes.byref(used)), "stst_pcg_solve_guarded")
+    return s, it.value, rr.value, used.value
+
+
 class Problem:
     """Owns a handle; convenience around the C calls (allocation of device vectors via torch)."""
 
@@ -282,6 +369,11 @@ class Problem:
         x = self.vec() if x is None else x
         s, it, rr = stst_pcg_solve(self.h, rhs, x, tol, maxit)
         return x, s, it, rr
+
+    def pcg_guarded(self, rhs, x, tol=1e-8, maxit=200):
+        """PCG from the guess in x (replaced by 0 on the device when it is worse than 0)."""
+        s, it, rr, used = stst_pcg_solve_guarded(self.h, rhs, x, tol, maxit)
+        return x, s, it, rr, used
 
     def ir(self, rhs, x=None, tol=1e-8, maxit=20, inner_tol=1e-4, inner_maxit=50):
         x = self.vec() if x is None else x
