@@ -10,7 +10,11 @@ initial datum (278,850 complex unknowns). Inputs are resident in HBM when
 the timed region starts; the L2 cache is flushed before every step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--config c2] [--prec fp64|fp32]
+                  [--config c2] [--prec fp64|fp32|bf16]
+
+--config c4 times the batched workload (128 problems, one graph launch per step); --config c5
+trains the learned warm start on method-generated solutions, then times solves of new problems
+from the network's iterate against cold-start PCG.
 
 One JSON line on rank 0. With --impl reference the CPU oracle is timed
 instead (a bounded sample: setup plus a few PCG iterations, extrapolated to
@@ -48,6 +52,10 @@ def parse():
     ap.add_argument("--solver", default="pcg", choices=["pcg", "ir"])
     ap.add_argument("--inner-tol", type=float, default=1e-4)
     ap.add_argument("--batch", type=int, default=128, help="number of problems of the c4 workload")
+    ap.add_argument("--train", type=int, default=10000, help="training solves of the c5 workload")
+    ap.add_argument("--stages", type=int, default=3, help="network stages of the c5 warm start")
+    ap.add_argument("--train-steps", type=int, default=6000, help="Adam steps per stage (c5)")
+    ap.add_argument("--basis", type=int, default=1024, help="basis size K of the c5 warm start")
     return ap.parse_args()
 
 
@@ -271,6 +279,155 @@ def run_batch(args):
     S.stst_batch_destroy(batch)
     for p in probs:
         p.close()
+
+
+def run_warmstart(args):
+    """Learned warm start (c5): train on method-generated solutions, then time solves of new problems
+    from the network's iterate (guarded PCG) against cold-start PCG on the same problems."""
+    import numpy as np
+    import torch
+    import paper_2311_18461_gb300 as S
+    from paper_2311_18461_gb300.warmstart import WarmStart
+    from inputs import CONFIGS, potential, wavepacket_factors, wavepacket_params
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    torch.cuda.set_device(local)
+    cfg = CONFIGS["c5"]
+    tol = cfg["tol"]
+    prec = {"fp64": S.STST_PREC_FP64, "fp32": S.STST_PREC_FP32, "bf16": S.STST_PREC_BF16}[args.prec]
+    prob = S.Problem(2, cfg["n_el"], [cfg["p"]] * 3, T=cfg["T"], nu=cfg["nu"], prec_mode=prec)
+    V = potential(cfg)
+    cols = [sample_1d(prob, term[l - 1], l) for term in V for l in (1, 2)]
+    prob.set_potential(torch.tensor(np.concatenate(cols), dtype=torch.float64, device="cuda"), len(V))
+    prob.build_fd()
+    g1, g2 = (prob.quad_points(l).cpu().numpy() for l in (1, 2))
+
+    def u0_qp(par):
+        f = wavepacket_factors(par)
+        U = np.asarray(f[1](g2)).reshape(-1, 1) * np.asarray(f[0](g1)).reshape(1, -1)
+        return torch.tensor(np.ascontiguousarray(U).ravel(), dtype=torch.complex128, device="cuda")
+
+    seed = cfg["u0"][1]
+    rng = np.random.default_rng(seed)
+    train = [wavepacket_params(rng, 2) for _ in range(args.train)]
+    K = args.basis
+    ws = WarmStart(prob, K, K, hidden=(), stages=args.stages, max_batch=256, seed=seed)
+    t0 = time.time()
+    its_train = ws.collect([lambda par=par: u0_qp(par) for par in train], tol=tol)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    ws.fit(power_its=1, seed=seed + 1)
+    torch.cuda.synchronize()
+    t2 = time.time()
+    ws.train(args.train_steps, batch=256, lr0=3e-3, lr1=3e-6, seed=seed + 2)
+    t3 = time.time()
+    # new problems (a different seed), inputs resident in HBM
+    trng = np.random.default_rng(seed + 1000)
+    n_test = max(args.steps, 1) + max(args.warmup, 3)
+    tests = []
+    for _ in range(n_test):
+        f, c0 = prob.rhs(u0_qp=u0_qp(wavepacket_params(trng, 2)), want_c0=True)
+        tests.append((f, c0))
+    torch.cuda.synchronize()
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        a.record()
+        r = fn()
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b), r
+
+    warm_ms, cold_ms, it_w, it_c, e0s, diffs, used = [], [], [], [], [], [], []
+    sampler = ClockSampler(local)
+    for i, (f, c0) in enumerate(tests):
+        if i == max(args.warmup, 3):
+            sampler.start()
+
+        def cold():
+            x, s, it, rr = prob.pcg(f, tol=tol)
+            return x, s, it
+
+        def warm():
+            x0 = ws.predict(c0)[0]
+            x, s, it, rr, u = ws.solve(f, x0, tol=tol)
+            return x, s, it, u
+
+        tc, (xc, sc, itc) = timed(cold)
+        x0 = ws.predict(c0)[0].clone()
+        e0 = (torch.linalg.vector_norm(x0 - xc) / torch.linalg.vector_norm(xc)).item()
+        tw, (xw, sw, itw, u) = timed(warm)
+        if sc != 0 or sw != 0:
+            raise RuntimeError(f"solve failed: cold {sc}, warm {sw}")
+        if i >= max(args.warmup, 3):
+            warm_ms.append(tw)
+            cold_ms.append(tc)
+            it_w.append(itw)
+            it_c.append(itc)
+            e0s.append(e0)
+            diffs.append((torch.linalg.vector_norm(xw - xc) / torch.linalg.vector_norm(xc)).item())
+            used.append(u)
+    clocks = sampler.stop()
+    # end to end through the public calls: rhs and c0 from pinned host memory, solution back, every step
+    f_h = [f.cpu().pin_memory() for f, _ in tests[:args.steps]]
+    c_h = [c.cpu().pin_memory() for _, c in tests[:args.steps]]
+    x_h = torch.empty_like(f_h[0]).pin_memory()
+    fd, cd = prob.vec(), torch.empty_like(tests[0][1])
+    e2e = []
+    for fh, ch in zip(f_h, c_h):
+        def e2e_step():
+            fd.copy_(fh, non_blocking=True)
+            cd.copy_(ch, non_blocking=True)
+            x0 = ws.predict(cd)[0]
+            x, s, it, rr, u = ws.solve(fd, x0, tol=tol)
+            x_h.copy_(x, non_blocking=True)
+            return s
+        e2e.append(timed(e2e_step)[0])
+    # the expansion kernel alone (reads the basis once: HBM-bound)
+    Cq = torch.zeros((1, K), dtype=torch.float32, device="cuda")
+    Xq = torch.empty((1, ws.m), dtype=torch.float64, device="cuda")
+    exp_ms = []
+    for _ in range(5):
+        exp_ms.append(timed(lambda: S.stst_pod_expand(ws.Q_out, K, ws.m, Cq, 1, 1.0, 0.0, None, Xq))[0])
+    exp_ms = statistics.median(exp_ms)
+    peaks, src = load_peaks()
+    hbm = float(peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"]))
+    bytes_exp = 4.0 * K * ws.m + 8.0 * ws.m
+    ms = statistics.mean(warm_ms)
+    out = {
+        "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": len(warm_ms),
+        "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f64+f32", "bf16": "f64+f32+bf16"}[args.prec] + "+bf16 net",
+        "data": "synthetic",
+        "config": {"workload": f"c5: 2D+t p=3 48^2 x 48 elements ({prob.n_dof} unknowns), harmonic V in [0,10], "
+                               f"wavepacket u0 (centre, width, momentum, phase drawn), tol {tol:g}",
+                   "step": "one new problem: network inference (project c0, forward of every stage, expand) + "
+                           "guarded PCG from the predicted iterate",
+                   "model": f"{args.stages} linear stages {K}->{K}, {ws.n_params} parameters, BF16 weights, "
+                            f"FP32 accumulation", "training_solves": args.train,
+                   "l2": "flushed (512 MB write) before each step", "parallelism": f"replicas x{world}"},
+        "warm": {"ms": ms, "pcg_iterations_mean": statistics.mean(it_w), "x0_rel_err_median": statistics.median(e0s),
+                 "final_rel_diff_vs_cold_max": max(diffs), "warm_start_kept": int(sum(used))},
+        "cold": {"ms": statistics.mean(cold_ms), "pcg_iterations_mean": statistics.mean(it_c)},
+        "training": {"collect_s": t1 - t0, "pcg_iterations_mean": statistics.mean(its_train), "basis_s": t2 - t1,
+                     "train_s": t3 - t2, "adam_steps_per_stage": args.train_steps},
+        "roofline": {"kernel": "k_pod_expand_rows", "bound": "hbm", "achieved": bytes_exp / (exp_ms * 1e-3) / 1e9,
+                     "peak": hbm, "unit": "GB/s", "frac": bytes_exp / (exp_ms * 1e-3) / 1e9 / hbm,
+                     "peak_source": src, "traffic": None},
+        "clocks": clocks,
+        "e2e": {"value": statistics.mean(e2e) / 1e3, "unit": "s", "h2d_bytes_per_step": 16 * (prob.n_dof + prob.N_s),
+                "d2h_bytes_per_step": 16 * prob.n_dof},
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ws.close()
+    prob.close()
 
 
 def run_ours(args):
@@ -541,6 +698,8 @@ def main():
         build.build()
         if args.config == "c4":
             run_batch(args)
+        elif args.config == "c5":
+            run_warmstart(args)
         else:
             run_ours(args)
 
