@@ -117,26 +117,25 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def source_hash():
+def source_hash(files):
+    """Hash of the CUDA sources a kernel is built from (traffic figures are void once they change)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2311_18461_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, name), "rb").read())
+    for name in sorted(files):
+        h.update(open(os.path.join(csrc, name), "rb").read())
     return h.hexdigest()[:16]
 
 
 def traffic_for(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if taken on the current sources."""
+    """DRAM bytes per launch from the committed ncu summary, if taken on the kernel's current sources."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
-        rec = json.load(open(path))
+        rec = json.load(open(path)).get("kernels", {}).get(kernel)
+        if not rec or rec.get("source_hash") != source_hash(rec["sources"]):
+            return None
+        return rec.get("dram_bytes_per_launch")
     except Exception:
         return None
-    if rec.get("source_hash") != source_hash():
-        return None
-    v = rec.get("kernels", {}).get(kernel)
-    return v.get("dram_bytes_per_launch") if v else None
 
 
 def workload(cfg_name):

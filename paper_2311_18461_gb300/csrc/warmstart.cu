@@ -501,8 +501,8 @@ __global__ void __launch_bounds__(256) k_pod_project_rows(const double *__restri
   }
 }
 
-// X (n x m) = alpha C (n x K) Q (K x m) + beta X: one thread per 4 columns (float4 loads of Q, 8 basis
-// rows in flight), C in shared memory; FP32 products summed in FP32 over 32 basis rows, then in FP64.
+// X (n x m) = alpha C (n x K) Q (K x m) + beta X: one thread per 4 columns (float4 loads of Q, 8 or 16
+// basis rows in flight), C in shared memory; FP32 products summed in FP32 over 32 basis rows, then in FP64.
 template <int NR>
 __global__ void __launch_bounds__(256) k_pod_expand_rows(const float *__restrict__ Q, int K, long long m,
                                                          const float *__restrict__ C, int n, float alpha, float beta,
@@ -526,13 +526,16 @@ __global__ void __launch_bounds__(256) k_pod_expand_rows(const float *__restrict
     for (int r = 0; r < NR; ++r)
 #pragma unroll
       for (int i = 0; i < 4; ++i) part[r][i] = 0.f;
+    // UNR basis rows in flight per thread: the grid has only m/1024 CTAs, so the loads of one thread
+    // must cover the HBM latency (16 rows of 16 bytes for one or two right-hand sides)
+    constexpr int UNR = NR <= 2 ? 16 : 8;
     int k = k0;
-    for (; k + 8 <= k1; k += 8) {
-      float4 qv[8];
+    for (; k + UNR <= k1; k += UNR) {
+      float4 qv[UNR];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) qv[u] = __ldg(q + (long long)(k + u) * step);
+      for (int u = 0; u < UNR; ++u) qv[u] = __ldg(q + (long long)(k + u) * step);
 #pragma unroll
-      for (int u = 0; u < 8; ++u)
+      for (int u = 0; u < UNR; ++u)
 #pragma unroll
         for (int r = 0; r < NR; ++r)
           if (r < n) {
