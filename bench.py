@@ -606,6 +606,8 @@ def run_ours(args):
         "apply_prec_ms": t_prec,
         "apply_sys_ms": t_sys,
         "mat_vec_plan": {"passes": n_passes, "band_apps_per_dof": band_apps, "flops_per_dof": flops_dof},
+        "mode_product_tiles": [dict(zip(("cols_per_cta", "rows_per_cta", "tuned_us"), S.stst_tile_info(prob.h, l)))
+                               for l in range(1, cfg["d"] + 1)],
         "kernels_ms_per_solve": {k: round(v[1], 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
         "kernel_launches_per_solve": {k: v[0] for k, v in prof.items()},
         "gpu_launches": int(sum(v[0] for v in prof.values())) * args.steps,

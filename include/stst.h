@@ -210,6 +210,22 @@ int stst_batch_solve(stst_batch b, double tol, int maxit, int *iters, double *re
 int stst_batch_destroy(stst_batch b);
 
 /*
+ * stst_set_autotune: mode 1 (the default) makes stst_build_fd and stst_batch_create time the candidate
+ * tiles of the SIMT mode products (8 cpt columns with cpt in {2, 4}, 32 rpt output rows with rpt in 1..4,
+ * per CTA) once per problem shape and precision, keeping the fastest (cached for the process); mode 0 uses
+ * the fixed default (32 columns, all rows of the mode up to 128 per CTA); mode 10 rpt + cpt forces that
+ * tile where it fits in shared memory. Results do not depend on the tile (each output is summed in the
+ * same order); the grouping of the PCG dot-product partials does. Process-wide, for handles whose
+ * preconditioner is built afterwards. STST_ERR_ARG for other modes.
+ * stst_tile_info: the tile of direction dir (1..d) of the handle: columns and output rows per CTA
+ * (host, may be NULL) and its measured microseconds per launch (0 when not measured).
+ */
+int stst_set_autotune(int mode);
+/* Name and description of the CUDA error behind the calling thread's last STST_ERR_CUDA (static string). */
+const char *stst_last_cuda_error(void);
+int stst_tile_info(stst_handle h, int dir, int *cols_per_cta, int *rows_per_cta, double *us);
+
+/*
  * stst_profile: enable (1) or disable (0) per-kernel timing for the handle's
  * calls. Enabling clears previous records. While enabled every kernel launch
  * of a call is bracketed by CUDA events on the handle's stream and the call

@@ -18,7 +18,10 @@ STATUS = {0: "OK", 1: "NOT_CONVERGED", 2: "BREAKDOWN", 3: "NOT_HPD", 4: "TIMEOUT
 class StstError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
-        super().__init__(f"{where}: {STATUS.get(status, status)} ({_strerror(status)})")
+        detail = _strerror(status)
+        if status == -4:
+            detail += "; " + stst_last_cuda_error()
+        super().__init__(f"{where}: {STATUS.get(status, status)} ({detail})")
 
 
 _lib = None
@@ -53,6 +56,8 @@ def lib():
             "stst_batch_destroy": [P],
             "stst_plan_info": [P, IP, IP, DP],
             "stst_profile_read": [P, I, ctypes.c_char_p, I, ctypes.POINTER(LL), DP],
+            "stst_set_autotune": [I],
+            "stst_tile_info": [P, I, IP, IP, DP],
             "stst_ws_create": [ctypes.POINTER(P), I, IP, I, ctypes.c_ulonglong, P],
             "stst_ws_destroy": [P],
             "stst_ws_num_params": [P, ctypes.POINTER(LL)],
@@ -73,6 +78,8 @@ def lib():
             f.restype = I
         L.stst_strerror.argtypes = [I]
         L.stst_strerror.restype = ctypes.c_char_p
+        L.stst_last_cuda_error.argtypes = []
+        L.stst_last_cuda_error.restype = ctypes.c_char_p
         _lib = L
     return _lib
 
@@ -86,6 +93,13 @@ def _strerror(status):
 
 def stst_strerror(status):
     return lib().stst_strerror(status).decode()
+
+
+def stst_last_cuda_error():
+    try:
+        return lib().stst_last_cuda_error().decode()
+    except Exception:
+        return ""
 
 
 def _ptr(t):
@@ -231,6 +245,18 @@ def stst_profile_read(h):
         out[name.value.decode()] = (cnt.value, ms.value)
         idx += 1
     return out
+
+
+def stst_set_autotune(mode):
+    return _chk(lib().stst_set_autotune(int(mode)), "stst_set_autotune")
+
+
+def stst_tile_info(h, dir):
+    c = ctypes.c_int()
+    r = ctypes.c_int()
+    us = ctypes.c_double()
+    _chk(lib().stst_tile_info(h, int(dir), ctypes.byref(c), ctypes.byref(r), ctypes.byref(us)), "stst_tile_info")
+    return c.value, r.value, us.value
 
 
 def stst_ws_create(sizes, max_batch, seed=0, stream=None):

@@ -6,6 +6,9 @@
 //  * k_timesolve: the N_s independent banded Hermitian solves H_i x_i = y_i (Algorithm 1, step 3,
 //    Eq. independent_problems) with precomputed Cholesky factors, one thread per system.
 #include "common.cuh"
+#include <map>
+#include <mutex>
+#include <tuple>
 #include "async.cuh"
 
 template <typename R> struct C2;
@@ -236,58 +239,69 @@ int run_plan(const Plan &plan, const void *x, void *y, int precision, int epi, c
 // 256 threads = 8 column groups x 32 row groups; each thread keeps RPT rows x 4 columns of complex
 // accumulators in registers (rows rg, rg+32, ..., columns 4 cg .. 4 cg + 3).
 // ------------------------------------------------------------------------------------------------
-template <typename R, typename TI, typename TO, int RPT>
+// Mode product with U (step 2: y_j = sum_i U[i][j] x_i) or U^T (step 4), on the columns of the
+// time-fastest tensor. Tile: CW = 8 CPT columns and RB = 32 RPT output rows per CTA (grid.y covers the
+// rows), U's slice and the x tile staged in shared memory with cp.async; a thread holds CPT columns x
+// RPT rows of accumulators. Rows past n are zero in shared memory. Every output is summed over i in
+// the same order whatever the tile, so all tiles give bitwise equal results.
+template <typename R, typename TI, typename TO, int RPT, int CPT>
 __global__ void __launch_bounds__(256) k_modeprod(const TI *__restrict__ X, TO *__restrict__ Y, const R *__restrict__ U,
                                                   int n, long long inner, long long ncols, int backward,
                                                   const TO *__restrict__ dotvec, double *dot_partials,
                                                   const int *done) {
   using T = typename C2<R>::T;
-  constexpr int CW = 32;
+  constexpr int CW = 8 * CPT, RB = 32 * RPT;
   if (done && *done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R *sU = (R *)smem_raw;                                            // n*n
-  T *sX = (T *)(smem_raw + ((n * n * sizeof(R) + 15) / 16) * 16);  // n * CW
+  R *sU = (R *)smem_raw;                                             // n x RB
+  T *sX = (T *)(smem_raw + ((n * RB * sizeof(R) + 15) / 16) * 16);  // n x CW
   __shared__ double sh[32];
   const long long col0 = (long long)blockIdx.x * CW;
-  // U -> shared: sU[i*n + j] = coefficient of x_i in y_j (U for step 2, U^T for step 4). Reads of U
-  // are coalesced; the backward case writes the transpose into shared memory. (i, j) advance
-  // incrementally, so no division per element.
-  {
-    const int nn = n * n;
-    int e = threadIdx.x, i = e / n, j = e - (e / n) * n;
-    const int di = 256 / n, dj = 256 - (256 / n) * n;
-    for (; e < nn; e += 256) {
-      cp_async<sizeof(R)>(backward ? &sU[j * n + i] : &sU[e], &U[e]);
+  const int j0 = blockIdx.y * RB;
+  // U slice: sU[i*RB + jj] = coefficient of x_i in y_{j0+jj}; source reads are coalesced either way
+  if (!backward) {
+    for (int e = threadIdx.x; e < n * RB; e += 256) {  // (i, jj), jj fastest: source U[i][j0 + jj]
+      const int i = e / RB, jj = e - i * RB;
+      if (j0 + jj < n) cp_async<sizeof(R)>(&sU[e], &U[(long long)i * n + j0 + jj]);
+      else sU[e] = (R)0;
+    }
+  } else {
+    int e = threadIdx.x, jj = e / n, i = e - (e / n) * n;  // (jj, i), i fastest: source U[j0 + jj][i]
+    const int dj = 256 / n, di = 256 - (256 / n) * n;
+    for (; e < n * RB; e += 256) {
+      if (j0 + jj < n) cp_async<sizeof(R)>(&sU[i * RB + jj], &U[(long long)(j0 + jj) * n + i]);
+      else sU[i * RB + jj] = (R)0;
       i += di;
-      j += dj;
-      if (j >= n) { j -= n; ++i; }
+      jj += dj;
+      if (i >= n) { i -= n; ++jj; }
     }
   }
-  // x tile: this thread's column cc = tid % 32 is fixed, its rows are tid / 32 + 8k
+  // x tile: this thread's column cc = tid % CW is fixed, its rows are tid / CW + (256 / CW) k
   {
-    const int cc = threadIdx.x & 31;
+    constexpr int RSTEP = 256 / CW;
+    const int cc = threadIdx.x % CW;
     const long long col = col0 + cc;
     const bool in = col < ncols;
     const long long o = in ? col / inner : 0, c = in ? col % inner : 0;
     const TI *src = X + o * n * inner + c;
     if constexpr (sizeof(TI) == sizeof(T)) {
-      for (int i = threadIdx.x >> 5; i < n; i += 8) {
+      for (int i = threadIdx.x / CW; i < n; i += RSTEP) {
         if (in) cp_async<sizeof(T)>(&sX[i * CW + cc], src + (long long)i * inner);
         else { T z; z.x = 0; z.y = 0; sX[i * CW + cc] = z; }
       }
     } else {
       // FP64 input converted to FP32: eight loads in flight per batch
-      for (int i0 = threadIdx.x >> 5; i0 < n; i0 += 64) {
+      for (int i0 = threadIdx.x / CW; i0 < n; i0 += 8 * RSTEP) {
         TI v[8];
 #pragma unroll
         for (int b = 0; b < 8; ++b) {
-          const int i = i0 + 8 * b;
+          const int i = i0 + RSTEP * b;
           if (in && i < n) v[b] = src[(long long)i * inner];
           else { v[b].x = 0; v[b].y = 0; }
         }
 #pragma unroll
         for (int b = 0; b < 8; ++b) {
-          const int i = i0 + 8 * b;
+          const int i = i0 + RSTEP * b;
           if (i < n) {
             T t;
             t.x = (R)v[b].x;
@@ -302,28 +316,29 @@ __global__ void __launch_bounds__(256) k_modeprod(const TI *__restrict__ X, TO *
   }
   __syncthreads();
   const int cg = threadIdx.x & 7, rg = threadIdx.x >> 3;
-  R ax[RPT][4], ay[RPT][4];
+  R ax[RPT][CPT], ay[RPT][CPT];
 #pragma unroll
   for (int r = 0; r < RPT; ++r)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) { ax[r][c] = 0; ay[r][c] = 0; }
+    for (int c = 0; c < CPT; ++c) { ax[r][c] = 0; ay[r][c] = 0; }
   for (int i = 0; i < n; ++i) {
-    T xv[4];
-    if constexpr (sizeof(T) == 8) {  // float2: two 16-byte reads
-      const float4 *q = reinterpret_cast<const float4 *>(&sX[i * CW + cg * 4]);
-      float4 a = q[0], b = q[1];
-      xv[0].x = a.x; xv[0].y = a.y; xv[1].x = a.z; xv[1].y = a.w;
-      xv[2].x = b.x; xv[2].y = b.y; xv[3].x = b.z; xv[3].y = b.w;
+    T xv[CPT];
+    if constexpr (sizeof(T) == 8) {  // float2 columns: 16-byte reads
+      const float4 *q = reinterpret_cast<const float4 *>(&sX[i * CW + cg * CPT]);
+#pragma unroll
+      for (int h2 = 0; h2 < CPT / 2; ++h2) {
+        const float4 a = q[h2];
+        xv[2 * h2].x = a.x; xv[2 * h2].y = a.y; xv[2 * h2 + 1].x = a.z; xv[2 * h2 + 1].y = a.w;
+      }
     } else {
 #pragma unroll
-      for (int c = 0; c < 4; ++c) xv[c] = sX[i * CW + cg * 4 + c];
+      for (int c = 0; c < CPT; ++c) xv[c] = sX[i * CW + cg * CPT + c];
     }
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
-      const int j = rg + 32 * r;
-      const R u = (j < n) ? sU[i * n + j] : (R)0;
+      const R u = sU[i * RB + rg + 32 * r];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
+      for (int c = 0; c < CPT; ++c) {
         ax[r][c] += u * xv[c].x;
         ay[r][c] += u * xv[c].y;
       }
@@ -331,13 +346,13 @@ __global__ void __launch_bounds__(256) k_modeprod(const TI *__restrict__ X, TO *
   }
   double dacc = 0.0;
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    const long long col = col0 + cg * 4 + c;
+  for (int c = 0; c < CPT; ++c) {
+    const long long col = col0 + cg * CPT + c;
     if (col >= ncols) continue;
     const long long o = col / inner, cin = col % inner;
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
-      const int j = rg + 32 * r;
+      const int j = j0 + rg + 32 * r;
       if (j < n) {
         const long long idx = (o * n + j) * inner + cin;
         TO res;
@@ -353,36 +368,160 @@ __global__ void __launch_bounds__(256) k_modeprod(const TI *__restrict__ X, TO *
   }
   if (dot_partials) {
     double s = block_sum(dacc, sh);
-    if (threadIdx.x == 0) dot_partials[blockIdx.x] = s;
+    if (threadIdx.x == 0) dot_partials[blockIdx.y * gridDim.x + blockIdx.x] = s;
   }
+}
+
+static size_t modeprod_smem(int n, MpCfg c, size_t rsize) {
+  return ((n * 32 * c.rpt * rsize + 15) / 16) * 16 + (size_t)n * 8 * c.cpt * 2 * rsize;
+}
+
+static dim3 modeprod_grid(int n, long long ncols, MpCfg c) {
+  return dim3((unsigned)grid_for(ncols, 8 * c.cpt), (unsigned)((n + 32 * c.rpt - 1) / (32 * c.rpt)));
 }
 
 template <typename R, typename TI, typename TO>
 static int launch_modeprod(const TI *X, TO *Y, const R *U, int n, long long inner, long long outer, int backward,
-                           const TO *dotvec, double *dot_partials, const int *done, cudaStream_t s,
-                           int *grid_out) {
-  long long ncols = inner * outer;
-  constexpr int CW = 32;
-  int grid = grid_for(ncols, CW);
-  if (dot_partials && grid > STST_MAXPART) return STST_ERR_ARG;
+                           const TO *dotvec, double *dot_partials, const int *done, cudaStream_t s, MpCfg cfg) {
+  const long long ncols = inner * outer;
+  const dim3 grid = modeprod_grid(n, ncols, cfg);
+  if (dot_partials && (long long)grid.x * grid.y > STST_MAXPART) return STST_ERR_ARG;
+  if (grid.x > 0x7fffffffu || grid.y > 65535u) return STST_ERR_ARG;
   STST_PROF(sizeof(R) == 8 ? "modeprod_f64" : "modeprod_f32", s);
-  size_t sm = ((n * n * sizeof(R) + 15) / 16) * 16 + (size_t)n * CW * sizeof(typename C2<R>::T);
-  const int rpt = (n + 31) / 32;
-  switch (rpt) {
-#define CASE(RR)                                                                                              \
-  case RR:                                                                                                    \
-    if (sm > 48 * 1024)                                                                                       \
-      STST_CUDA(cudaFuncSetAttribute(k_modeprod<R, TI, TO, RR>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                     (int)sm));                                                               \
-    k_modeprod<R, TI, TO, RR><<<grid, 256, sm, s>>>(X, Y, U, n, inner, ncols, backward, dotvec, dot_partials, \
-                                                     done);                                                   \
-    break;
-    CASE(1) CASE(2) CASE(3) CASE(4)
+  const size_t sm = modeprod_smem(n, cfg, sizeof(R));
+  auto go = [&](auto kern) -> int {
+    STST_TRY(ensure_dyn_smem((const void *)kern, sm));
+    kern<<<grid, 256, sm, s>>>(X, Y, U, n, inner, ncols, backward, dotvec, dot_partials, done);
+    return STST_OK;
+  };
+  int st = STST_ERR_ARG;
+  const int key = cfg.rpt * 10 + cfg.cpt;
+  switch (key) {
+#define CASE(RR, CC) case RR * 10 + CC: st = go(k_modeprod<R, TI, TO, RR, CC>); break;
+    CASE(1, 2) CASE(1, 4) CASE(2, 2) CASE(2, 4) CASE(3, 2) CASE(3, 4) CASE(4, 2) CASE(4, 4)
 #undef CASE
-    default: return STST_ERR_ARG;
+    default: break;
   }
+  STST_TRY(st);
   STST_CUDA(cudaGetLastError());
-  if (grid_out) *grid_out = grid;
+  return STST_OK;
+}
+
+// ---- tile autotuner for the SIMT mode products --------------------------------------------------
+// Candidates: 16 or 32 columns, 32..128 output rows per CTA. Each is timed with CUDA events (two warm
+// launches, five timed) on the handle's work vectors; the fastest per (precision, n, inner, outer) is
+// cached for the process. Runs outside graph capture (stst_build_fd, stst_batch_create).
+MpCfg modeprod_default(int n) {
+  MpCfg c;
+  c.cpt = 4;
+  c.rpt = (n + 31) / 32;
+  if (c.rpt > 4) c.rpt = 4;
+  if (c.rpt < 1) c.rpt = 1;
+  return c;
+}
+
+int g_tune_enabled = 1;
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, long long, long long>, std::pair<MpCfg, float>> g_tune_cache;
+
+template <typename R>
+static int tune_one(stst_problem *h, int l, long long inner, long long outer, MpCfg *best, float *best_us) {
+  using T = typename C2<R>::T;
+  const int n = h->dir[l].n;
+  const auto key = std::make_tuple((int)sizeof(R), n, inner, outer);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      *best = it->second.first;
+      *best_us = it->second.second;
+      return STST_OK;
+    }
+  }
+  cudaStream_t st = h->stream;
+  const R *U = sizeof(R) == 8 ? (const R *)h->U[l] : (const R *)h->U32[l];
+  const T *X = (const T *)h->w_t1;
+  T *Y = (T *)h->w_t2;
+  cudaEvent_t e0, e1;
+  STST_CUDA(cudaEventCreate(&e0));
+  STST_CUDA(cudaEventCreate(&e1));
+  MpCfg cand = modeprod_default(n);
+  float cand_us = 1e30f;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  int status = STST_OK;
+  const int maxr = (n + 31) / 32;
+  for (int rpt = 1; rpt <= 4 && rpt <= maxr && status == STST_OK; ++rpt)
+    for (int cpt = 2; cpt <= 4 && status == STST_OK; cpt += 2) {
+      MpCfg c;
+      c.cpt = cpt;
+      c.rpt = rpt;
+      if (modeprod_smem(n, c, sizeof(R)) > (size_t)optin) continue;
+      for (int w = 0; w < 2 && status == STST_OK; ++w)
+        status = launch_modeprod<R, T, T>(X, Y, U, n, inner, outer, 0, nullptr, nullptr, nullptr, st, c);
+      if (status != STST_OK) break;
+      cudaEventRecord(e0, st);
+      for (int w = 0; w < 5 && status == STST_OK; ++w)
+        status = launch_modeprod<R, T, T>(X, Y, U, n, inner, outer, 0, nullptr, nullptr, nullptr, st, c);
+      cudaEventRecord(e1, st);
+      const cudaError_t es = cudaEventSynchronize(e1);
+      if (es != cudaSuccess) {
+        stst_last_cuda = es;
+        status = STST_ERR_CUDA;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      const float us = ms * 1000.f / 5.f;
+      if (status == STST_OK && us < cand_us) {
+        cand_us = us;
+        cand = c;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  STST_TRY(status);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = std::make_pair(cand, cand_us);
+  }
+  *best = cand;
+  *best_us = cand_us;
+  return STST_OK;
+}
+
+int tune_modeprod(stst_problem *h) {
+  if (h->tuned) return STST_OK;
+  if (h->prec_mode == STST_PREC_BF16 || g_tune_enabled != 1) {
+    for (int l = 1; l <= h->d; ++l) {
+      h->mp_cfg[l] = modeprod_default(h->dir[l].n);
+      const int rpt = g_tune_enabled / 10, cpt = g_tune_enabled % 10;  // a forced tile (10 rpt + cpt)
+      if (rpt >= 1 && rpt <= 4 && (cpt == 2 || cpt == 4)) {
+        MpCfg c;
+        c.cpt = cpt;
+        c.rpt = rpt;
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        const size_t rs = h->prec_mode == STST_PREC_FP64 ? sizeof(double) : sizeof(float);
+        if (modeprod_smem(h->dir[l].n, c, rs) <= (size_t)optin) h->mp_cfg[l] = c;
+      }
+    }
+    h->tuned = 1;
+    return STST_OK;
+  }
+  long long acc = h->n_t();
+  for (int l = 1; l <= h->d; ++l) {
+    const long long inner = acc, outer = h->N_dof / (acc * h->dir[l].n);
+    acc *= h->dir[l].n;
+    MpCfg c;
+    float us = 0.f;
+    if (h->prec_mode == STST_PREC_FP64) STST_TRY(tune_one<double>(h, l, inner, outer, &c, &us));
+    else STST_TRY(tune_one<float>(h, l, inner, outer, &c, &us));
+    h->mp_cfg[l] = c;
+    h->mp_us[l] = us;
+  }
+  h->tuned = 1;
   return STST_OK;
 }
 
@@ -532,8 +671,7 @@ static int launch_timesolve(void *Y, const void *G, const R *D, int nt, long lon
   switch (P) {
 #define CASE(PP)                                                                                          \
   case PP:                                                                                                \
-    if (sm > 48 * 1024) STST_CUDA(cudaFuncSetAttribute(k_timesolve<R, PP>,                                \
-                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm)); \
+    STST_TRY(ensure_dyn_smem((const void *)k_timesolve<R, PP>, sm));                                          \
     k_timesolve<R, PP><<<grid, 32, sm, s>>>(Y, G, D, nt, Ns, TC, done);                                   \
     break;
     CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
@@ -575,17 +713,16 @@ int fd_apply(stst_problem *h, const double *r, double *s, int precision, const v
     for (int l = 1; l <= d; ++l) {
       double2 *dst = bufs[cur];
       STST_TRY((launch_modeprod<double, double2, double2>(src, dst, h->U[l], h->dir[l].n, inner[l], outer[l], 0,
-                                                           nullptr, nullptr, done, st, nullptr)));
+                                                           nullptr, nullptr, done, st, h->mp_cfg[l])));
       src = dst;
       cur ^= 1;
     }
     STST_TRY(launch_timesolve<double>((void *)src, h->Hg, h->Hd, nt, Ns, h->dir[0].p, done, st));
     for (int l = d; l >= 1; --l) {
       double2 *dst = (l == 1) ? (double2 *)s : bufs[cur];
-      int grid = 0;
       STST_TRY((launch_modeprod<double, double2, double2>(src, dst, h->U[l], h->dir[l].n, inner[l], outer[l], 1,
                                                            l == 1 ? (const double2 *)dotvec : nullptr,
-                                                           l == 1 ? dot_partials : nullptr, done, st, &grid)));
+                                                           l == 1 ? dot_partials : nullptr, done, st, h->mp_cfg[l])));
       src = dst;
       cur ^= 1;
     }
@@ -647,14 +784,14 @@ int fd_apply(stst_problem *h, const double *r, double *s, int precision, const v
     if (l == 1) {
       if (in32) {
         STST_TRY((launch_modeprod<float, float2, float2>((const float2 *)in32, dst, h->U32[l], h->dir[l].n, inner[l],
-                                                         outer[l], 0, nullptr, nullptr, done, st, nullptr)));
+                                                         outer[l], 0, nullptr, nullptr, done, st, h->mp_cfg[l])));
       } else {
         STST_TRY((launch_modeprod<float, double2, float2>((const double2 *)r, dst, h->U32[l], h->dir[l].n, inner[l],
-                                                          outer[l], 0, nullptr, nullptr, done, st, nullptr)));
+                                                          outer[l], 0, nullptr, nullptr, done, st, h->mp_cfg[l])));
       }
     } else {
       STST_TRY((launch_modeprod<float, float2, float2>(src32, dst, h->U32[l], h->dir[l].n, inner[l], outer[l], 0,
-                                                       nullptr, nullptr, done, st, nullptr)));
+                                                       nullptr, nullptr, done, st, h->mp_cfg[l])));
     }
     src32 = dst;
     cur ^= 1;
@@ -665,16 +802,16 @@ int fd_apply(stst_problem *h, const double *r, double *s, int precision, const v
       if (out32) {
         STST_TRY((launch_modeprod<float, float2, float2>(src32, (float2 *)out32, h->U32[l], h->dir[l].n, inner[l],
                                                          outer[l], 1, (const float2 *)dotvec, dot_partials, done, st,
-                                                         nullptr)));
+                                                         h->mp_cfg[l])));
       } else {
         STST_TRY((launch_modeprod<float, float2, double2>(src32, (double2 *)s, h->U32[l], h->dir[l].n, inner[l],
                                                           outer[l], 1, (const double2 *)dotvec, dot_partials, done,
-                                                          st, nullptr)));
+                                                          st, h->mp_cfg[l])));
       }
     } else {
       float2 *dst = bufs[cur];
       STST_TRY((launch_modeprod<float, float2, float2>(src32, dst, h->U32[l], h->dir[l].n, inner[l], outer[l], 1,
-                                                       nullptr, nullptr, done, st, nullptr)));
+                                                       nullptr, nullptr, done, st, h->mp_cfg[l])));
       src32 = dst;
       cur ^= 1;
     }
@@ -686,5 +823,6 @@ int fd_apply(stst_problem *h, const double *r, double *s, int precision, const v
 int fd_partials_count(stst_problem *h) {
   long long ncols = h->N_dof / h->dir[1].n;
   if (h->prec_mode == STST_PREC_BF16) return tc_partials_count(ncols);
-  return grid_for(ncols, 32);
+  const dim3 g = modeprod_grid(h->dir[1].n, ncols, h->mp_cfg[1]);
+  return (int)(g.x * g.y);
 }

@@ -3,11 +3,25 @@
 // Eq. time_mat / Eq. space_mat (optionally weighted), basis tables at the quadrature
 // points, and the banded Cholesky factor of the reduced mass matrix.
 #include "common.cuh"
+#include <mutex>
+#include <unordered_map>
 #include <cmath>
 
 thread_local cudaError_t stst_last_cuda = cudaSuccess;
 
 int grid_for(long long n, int block) { return (int)((n + block - 1) / block); }
+
+int ensure_dyn_smem(const void *kern, size_t bytes) {
+  static std::mutex mu;
+  static std::unordered_map<const void *, size_t> done;
+  if (bytes <= 32 * 1024) return STST_OK;  // below the default limit whatever the static part (< 16 KB here)
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = done.find(kern);
+  if (it != done.end() && it->second >= bytes) return STST_OK;
+  STST_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  done[kern] = bytes;
+  return STST_OK;
+}
 
 // Knot xi_j of the open uniform knot vector on [0,1] (degree p, n_el elements), 0-based j.
 __device__ __forceinline__ double knot(int j, int p, int n_el) {

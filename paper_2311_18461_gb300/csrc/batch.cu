@@ -182,6 +182,8 @@ extern "C" int stst_batch_create(stst_batch *out, int count, const stst_handle *
     s = STST_ERR_OOM;
   cudaGraph_t G = nullptr;
   if (s == STST_OK && cudaGraphCreate(&G, 0) != cudaSuccess) s = STST_ERR_CUDA;
+  // tiles are chosen before capture (timing cannot run inside it); shapes seen before reuse the cache
+  for (int i = 0; s == STST_OK && i < count; ++i) s = tune_modeprod(b->hs[i]);
   for (int i = 0; s == STST_OK && i < count; ++i) {
     // every problem's handle streams are idle: capturing on them records, it does not run
     if (cudaStreamSynchronize(b->hs[i]->stream) != cudaSuccess) s = STST_ERR_CUDA;

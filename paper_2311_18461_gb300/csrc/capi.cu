@@ -10,6 +10,7 @@
 // level 0 applies each distinct matrix of the first mode once; later levels group the terms by the
 // matrices they still need. The mode order with the fewest band applications is chosen.
 #include "common.cuh"
+#include <cstdio>
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -588,6 +589,7 @@ int stst_create(stst_handle *out, int d, const int *n_el, const int *p, double T
     }
     h->own_stream = 1;
   }
+  for (int l = 1; l <= d; ++l) h->mp_cfg[l] = modeprod_default(n_el[l] + p[l] - 2);
   int s = create_impl(h, d, n_el, p, T, nu, prec_mode);
   if (s != STST_OK) {
     destroy_all(h);
@@ -740,7 +742,30 @@ int stst_set_potential(stst_handle h, int rank, const double *v_qp) {
 int stst_build_fd(stst_handle h) {
   STST_TRY(check(h));
   ApiScope scope(h);
-  return fd_setup(h);
+  STST_TRY(fd_setup(h));
+  return tune_modeprod(h);
+}
+
+const char *stst_last_cuda_error(void) {
+  static thread_local char buf[160];
+  snprintf(buf, sizeof(buf), "%s: %s", cudaGetErrorName(stst_last_cuda), cudaGetErrorString(stst_last_cuda));
+  return buf;
+}
+
+int stst_set_autotune(int mode) {
+  const int rpt = mode / 10, cpt = mode % 10;
+  if (mode != 0 && mode != 1 && !(rpt >= 1 && rpt <= 4 && (cpt == 2 || cpt == 4))) return STST_ERR_ARG;
+  g_tune_enabled = mode;
+  return STST_OK;
+}
+
+int stst_tile_info(stst_handle h, int dir, int *cols_per_cta, int *rows_per_cta, double *us) {
+  STST_TRY(check(h));
+  if (dir < 1 || dir > h->d) return STST_ERR_ARG;
+  if (cols_per_cta) *cols_per_cta = 8 * h->mp_cfg[dir].cpt;
+  if (rows_per_cta) *rows_per_cta = 32 * h->mp_cfg[dir].rpt;
+  if (us) *us = h->mp_us[dir];
+  return STST_OK;
 }
 
 int stst_apply_sys(stst_handle h, const double *x, double *y) {

@@ -79,6 +79,11 @@ struct Plan {
 };
 
 // ---- PCG control block (device) ---------------------------------------------------------------
+// Tile of the SIMT mode product: cpt columns per thread (8 cpt per CTA), rpt groups of 32 output rows.
+struct MpCfg {
+  int cpt, rpt;
+};
+
 struct PcgCtl {
   double ff, rr, rho, pq, alpha, beta, rz_old, tol2;
   int it, maxit, done, status;
@@ -115,6 +120,9 @@ struct stst_problem {
 
   // FD
   int fd_ready;
+  MpCfg mp_cfg[STST_MAXD + 1];     // mode-product tile per direction (autotuned or default)
+  float mp_us[STST_MAXD + 1];      // its measured time per launch (0: not measured)
+  int tuned;
   int eig_src[STST_MAXD + 1];
   double *U[STST_MAXD + 1];
   float *U32[STST_MAXD + 1];
@@ -199,6 +207,13 @@ int ir_run(stst_problem *h, const double *rhs, double *x, double tol, int maxit,
            int inner_maxit, int *iters, int *outer, double *relres);
 
 int grid_for(long long n, int block);
+int fd_partials_count(stst_problem *h);
+// Opts kernel `kern` into `bytes` of dynamic shared memory (with its static shared memory the default
+// limit is 48 KB in total); remembers the largest size set per kernel, so repeated launches skip the call.
+int ensure_dyn_smem(const void *kern, size_t bytes);
+MpCfg modeprod_default(int n);
+int tune_modeprod(stst_problem *h);  // times the mode-product tiles once per shape (outside graph capture)
+extern int g_tune_enabled;
 
 // tensor-core mode products (modeprod_tc.cu)
 int launch_u_to_bf16(const double *U, int n, __nv_bfloat16 *out, cudaStream_t s);

@@ -20,7 +20,8 @@
 // and U0 = C^{-T} Q. Outputs U0 (row-major n x n, column j = eigenvector j) and lam0 ascending.
 // ------------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(512) k_eig_tridiag(const double *__restrict__ Mb, const double *__restrict__ Lb,
-                                                     int n, int p, double *U0, double *lam0, float *lu, int *flags) {
+                                                     int n, int p, double *U0, double *lam0, float *lu, int *flags,
+                                                     int lu_smem) {
   extern __shared__ __align__(16) float sm[];
   const int ld = n + 1;
   float *A = sm;                   // n x ld: matrix, then Householder vectors below the diagonal
@@ -31,6 +32,7 @@ __global__ void __launch_bounds__(512) k_eig_tridiag(const double *__restrict__ 
   float *bet = od + n;             // Householder beta_k
   float *pv = bet + n;             // work vector p
   float *wv = pv + n;              // work vector w
+  if (lu_smem) lu = wv + n;        // 3 n^2 floats of LU rows in shared memory when they fit
   __shared__ float red[32];
   __shared__ float bc[4];
   const int tid = threadIdx.x, nth = blockDim.x;
@@ -106,11 +108,16 @@ __global__ void __launch_bounds__(512) k_eig_tridiag(const double *__restrict__ 
     }
     __syncthreads();
     if (beta > 0.f) {
-      // p = beta * A_sub v (one thread per row)
-      for (int i = tid; i < m; i += nth) {
+      // p = beta * A_sub v: eight lanes per row, combined by shuffles within each group of eight
+      for (int base = 0; base < m; base += nth >> 3) {
+        const int i = base + (tid >> 3), q = tid & 7;
         float s = 0.f;
-        for (int j = 0; j < m; ++j) s += A[(k + 1 + i) * ld + (k + 1 + j)] * A[(k + 1 + j) * ld + k];
-        pv[i] = beta * s;
+        if (i < m)
+          for (int j = q; j < m; j += 8) s += A[(k + 1 + i) * ld + (k + 1 + j)] * A[(k + 1 + j) * ld + k];
+        s += __shfl_xor_sync(0xffffffffu, s, 1);
+        s += __shfl_xor_sync(0xffffffffu, s, 2);
+        s += __shfl_xor_sync(0xffffffffu, s, 4);
+        if (q == 0 && i < m) pv[i] = beta * s;
       }
       __syncthreads();
       if (tid < 32) {
@@ -250,16 +257,31 @@ __global__ void __launch_bounds__(512) k_eig_tridiag(const double *__restrict__ 
     }
   }
   __syncthreads();
-  // 6. back-transform the eigenvectors: x <- H_0 H_1 ... H_{n-3} x, H_k = I - beta_k v_k v_k^T on rows k+1..
-  for (int j = tid; j < n; j += nth) {
-    for (int k = n - 3; k >= 0; --k) {
-      float b = bet[k];
-      if (b == 0.f) continue;
-      float s = 0.f;
-      for (int i = k + 1; i < n; ++i) s += A[i * ld + k] * X[i * ld + j];
-      s *= b;
-      for (int i = k + 1; i < n; ++i) X[i * ld + j] -= s * A[i * ld + k];
+  // 6. back-transform the eigenvectors: X <- H_0 H_1 ... H_{n-3} X, H_k = I - beta_k v_k v_k^T on rows
+  //    k+1..; per reflection, s_j = beta_k v_k^T X[:, j] by eight lanes per column, then the rank-1 update
+  //    over all entries (pv, wv are free once the eigenvalues are in lam0)
+  for (int k = n - 3; k >= 0; --k) {
+    const float b = bet[k];
+    if (b == 0.f) continue;  // uniform over the block
+    for (int base = 0; base < n; base += nth >> 3) {
+      const int j = base + (tid >> 3), q = tid & 7;
+      float sj = 0.f;
+      if (j < n)
+        for (int i = k + 1 + q; i < n; i += 8) sj += A[i * ld + k] * X[i * ld + j];
+      sj += __shfl_xor_sync(0xffffffffu, sj, 1);
+      sj += __shfl_xor_sync(0xffffffffu, sj, 2);
+      sj += __shfl_xor_sync(0xffffffffu, sj, 4);
+      if (q == 0 && j < n) wv[j] = b * sj;
     }
+    __syncthreads();
+    const int rows = n - k - 1;
+    for (int e = tid; e < rows * n; e += nth) {
+      const int i = k + 1 + e / n, j = e - (e / n) * n;
+      X[i * ld + j] -= wv[j] * A[i * ld + k];
+    }
+    __syncthreads();
+  }
+  for (int j = tid; j < n; j += nth) {
     // normalize (2-norm) and U0 = C^{-T} x : back substitution
     float s = 0.f;
     for (int i = 0; i < n; ++i) s += X[i * ld + j] * X[i * ld + j];
@@ -551,9 +573,16 @@ int fd_setup_launch(stst_problem *h) {
     const int n = h->dir[l].n, p = h->dir[l].p;
     const BandMat &M = h->mats[l][0], &L = h->mats[l][1];
     size_t sm = (2 * (size_t)n * (n + 1) + (size_t)n * (p + 1) + 5 * (size_t)n) * sizeof(float);
-    STST_CUDA(cudaFuncSetAttribute(k_eig_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const size_t sm_lu = sm + 3 * (size_t)n * n * sizeof(float);
+    int dev = 0, optin = 0;
+    STST_CUDA(cudaGetDevice(&dev));
+    STST_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const int lu_smem = sm_lu <= (size_t)optin ? 1 : 0;
+    if (lu_smem) sm = sm_lu;
+    STST_TRY(ensure_dyn_smem((const void *)k_eig_tridiag, sm));
     { STST_PROF("eig_tridiag_f32", st);
-    k_eig_tridiag<<<1, 512, sm, st>>>(M.d, L.d, n, p, h->U[l], h->lam[l], (float *)h->oa_work, h->flags); }
+    k_eig_tridiag<<<1, 512, sm, st>>>(M.d, L.d, n, p, h->U[l], h->lam[l], (float *)h->oa_work, h->flags,
+                                      lu_smem); }
     STST_CUDA(cudaGetLastError());
     double *X = h->U[l], *PM = h->oa_work, *PL = PM + n * n, *R = PL + n * n, *S = R + n * n, *E = S + n * n,
            *Xn = E + n * n;

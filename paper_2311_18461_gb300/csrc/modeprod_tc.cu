@@ -258,13 +258,11 @@ int launch_modeprod_tc(const TI *X, TO *Y, const __nv_bfloat16 *Bk, long long lo
                     (size_t)n * 64 * sizeof(float2);
   STST_PROF(split == 3 ? "modeprod_bf16x3_tc" : "modeprod_bf16_tc", s);
   if (split == 3) {
-    if (sm > 48 * 1024)
-      STST_CUDA(cudaFuncSetAttribute(k_modeprod_tc<TI, TO, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    STST_TRY(ensure_dyn_smem((const void *)k_modeprod_tc<TI, TO, 3>, sm));
     k_modeprod_tc<TI, TO, 3><<<grid, 128, sm, s>>>(X, Y, Bk, lo_stride, n, np, kp, inner, ncols, dotvec,
                                                    dot_partials, done, errflag);
   } else {
-    if (sm > 48 * 1024)
-      STST_CUDA(cudaFuncSetAttribute(k_modeprod_tc<TI, TO, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    STST_TRY(ensure_dyn_smem((const void *)k_modeprod_tc<TI, TO, 1>, sm));
     k_modeprod_tc<TI, TO, 1><<<grid, 128, sm, s>>>(X, Y, Bk, lo_stride, n, np, kp, inner, ncols, dotvec,
                                                    dot_partials, done, errflag);
   }

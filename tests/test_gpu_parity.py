@@ -280,3 +280,27 @@ def test_apply_prec_size_sweep(p):
                 bad.append((n_el, prec, err))
             prob.close()
     assert not bad, bad
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", [0, 1])
+def test_mode_product_tiles_agree_bitwise(prec):
+    """Every mode-product tile sums each output in the same order: apply_prec is bitwise identical."""
+    import torch
+    import paper_2311_18461_gb300 as P
+    outs = {}
+    try:
+        for mode in (0, 12, 14, 22, 24, 32, 34, 42, 44, 1):
+            P.stst_set_autotune(mode)
+            prob = P.Problem(2, [5, 40, 70], 3, prec_mode=prec)  # n_l = 41 and 71
+            prob.build_fd()
+            r = torch.tensor(np.random.default_rng(3).standard_normal(2 * prob.n_dof), device="cuda").view(
+                torch.complex128)
+            outs[mode] = (prob.apply_prec(r).cpu().numpy(), [P.stst_tile_info(prob.h, l) for l in (1, 2)])
+            prob.close()
+    finally:
+        P.stst_set_autotune(1)
+    ref = outs[0][0]
+    for mode, (o, tiles) in outs.items():
+        assert np.array_equal(o, ref), (mode, tiles)
+    assert outs[12][1][0][:2] == (16, 32) and outs[44][1][1][:2] == (32, 128)
