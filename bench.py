@@ -429,6 +429,28 @@ def run_warmstart(args):
     prob.close()
 
 
+def roofline_steps(n_dof, n_l, flops_dof, t_prec_ms, t_sys_ms, prec, peaks, fp64_peak, fp32_peak):
+    """t_bound / t_measured per operator, t_bound = max(flops / pipe peak, algorithmic bytes / HBM peak).
+
+    apply_prec (Algorithm 1 steps 2-4): 8 N sum_l n_l flops for the mode products (4 n_l per complex
+    unknown per mode, forward and backward) on the FP32 or FP64 pipe; apply_sys (Eq. syst_mat): the
+    planner's flops per unknown on the FP64 pipe. Bytes: r in and s out in FP64, 32 B per unknown."""
+    hbm = peaks["hbm_gbs"] * 1e9
+    out = {}
+    fl = 8.0 * n_dof * sum(n_l)
+    pk = (fp64_peak if prec == "fp64" else fp32_peak) * 1e12
+    tb = max(fl / pk, 32.0 * n_dof / hbm)
+    out["apply_prec"] = {"flops": fl, "bytes": 32.0 * n_dof, "pipe": "fp64" if prec == "fp64" else "fp32",
+                         "t_bound_ms": tb * 1e3, "t_ms": t_prec_ms, "frac": tb * 1e3 / t_prec_ms}
+    if prec == "bf16":
+        out["apply_prec"]["pipe"] = "fp32 bound used (BF16x3 on tensor cores, time solves FP32)"
+    fl = flops_dof * n_dof
+    tb = max(fl / (fp64_peak * 1e12), 32.0 * n_dof / hbm)
+    out["apply_sys"] = {"flops": fl, "bytes": 32.0 * n_dof, "pipe": "fp64", "t_bound_ms": tb * 1e3, "t_ms": t_sys_ms,
+                        "frac": tb * 1e3 / t_sys_ms}
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -488,6 +510,23 @@ def run_ours(args):
             t = torch.tensor([ms], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ms = float(t.item())
+
+        # PCG alone (preconditioner built beforehand): the paper's "solve" without its setup
+        prob.build_fd()
+        pcg_only = []
+        for _ in range(args.steps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            x.zero_()
+            e0.record(stream)
+            if args.solver == "ir":
+                S.stst_ir_solve(prob.h, b, x, tol, 30, args.inner_tol, 200)
+            else:
+                S.stst_pcg_solve(prob.h, b, x, tol, 200)
+            e1.record(stream)
+            e1.synchronize()
+            pcg_only.append(e0.elapsed_time(e1))
+        pcg_only_ms = statistics.mean(pcg_only)
 
         # end to end through the C ABI with host buffers: pinned rhs in, solution out, every step
         b_host = b.cpu().pin_memory()
@@ -602,12 +641,16 @@ def run_ours(args):
                    "pcg_iterations": statistics.median(iters),
                    "step": "build_fd (setup) + pcg_solve from x0 = 0", "l2": "flushed (512 MB write) before each step",
                    "parallelism": f"replicas x{world}"},
+        "pcg_only_ms": pcg_only_ms,
+        "roofline_steps": roofline_steps(n_dof, n_l, flops_dof, t_prec, t_sys, args.prec, peaks, fp64_peak, fp32_peak),
         "apply_prec_dofs_per_s": n_dof / (t_prec / 1e3),
         "apply_prec_ms": t_prec,
         "apply_sys_ms": t_sys,
         "mat_vec_plan": {"passes": n_passes, "band_apps_per_dof": band_apps, "flops_per_dof": flops_dof},
         "mode_product_tiles": [dict(zip(("cols_per_cta", "rows_per_cta", "tuned_us"), S.stst_tile_info(prob.h, l)))
                                for l in range(1, cfg["d"] + 1)],
+        "time_solver": dict(zip(("segments", "segment_len", "segmented"),
+                                S.stst_time_solver_info(prob.h, 0 if args.prec == "fp64" else 1))),
         "kernels_ms_per_solve": {k: round(v[1], 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
         "kernel_launches_per_solve": {k: v[0] for k, v in prof.items()},
         "gpu_launches": int(sum(v[0] for v in prof.values())) * args.steps,

@@ -221,6 +221,19 @@ int stst_batch_destroy(stst_batch b);
  * (host, may be NULL) and its measured microseconds per launch (0 when not measured).
  */
 int stst_set_autotune(int mode);
+/*
+ * stst_set_time_solver: the kernel of Algorithm 1 step 3 (the N_s banded time solves): mode 0 (default)
+ * chooses per problem shape when the preconditioner is built (timed under autotune mode 1, else the
+ * segmented kernel when the sequential one would leave SMs idle); 1 = sequential recurrences (one thread
+ * per system); 2 = segmented, parallel in time where its shared memory fits: the time axis is cut into
+ * S <= 8 segments that run concurrently, with P x P transfer matrices (precomputed from the factors by
+ * stst_build_fd) carrying the recurrence state across segments. The two give the same solves up to
+ * rounding. Process-wide, for handles whose preconditioner is built afterwards. STST_ERR_ARG otherwise.
+ * stst_time_solver_info: for precision STST_PREC_FP64 (0) or STST_PREC_FP32 (1) factors: the number of
+ * segments (0 when the segmented kernel does not fit), their length, and whether it is used (host).
+ */
+int stst_set_time_solver(int mode);
+int stst_time_solver_info(stst_handle h, int precision, int *segments, int *segment_len, int *segmented);
 /* Name and description of the CUDA error behind the calling thread's last STST_ERR_CUDA (static string). */
 const char *stst_last_cuda_error(void);
 int stst_tile_info(stst_handle h, int dir, int *cols_per_cta, int *rows_per_cta, double *us);

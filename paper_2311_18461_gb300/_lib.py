@@ -57,6 +57,8 @@ def lib():
             "stst_plan_info": [P, IP, IP, DP],
             "stst_profile_read": [P, I, ctypes.c_char_p, I, ctypes.POINTER(LL), DP],
             "stst_set_autotune": [I],
+            "stst_set_time_solver": [I],
+            "stst_time_solver_info": [P, I, IP, IP, IP],
             "stst_tile_info": [P, I, IP, IP, DP],
             "stst_ws_create": [ctypes.POINTER(P), I, IP, I, ctypes.c_ulonglong, P],
             "stst_ws_destroy": [P],
@@ -249,6 +251,19 @@ def stst_profile_read(h):
 
 def stst_set_autotune(mode):
     return _chk(lib().stst_set_autotune(int(mode)), "stst_set_autotune")
+
+
+def stst_set_time_solver(mode):
+    return _chk(lib().stst_set_time_solver(int(mode)), "stst_set_time_solver")
+
+
+def stst_time_solver_info(h, precision):
+    S = ctypes.c_int()
+    L = ctypes.c_int()
+    used = ctypes.c_int()
+    _chk(lib().stst_time_solver_info(h, int(precision), ctypes.byref(S), ctypes.byref(L), ctypes.byref(used)),
+         "stst_time_solver_info")
+    return S.value, L.value, used.value
 
 
 def stst_tile_info(h, dir):

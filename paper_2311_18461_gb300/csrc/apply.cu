@@ -490,8 +490,7 @@ static int tune_one(stst_problem *h, int l, long long inner, long long outer, Mp
   return STST_OK;
 }
 
-int tune_modeprod(stst_problem *h) {
-  if (h->tuned) return STST_OK;
+static int tune_mp_tiles(stst_problem *h) {
   if (h->prec_mode == STST_PREC_BF16 || g_tune_enabled != 1) {
     for (int l = 1; l <= h->d; ++l) {
       h->mp_cfg[l] = modeprod_default(h->dir[l].n);
@@ -507,7 +506,6 @@ int tune_modeprod(stst_problem *h) {
         if (modeprod_smem(h->dir[l].n, c, rs) <= (size_t)optin) h->mp_cfg[l] = c;
       }
     }
-    h->tuned = 1;
     return STST_OK;
   }
   long long acc = h->n_t();
@@ -521,7 +519,6 @@ int tune_modeprod(stst_problem *h) {
     h->mp_cfg[l] = c;
     h->mp_us[l] = us;
   }
-  h->tuned = 1;
   return STST_OK;
 }
 
@@ -654,6 +651,277 @@ __global__ void __launch_bounds__(32) k_timesolve(void *__restrict__ Yv, const v
   }
 }
 
+// ------------------------------------------------------------------------------------------------
+// Parallel-in-time time solves. Each system's time axis is cut into S segments that run concurrently
+// (one warp per segment, 32 systems per CTA). A banded recurrence carries a state of P values; its map
+// across a segment is affine: out = (zero-start run) + T_s in. The transfer matrices T_s depend only on
+// the factors and are computed once at setup (k_time_transfer). An application runs every segment from
+// a zero state, carries the true states across the segments with the T_s (one lane per system, S steps),
+// and reruns every segment from its true state; the same three steps solve G^H x = w backwards. The
+// serial depth per solve drops from 2 n_t steps to about 4 n_t / S + 2 S.
+// Layouts: T_s[((s P + r) P + c) Ns + i] (r: output state, c: input state). Forward states hold
+// (w_{t-1}, ..., w_{t-P}); backward states hold (x_{t+1}, ..., x_{t+P}).
+// ------------------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void cmul_sub(T &acc, const T g, const T z) {  // acc -= g z
+  acc.x -= g.x * z.x - g.y * z.y;
+  acc.y -= g.x * z.y + g.y * z.x;
+}
+template <typename T>
+__device__ __forceinline__ void cjmul_sub(T &acc, const T g, const T z) {  // acc -= conj(g) z
+  acc.x -= g.x * z.x + g.y * z.y;
+  acc.y -= g.x * z.y - g.y * z.x;
+}
+
+template <typename R, int P>
+__global__ void k_time_transfer(const void *__restrict__ Gv, const R *__restrict__ D, int nt, long long Ns, int S,
+                                int L, void *Tfv, void *Tbv) {
+  using T = typename C2<R>::T;
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= Ns * S * P) return;
+  const long long i = idx % Ns, rest = idx / Ns;
+  const int c = (int)(rest % P), s = (int)(rest / P);
+  const T *G = (const T *)Gv;
+  T *Tf = (T *)Tfv, *Tb = (T *)Tbv;
+  const int a = s * L, b = min(nt, a + L);
+  T st[P];
+#pragma unroll
+  for (int k = 0; k < P; ++k) { st[k].x = 0; st[k].y = 0; }
+  st[c].x = 1;
+  for (int t = a; t < b; ++t) {  // homogeneous forward recurrence
+    T acc;
+    acc.x = 0;
+    acc.y = 0;
+#pragma unroll
+    for (int k = 1; k <= P; ++k) cmul_sub(acc, G[((long long)t * P + (k - 1)) * Ns + i], st[k - 1]);
+    const R dinv = D[(long long)t * Ns + i];
+#pragma unroll
+    for (int k = P - 1; k > 0; --k) st[k] = st[k - 1];
+    st[0].x = acc.x * dinv;
+    st[0].y = acc.y * dinv;
+  }
+#pragma unroll
+  for (int r = 0; r < P; ++r) Tf[((long long)(s * P + r) * P + c) * Ns + i] = st[r];
+#pragma unroll
+  for (int k = 0; k < P; ++k) { st[k].x = 0; st[k].y = 0; }
+  st[c].x = 1;
+  for (int t = b - 1; t >= a; --t) {  // homogeneous backward recurrence
+    T acc;
+    acc.x = 0;
+    acc.y = 0;
+#pragma unroll
+    for (int k = 1; k <= P; ++k)
+      if (t + k < nt) cjmul_sub(acc, G[((long long)(t + k) * P + (k - 1)) * Ns + i], st[k - 1]);
+    const R dinv = D[(long long)t * Ns + i];
+#pragma unroll
+    for (int k = P - 1; k > 0; --k) st[k] = st[k - 1];
+    st[0].x = acc.x * dinv;
+    st[0].y = acc.y * dinv;
+  }
+#pragma unroll
+  for (int r = 0; r < P; ++r) Tb[((long long)(s * P + r) * P + c) * Ns + i] = st[r];
+}
+
+template <typename R, int P>
+__global__ void __launch_bounds__(256) k_timesolve_seg(void *__restrict__ Yv, const void *__restrict__ Gv,
+                                                       const R *__restrict__ D, const void *__restrict__ Tfv,
+                                                       const void *__restrict__ Tbv, int nt, long long Ns, int S,
+                                                       int L, const int *done) {
+  using T = typename C2<R>::T;
+  if (done && *done) return;
+  extern __shared__ __align__(16) unsigned char tss[];
+  T *ty = (T *)tss;                              // [nt][33]: data, then w, then x
+  T *tg = ty + (size_t)nt * 33;                  // [nt][P][32]: G[t][t-k]
+  T *sp = tg + (size_t)nt * P * 32;              // [S][P][32]: states after a zero-start run
+  T *si = sp + (size_t)S * P * 32;               // [S][P][32]: true incoming states
+  T *tf = si + (size_t)S * P * 32;               // [S][P][P][32]
+  T *tb = tf + (size_t)S * P * P * 32;           // [S][P][P][32]
+  R *td = (R *)(tb + (size_t)S * P * P * 32);    // [nt][32]: 1 / G[t][t]
+  T *Y = (T *)Yv;
+  const T *G = (const T *)Gv, *Tf = (const T *)Tfv, *Tb = (const T *)Tbv;
+  const int nth = blockDim.x;
+  const long long i0 = (long long)blockIdx.x * 32;
+  const int nsys = (int)min((long long)32, Ns - i0);
+  T zero;
+  zero.x = 0;
+  zero.y = 0;
+  for (int e = threadIdx.x; e < 32 * nt; e += nth) {  // system ss, time u: u fastest (coalesced reads)
+    const int ss = e / nt, u = e - (e / nt) * nt;
+    if (ss < nsys) cp_async<sizeof(T)>(&ty[u * 33 + ss], &Y[(i0 + ss) * nt + u]);
+    else ty[u * 33 + ss] = zero;
+  }
+  for (int e = threadIdx.x; e < nt * P * 32; e += nth) {
+    const int ss = e & 31;
+    if (ss < nsys) cp_async<sizeof(T)>(&tg[e], &G[(long long)(e >> 5) * Ns + i0 + ss]);
+    else tg[e] = zero;
+  }
+  for (int e = threadIdx.x; e < S * P * P * 32; e += nth) {
+    const int ss = e & 31;
+    if (ss < nsys) {
+      cp_async<sizeof(T)>(&tf[e], &Tf[(long long)(e >> 5) * Ns + i0 + ss]);
+      cp_async<sizeof(T)>(&tb[e], &Tb[(long long)(e >> 5) * Ns + i0 + ss]);
+    } else {
+      tf[e] = zero;
+      tb[e] = zero;
+    }
+  }
+  for (int e = threadIdx.x; e < nt * 32; e += nth) {
+    const int ss = e & 31;
+    if (ss < nsys) cp_async<sizeof(R)>(&td[e], &D[(long long)(e >> 5) * Ns + i0 + ss]);
+    else td[e] = (R)0;
+  }
+  cp_async_commit();
+  cp_async_wait_all();
+  __syncthreads();
+  const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5;
+  const int a = seg * L, b = min(nt, a + L);
+  T st[P];
+  auto forward = [&](bool write) {
+    for (int t = a; t < b; ++t) {
+      T acc = ty[t * 33 + lane];
+#pragma unroll
+      for (int k = 1; k <= P; ++k) cmul_sub(acc, tg[(t * P + (k - 1)) * 32 + lane], st[k - 1]);
+      const R dinv = td[t * 32 + lane];
+#pragma unroll
+      for (int k = P - 1; k > 0; --k) st[k] = st[k - 1];
+      st[0].x = acc.x * dinv;
+      st[0].y = acc.y * dinv;
+      if (write) ty[t * 33 + lane] = st[0];
+    }
+  };
+  auto backward = [&](bool write) {
+    for (int t = b - 1; t >= a; --t) {
+      T acc = ty[t * 33 + lane];
+#pragma unroll
+      for (int k = 1; k <= P; ++k)
+        if (t + k < nt) cjmul_sub(acc, tg[((t + k) * P + (k - 1)) * 32 + lane], st[k - 1]);
+      const R dinv = td[t * 32 + lane];
+#pragma unroll
+      for (int k = P - 1; k > 0; --k) st[k] = st[k - 1];
+      st[0].x = acc.x * dinv;
+      st[0].y = acc.y * dinv;
+      if (write) ty[t * 33 + lane] = st[0];
+    }
+  };
+  // carry: one lane per system walks the segments in `dir` order; in of the first segment is zero,
+  // in of the next = out of this = sp + T in
+  auto carry = [&](const T *tr, int first, int step) {
+    T cur[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) cur[k] = zero;
+    for (int s2 = first, n2 = 0; n2 < S; ++n2, s2 += step) {
+      T nxt[P];
+#pragma unroll
+      for (int r = 0; r < P; ++r) {
+        si[(s2 * P + r) * 32 + lane] = cur[r];
+        T o = sp[(s2 * P + r) * 32 + lane];
+#pragma unroll
+        for (int c = 0; c < P; ++c) {
+          const T g = tr[((s2 * P + r) * P + c) * 32 + lane];
+          o.x += g.x * cur[c].x - g.y * cur[c].y;
+          o.y += g.x * cur[c].y + g.y * cur[c].x;
+        }
+        nxt[r] = o;
+      }
+#pragma unroll
+      for (int r = 0; r < P; ++r) cur[r] = nxt[r];
+    }
+  };
+  // G w = y
+#pragma unroll
+  for (int k = 0; k < P; ++k) st[k] = zero;
+  forward(false);
+#pragma unroll
+  for (int k = 0; k < P; ++k) sp[(seg * P + k) * 32 + lane] = st[k];
+  __syncthreads();
+  if (seg == 0) carry(tf, 0, 1);
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < P; ++k) st[k] = si[(seg * P + k) * 32 + lane];
+  forward(true);
+  __syncthreads();
+  // G^H x = w
+#pragma unroll
+  for (int k = 0; k < P; ++k) st[k] = zero;
+  backward(false);
+#pragma unroll
+  for (int k = 0; k < P; ++k) sp[(seg * P + k) * 32 + lane] = st[k];
+  __syncthreads();
+  if (seg == 0) carry(tb, S - 1, -1);
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < P; ++k) st[k] = si[(seg * P + k) * 32 + lane];
+  backward(true);
+  __syncthreads();
+  for (int e = threadIdx.x; e < nsys * nt; e += nth) {
+    const int ss = e / nt, u = e - (e / nt) * nt;
+    Y[(i0 + ss) * nt + u] = ty[u * 33 + ss];
+  }
+}
+
+size_t ts_seg_smem(int nt, int P, int S, size_t rs) {
+  const size_t cs = 2 * rs;
+  return (size_t)nt * 33 * cs + (size_t)nt * P * 32 * cs + 2 * (size_t)S * P * 32 * cs +
+         2 * (size_t)S * P * P * 32 * cs + (size_t)nt * 32 * rs;
+}
+
+// largest S <= 8 (segments of at least P steps) whose shared memory fits; S = 0 when none does
+void ts_segments(int nt, int P, size_t rs, int *S_out, int *L_out) {
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  *S_out = 0;
+  *L_out = nt;
+  for (int S = 8; S >= 2; --S) {
+    const int L = (nt + S - 1) / S;
+    if (L < P || (S - 1) * L >= nt) continue;
+    if (ts_seg_smem(nt, P, S, rs) > (size_t)optin) continue;
+    *S_out = S;
+    *L_out = L;
+    return;
+  }
+}
+
+template <typename R>
+int launch_time_transfer(const void *G, const R *D, int nt, long long Ns, int P, int S, int L, void *Tf, void *Tb,
+                         cudaStream_t s) {
+  if (S < 2) return STST_OK;
+  const long long n = Ns * S * P;
+  STST_PROF(sizeof(R) == 8 ? "time_transfer_f64" : "time_transfer_f32", s);
+  switch (P) {
+#define CASE(PP) case PP: k_time_transfer<R, PP><<<grid_for(n, 128), 128, 0, s>>>(G, D, nt, Ns, S, L, Tf, Tb); break;
+    CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+#undef CASE
+    default: return STST_ERR_ARG;
+  }
+  STST_CUDA(cudaGetLastError());
+  return STST_OK;
+}
+template int launch_time_transfer<float>(const void *, const float *, int, long long, int, int, int, void *, void *,
+                                         cudaStream_t);
+template int launch_time_transfer<double>(const void *, const double *, int, long long, int, int, int, void *, void *,
+                                          cudaStream_t);
+
+template <typename R>
+static int launch_timesolve_seg(void *Y, const void *G, const R *D, const void *Tf, const void *Tb, int nt,
+                                long long Ns, int P, int S, int L, const int *done, cudaStream_t s) {
+  const size_t sm = ts_seg_smem(nt, P, S, sizeof(R));
+  STST_PROF(sizeof(R) == 8 ? "timesolve_f64" : "timesolve_f32", s);
+  const int grid = grid_for(Ns, 32);
+  switch (P) {
+#define CASE(PP)                                                                                       \
+  case PP:                                                                                             \
+    STST_TRY(ensure_dyn_smem((const void *)k_timesolve_seg<R, PP>, sm));                               \
+    k_timesolve_seg<R, PP><<<grid, 32 * S, sm, s>>>(Y, G, D, Tf, Tb, nt, Ns, S, L, done);              \
+    break;
+    CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+#undef CASE
+    default: return STST_ERR_ARG;
+  }
+  STST_CUDA(cudaGetLastError());
+  return STST_OK;
+}
+
 template <typename R>
 static int launch_timesolve(void *Y, const void *G, const R *D, int nt, long long Ns, int P, const int *done,
                             cudaStream_t s) {
@@ -689,6 +957,19 @@ static int launch_timesolve(void *Y, const void *G, const R *D, int nt, long lon
 // in32 / out32: optional FP32 input / output (inner FP32 solver), replacing r / s.
 // The final mode product optionally accumulates per-CTA partials of Re<r, s> into dot_partials.
 // ------------------------------------------------------------------------------------------------
+
+// time solve of the preconditioner: segmented (parallel in time) or sequential, as chosen per handle
+template <typename R>
+static int time_solve(stst_problem *h, void *Y, const int *done, cudaStream_t st) {
+  const int q = sizeof(R) == 8 ? 1 : 0;
+  const void *G = q ? h->Hg : h->Hg32;
+  const R *D = q ? (const R *)h->Hd : (const R *)h->Hd32;
+  if (h->ts_seg[q] && h->ts_S[q] >= 2)
+    return launch_timesolve_seg<R>(Y, G, D, h->Tf[q], h->Tb[q], h->n_t(), h->N_s, h->dir[0].p, h->ts_S[q],
+                                   h->ts_L[q], done, st);
+  return launch_timesolve<R>(Y, G, D, h->n_t(), h->N_s, h->dir[0].p, done, st);
+}
+
 int fd_apply(stst_problem *h, const double *r, double *s, int precision, const void *dotvec, double *dot_partials,
              const int *done, void *bufA, void *bufB, float *out32, const float *in32) {
   const int d = h->d, nt = h->n_t();
@@ -717,7 +998,7 @@ int fd_apply(stst_problem *h, const double *r, double *s, int precision, const v
       src = dst;
       cur ^= 1;
     }
-    STST_TRY(launch_timesolve<double>((void *)src, h->Hg, h->Hd, nt, Ns, h->dir[0].p, done, st));
+    STST_TRY(time_solve<double>(h, (void *)src, done, st));
     for (int l = d; l >= 1; --l) {
       double2 *dst = (l == 1) ? (double2 *)s : bufs[cur];
       STST_TRY((launch_modeprod<double, double2, double2>(src, dst, h->U[l], h->dir[l].n, inner[l], outer[l], 1,
@@ -754,7 +1035,7 @@ int fd_apply(stst_problem *h, const double *r, double *s, int precision, const v
       src32 = dst;
       cur ^= 1;
     }
-    STST_TRY(launch_timesolve<float>((void *)src32, h->Hg32, h->Hd32, nt, Ns, h->dir[0].p, done, st));
+    STST_TRY(time_solve<float>(h, (void *)src32, done, st));
     for (int l = d; l >= 1; --l) {
       if (l == 1) {
         if (out32) {
@@ -796,7 +1077,7 @@ int fd_apply(stst_problem *h, const double *r, double *s, int precision, const v
     src32 = dst;
     cur ^= 1;
   }
-  STST_TRY(launch_timesolve<float>((void *)src32, h->Hg32, h->Hd32, nt, Ns, h->dir[0].p, done, st));
+  STST_TRY(time_solve<float>(h, (void *)src32, done, st));
   for (int l = d; l >= 1; --l) {
     if (l == 1) {
       if (out32) {
@@ -825,4 +1106,78 @@ int fd_partials_count(stst_problem *h) {
   if (h->prec_mode == STST_PREC_BF16) return tc_partials_count(ncols);
   const dim3 g = modeprod_grid(h->dir[1].n, ncols, h->mp_cfg[1]);
   return (int)(g.x * g.y);
+}
+
+// ---- choice of the time-solve kernel --------------------------------------------------------------
+// Measured (mode 1): both kernels timed in place on a work vector, cached per (precision, n_t, N_s, P).
+// Otherwise the segmented kernel is used when the sequential one would leave SMs without a warp.
+static std::map<std::tuple<int, int, long long, int>, int> g_ts_cache;
+int g_ts_mode = 0;  // 0 chosen per shape, 1 sequential, 2 segmented where it fits
+
+template <typename R>
+static int tune_ts(stst_problem *h) {
+  const int q = sizeof(R) == 8 ? 1 : 0;
+  const int nt = h->n_t(), P = h->dir[0].p;
+  const long long Ns = h->N_s;
+  h->ts_seg[q] = 0;
+  if (h->ts_S[q] < 2 || g_ts_mode == 1) return STST_OK;
+  if (g_ts_mode == 2) {
+    h->ts_seg[q] = 1;
+    return STST_OK;
+  }
+  if (g_tune_enabled != 1) {
+    h->ts_seg[q] = grid_for(Ns, 32) < 2 * 152 ? 1 : 0;
+    return STST_OK;
+  }
+  const auto key = std::make_tuple((int)sizeof(R), nt, Ns, P);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_ts_cache.find(key);
+    if (it != g_ts_cache.end()) {
+      h->ts_seg[q] = it->second;
+      return STST_OK;
+    }
+  }
+  cudaStream_t st = h->stream;
+  cudaEvent_t e0, e1;
+  STST_CUDA(cudaEventCreate(&e0));
+  STST_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int choice = 0, status = STST_OK;
+  for (int v = 0; v < 2 && status == STST_OK; ++v) {
+    h->ts_seg[q] = v;
+    for (int w = 0; w < 2 && status == STST_OK; ++w) status = time_solve<R>(h, h->w_t1, nullptr, st);
+    cudaEventRecord(e0, st);
+    for (int w = 0; w < 5 && status == STST_OK; ++w) status = time_solve<R>(h, h->w_t1, nullptr, st);
+    cudaEventRecord(e1, st);
+    const cudaError_t es = cudaEventSynchronize(e1);
+    if (es != cudaSuccess) {
+      stst_last_cuda = es;
+      status = STST_ERR_CUDA;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (status == STST_OK && ms < best) {
+      best = ms;
+      choice = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  STST_TRY(status);
+  h->ts_seg[q] = choice;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_ts_cache[key] = choice;
+  }
+  return STST_OK;
+}
+
+int tune_modeprod(stst_problem *h) {
+  if (h->tuned) return STST_OK;
+  STST_TRY(tune_mp_tiles(h));
+  STST_TRY(tune_ts<float>(h));
+  if (h->prec_mode == STST_PREC_FP64) STST_TRY(tune_ts<double>(h));
+  h->tuned = 1;
+  return STST_OK;
 }

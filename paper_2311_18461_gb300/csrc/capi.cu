@@ -411,6 +411,10 @@ void destroy_all(stst_problem *h) {
   cudaFree(h->Hd);
   cudaFree(h->Hg32);
   cudaFree(h->Hd32);
+  for (int q = 0; q < 2; ++q) {
+    cudaFree(h->Tf[q]);
+    cudaFree(h->Tb[q]);
+  }
   cudaFree(h->flags);
   double *ws[] = {h->w_x, h->w_r, h->w_z, h->w_zold, h->w_p, h->w_q, h->w_f, h->w_t1, h->w_t2};
   for (double *w : ws) cudaFree(w);
@@ -501,6 +505,15 @@ int create_impl(stst_problem *h, int d, const int *n_el, const int *p, double T,
   STST_TRY(alloc((void **)&h->Hd, sizeof(double) * nt * h->N_s));
   STST_TRY(alloc(&h->Hg32, sizeof(float2) * nt * Pt * h->N_s));
   STST_TRY(alloc((void **)&h->Hd32, sizeof(float) * nt * h->N_s));
+  for (int q = 0; q < 2; ++q) {  // transfer matrices of the segmented time solves (FP64 ones in FP64 mode)
+    h->ts_S[q] = 0;
+    if (q == 1 && prec_mode != STST_PREC_FP64) continue;
+    ts_segments((int)nt, (int)Pt, q ? sizeof(double) : sizeof(float), &h->ts_S[q], &h->ts_L[q]);
+    if (h->ts_S[q] < 2) continue;
+    const size_t cnt = (size_t)h->ts_S[q] * Pt * Pt * h->N_s * (q ? sizeof(double2) : sizeof(float2));
+    STST_TRY(alloc(&h->Tf[q], cnt));
+    STST_TRY(alloc(&h->Tb[q], cnt));
+  }
   const size_t vb = sizeof(double2) * (size_t)h->N_dof;
   double **ws[] = {&h->w_x, &h->w_r, &h->w_z, &h->w_zold, &h->w_p, &h->w_q, &h->w_f, &h->w_t1, &h->w_t2};
   for (double **w : ws) STST_TRY(alloc((void **)w, vb));
@@ -756,6 +769,22 @@ int stst_set_autotune(int mode) {
   const int rpt = mode / 10, cpt = mode % 10;
   if (mode != 0 && mode != 1 && !(rpt >= 1 && rpt <= 4 && (cpt == 2 || cpt == 4))) return STST_ERR_ARG;
   g_tune_enabled = mode;
+  return STST_OK;
+}
+
+int stst_set_time_solver(int mode) {
+  if (mode < 0 || mode > 2) return STST_ERR_ARG;
+  g_ts_mode = mode;
+  return STST_OK;
+}
+
+int stst_time_solver_info(stst_handle h, int precision, int *segments, int *segment_len, int *segmented) {
+  STST_TRY(check(h));
+  if (precision != 0 && precision != 1) return STST_ERR_ARG;
+  const int q = precision == 0 ? 1 : 0;  // STST_PREC_FP64 uses the FP64 factors
+  if (segments) *segments = h->ts_S[q];
+  if (segment_len) *segment_len = h->ts_L[q];
+  if (segmented) *segmented = h->ts_seg[q];
   return STST_OK;
 }
 

@@ -133,6 +133,10 @@ struct stst_problem {
   double *Hd;                      // FP64 inverse diagonals n_t x N_s
   void *Hg32;                      // FP32 factors
   float *Hd32;
+  // parallel-in-time time solves, [0] FP32 factors, [1] FP64 factors: segments, segment length,
+  // forward / backward transfer matrices, and whether the segmented kernel is used
+  int ts_S[2], ts_L[2], ts_seg[2];
+  void *Tf[2], *Tb[2];
   int *flags;                      // device status flags: [0] factorization pivots, [1] bounded waits
   int *flags_host;                 // pinned copy
 
@@ -208,12 +212,17 @@ int ir_run(stst_problem *h, const double *rhs, double *x, double tol, int maxit,
 
 int grid_for(long long n, int block);
 int fd_partials_count(stst_problem *h);
+void ts_segments(int nt, int P, size_t rsize, int *S, int *L);
+template <typename R>
+int launch_time_transfer(const void *G, const R *D, int nt, long long Ns, int P, int S, int L, void *Tf, void *Tb,
+                         cudaStream_t s);
 // Opts kernel `kern` into `bytes` of dynamic shared memory (with its static shared memory the default
 // limit is 48 KB in total); remembers the largest size set per kernel, so repeated launches skip the call.
 int ensure_dyn_smem(const void *kern, size_t bytes);
 MpCfg modeprod_default(int n);
 int tune_modeprod(stst_problem *h);  // times the mode-product tiles once per shape (outside graph capture)
 extern int g_tune_enabled;
+extern int g_ts_mode;
 
 // tensor-core mode products (modeprod_tc.cu)
 int launch_u_to_bf16(const double *U, int n, __nv_bfloat16 *out, cudaStream_t s);

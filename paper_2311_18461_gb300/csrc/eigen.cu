@@ -637,6 +637,12 @@ int fd_setup_launch(stst_problem *h) {
     default: return STST_ERR_ARG;
   }
   STST_CUDA(cudaGetLastError());
+  // transfer matrices of the segmented (parallel-in-time) time solves
+  STST_TRY(launch_time_transfer<float>(h->Hg32, h->Hd32, h->n_t(), h->N_s, h->dir[0].p, h->ts_S[0], h->ts_L[0],
+                                       h->Tf[0], h->Tb[0], st));
+  if (f64)
+    STST_TRY(launch_time_transfer<double>(h->Hg, h->Hd, h->n_t(), h->N_s, h->dir[0].p, h->ts_S[1], h->ts_L[1],
+                                          h->Tf[1], h->Tb[1], st));
   return STST_OK;
 }
 

@@ -289,6 +289,7 @@ def test_mode_product_tiles_agree_bitwise(prec):
     import torch
     import paper_2311_18461_gb300 as P
     outs = {}
+    P.stst_set_time_solver(1)  # the same time solve for every tile
     try:
         for mode in (0, 12, 14, 22, 24, 32, 34, 42, 44, 1):
             P.stst_set_autotune(mode)
@@ -300,7 +301,35 @@ def test_mode_product_tiles_agree_bitwise(prec):
             prob.close()
     finally:
         P.stst_set_autotune(1)
+        P.stst_set_time_solver(0)
     ref = outs[0][0]
     for mode, (o, tiles) in outs.items():
         assert np.array_equal(o, ref), (mode, tiles)
     assert outs[12][1][0][:2] == (16, 32) and outs[44][1][1][:2] == (32, 128)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 1e-4)])
+@pytest.mark.parametrize("nt_el,pt", [(3, 1), (8, 2), (33, 3), (64, 3), (40, 4), (97, 2)])
+def test_segmented_time_solve_matches_sequential(prec, tol, nt_el, pt):
+    """Parallel-in-time (segmented) and sequential time solves agree up to rounding (the segmented form
+    reorders the recurrence: zero-start runs plus transfer matrices applied to the carried states)."""
+    import torch
+    import paper_2311_18461_gb300 as P
+    out = {}
+    try:
+        for mode in (1, 2):
+            P.stst_set_time_solver(mode)
+            prob = P.Problem(2, [nt_el, 9, 14], [pt, 3, 2], prec_mode=prec)
+            prob.build_fd()
+            info = P.stst_time_solver_info(prob.h, prec)
+            r = torch.tensor(np.random.default_rng(nt_el).standard_normal(2 * prob.n_dof),
+                             device="cuda").view(torch.complex128)
+            out[mode] = (prob.apply_prec(r).cpu().numpy(), info)
+            prob.close()
+    finally:
+        P.stst_set_time_solver(0)
+    assert out[1][1][2] == 0
+    if out[2][1][0] >= 2:
+        assert out[2][1][2] == 1
+    assert rel_err(out[2][0], out[1][0]) < tol, (out[2][1], rel_err(out[2][0], out[1][0]))
