@@ -117,21 +117,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def source_hash(files):
-    """Hash of the CUDA sources a kernel is built from (traffic figures are void once they change)."""
-    h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_2311_18461_gb300", "csrc")
-    for name in sorted(files):
-        h.update(open(os.path.join(csrc, name), "rb").read())
-    return h.hexdigest()[:16]
+def source_hash(span):
+    """Hash of a kernel's own source text (from `begin` up to `end` in `file`): traffic figures taken
+    with ncu are void once the kernel they describe has changed."""
+    path = os.path.join(ROOT, "paper_2311_18461_gb300", "csrc", span["file"])
+    text = open(path).read()
+    i = text.index(span["begin"])
+    j = text.index(span["end"], i)
+    return hashlib.sha256(text[i:j].encode()).hexdigest()[:16]
 
 
 def traffic_for(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if taken on the kernel's current sources."""
+    """DRAM bytes per launch from the committed ncu summary, if taken on the kernel's current source."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path)).get("kernels", {}).get(kernel)
-        if not rec or rec.get("source_hash") != source_hash(rec["sources"]):
+        if not rec or rec.get("source_hash") != source_hash(rec["span"]):
             return None
         return rec.get("dram_bytes_per_launch")
     except Exception:

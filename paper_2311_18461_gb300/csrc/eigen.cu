@@ -619,6 +619,7 @@ int fd_setup_launch(stst_problem *h) {
   size_t hsm = 3 * (size_t)h->n_t() * (2 * h->dir[0].p + 1) * (f64 ? sizeof(double) : sizeof(float));
   const int stage = hsm <= 48 * 1024;  // otherwise the bands are read from global memory
   if (!stage) hsm = 0;
+  {
   STST_PROF(f64 ? "hfactor_f64" : "hfactor_f32", st);
   switch (h->dir[0].p) {
 #define CASE(PP)                                                                                                 \
@@ -637,6 +638,7 @@ int fd_setup_launch(stst_problem *h) {
     default: return STST_ERR_ARG;
   }
   STST_CUDA(cudaGetLastError());
+  }  // profiler scopes do not nest: the hfactor record ends here
   // transfer matrices of the segmented (parallel-in-time) time solves
   STST_TRY(launch_time_transfer<float>(h->Hg32, h->Hd32, h->n_t(), h->N_s, h->dir[0].p, h->ts_S[0], h->ts_L[0],
                                        h->Tf[0], h->Tb[0], st));
