@@ -22,7 +22,10 @@ def _restricted_basis(disc, l):
     length = disc.T if l == 0 else 1.0
     D = basis_all(open_uniform_knots(disc.p[l], disc.n_el[l]), disc.p[l], x / length, nder=2)
     D = D / np.array([1.0, length, length ** 2])[:, None, None]
-    D = D[:, :, 1:] if l == 0 else D[:, :, 1:-1]
+    if l == 0:
+        D = D[:, :, :-1] if disc.formulation == "uw" else D[:, :, 1:]
+    else:
+        D = D[:, :, 1:-1]
     return x, w, D
 
 

@@ -39,9 +39,10 @@ def assemble_1d(p, n_el, length=1.0, nq=None, weight=None):
     return dict(M=M, L=L, J=J, K=K, K2=K2)
 
 
-def restrict_time(A):
-    """Drop the first basis function (the only one nonzero at t = 0): n_t = m_t - 1 (Sec. 3.2)."""
-    return A[1:, 1:]
+def restrict_time(A, formulation="ls"):
+    """Least squares: drop the first basis function (the only one nonzero at t = 0), n_t = m_t - 1
+    (Sec. 3.2). Ultraweak: drop the last one (the space with final conditions at T, Sec. 4.4)."""
+    return A[:-1, :-1] if formulation == "uw" else A[1:, 1:]
 
 
 def restrict_space(A):

@@ -31,7 +31,10 @@ def tables(disc, l, pts=None, full=False):
     D = basis_all(open_uniform_knots(disc.p[l], disc.n_el[l]), disc.p[l], x / length, nder=2)
     D = D / np.array([1.0, length, length ** 2])[:, None, None]
     if not full:
-        D = D[:, :, 1:] if l == 0 else D[:, :, 1:-1]
+        if l == 0:
+            D = D[:, :, :-1] if disc.formulation == "uw" else D[:, :, 1:]
+        else:
+            D = D[:, :, 1:-1]
     return D
 
 
@@ -170,3 +173,68 @@ def embed_solution(disc, ubar, XD=None, c=None):
     if c is not None:
         U[tuple([slice(1, -1)] * d + [0])] += c
     return U
+
+
+def spatial_load(disc, u0_fn):
+    """g_j = (u0, B_j)_{L2(Omega)} on the Dirichlet-reduced spatial basis (tensor Gauss rule)."""
+    d = disc.d
+    co = grid_coords(disc, time=False)
+    G = u0_fn(*co) * grid_weights(disc, time=False)
+    for l in range(1, d + 1):
+        G = mode_product(G, tables(disc, l)[0].T, d - l)
+    return G
+
+
+def rhs_ultraweak(disc, f_fn=None, u0_fn=None):
+    """Right-hand side of the ultraweak method (Sec. 4.4): b_i = (f, B_i) + i (u0, B_i(., 0)).
+
+    The basis functions B_i = b_k(t) B_j(x) span the space with final conditions; the only time
+    function nonzero at t = 0 is the first one, b_0(0) = 1, so the initial term sits on time index 0.
+    With u_h = S z_h, the method reads (S z_h, S B_i) = b_i (the matrix of the least-squares form on
+    this space)."""
+    assert disc.formulation == "uw"
+    d = disc.d
+    out = np.zeros(disc.shape, dtype=complex)
+    if f_fn is not None:
+        co = grid_coords(disc)
+        F = f_fn(*co) * grid_weights(disc)
+        F = np.broadcast_to(F, tuple(len(disc.quad(l)[0]) for l in range(d, 0, -1)) + (len(disc.quad(0)[0]),))
+        Z = mode_product(F, tables(disc, 0)[0].T, d)
+        for l in range(1, d + 1):
+            Z = mode_product(Z, tables(disc, l)[0].T, d - l)
+        out = out + Z
+    if u0_fn is not None:
+        out[..., 0] += 1j * spatial_load(disc, u0_fn)
+    return out.ravel()
+
+
+def apply_S_on_grid(disc, z, V=None, extra=0):
+    """Values of S z_h = i d_t z_h - nu Delta z_h (+ V z_h) on a tensor Gauss grid with `extra` more
+    points per element than the library's rule, and that grid's points and weights (for L2(Q) errors of
+    the ultraweak solution u_h = S z_h)."""
+    from .bspline import element_quadrature
+    d, nu = disc.d, disc.nu
+    pts, wts, tabs = [], [], []
+    for l in range(d + 1):
+        length = disc.T if l == 0 else 1.0
+        x, w = element_quadrature(disc.n_el[l], disc.nq[l] + extra, length)
+        pts.append(x)
+        wts.append(w)
+        tabs.append(tables(disc, l, pts=x))
+    Z = np.asarray(z, dtype=complex).reshape(disc.shape)
+
+    def ev(tder, sders):
+        Y = mode_product(Z, tabs[0][tder], d)
+        for l in range(1, d + 1):
+            Y = mode_product(Y, tabs[l][sders[l - 1]], d - l)
+        return Y
+
+    S = 1j * ev(1, [0] * d)
+    for l in range(d):
+        ders = [0] * d
+        ders[l] = 2
+        S = S - nu * ev(0, ders)
+    if V is not None:
+        co = np.meshgrid(*[pts[l] for l in range(d, 0, -1)], indexing="ij")
+        S = S + V(*co[::-1])[..., None] * ev(0, [0] * d)
+    return S, pts, wts

@@ -32,9 +32,12 @@ class Discretization:
 
     n_el: [n_el_t, n_el_1, ..., n_el_d]; p: [p_t, p_s] or [p_t, p_1, ..., p_d].
     potential: None, or a list of rank-one terms, each a list of d callables v_{r,l}(x_l).
+    formulation: "ls" (the least-squares method: time basis without its first function) or "uw"
+    (the ultraweak method of Sec. 4.4: the same matrix on the time basis without its last function,
+    i.e. the space with final conditions; the unknowns z give u_h = S z_h).
     """
 
-    def __init__(self, n_el, p, T=1.0, nu=1.0, potential=None):
+    def __init__(self, n_el, p, T=1.0, nu=1.0, potential=None, formulation="ls"):
         self.d = len(n_el) - 1
         self.n_el = list(n_el)
         if len(p) == 2 and self.d != 1:
@@ -43,6 +46,7 @@ class Discretization:
         self.T = float(T)
         self.nu = float(nu)
         self.potential = potential
+        self.formulation = formulation
         self.nq = [default_nq(q) for q in self.p]
         lengths = [self.T] + [1.0] * self.d
         self.full = [assemble_1d(self.p[l], self.n_el[l], lengths[l]) for l in range(self.d + 1)]
@@ -51,9 +55,9 @@ class Discretization:
         self.N_s = int(np.prod(self.n[1:]))
         self.N_dof = self.N_s * self.n[0]
         Ft = self.full[0]
-        self.Lt = restrict_time(Ft["L"])
-        self.Mt = restrict_time(Ft["M"])
-        self.Wt = 1j * restrict_time(Ft["K"])
+        self.Lt = restrict_time(Ft["L"], formulation)
+        self.Mt = restrict_time(Ft["M"], formulation)
+        self.Wt = 1j * restrict_time(Ft["K"], formulation)
         self.Wsym = self.Wt + self.Wt.conj().T
         self.sp = [None] + [{k: restrict_space(v) for k, v in self.full[l].items()} for l in range(1, self.d + 1)]
 

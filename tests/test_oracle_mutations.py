@@ -97,3 +97,19 @@ def test_flipped_residual_sign_is_caught():
 
 def test_missing_sample_weights_are_caught():
     assert _fd_mismatch(_mutated_loss_grad("dz = 2.0 * w[:, None] * R / B", "dz = 2.0 * R / B")) > 1e-2
+
+
+def test_ultraweak_initial_term_with_flipped_sign_is_caught():
+    from oracle import rhs as orhs
+    from oracle import direct as odirect
+    nu = 1.3
+    u = lambda t, x: (1 + t ** 2) * x ** 2 * (1 - x) + 0j
+    f = lambda t, x: 2j * t * x ** 2 * (1 - x) - nu * (1 + t ** 2) * (2 - 6 * x)
+    u0 = lambda x: x ** 2 * (1 - x) + 0j
+    disc = Discretization([3, 4], [2, 3], T=0.7, nu=nu, formulation="uw")
+    G, w, pts = odirect.sb_matrix(disc)
+    ref = (G.conj().T * w) @ np.array([u(*q) for q in pts])
+    good = orhs.rhs_ultraweak(disc, f, u0)
+    planted = orhs.rhs_ultraweak(disc, f, None) - (orhs.rhs_ultraweak(disc, None, u0))
+    assert np.abs(good - ref).max() <= 1e-11 * np.abs(ref).max()
+    assert np.abs(planted - ref).max() > 1e-2 * np.abs(ref).max()
