@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--config", default="c2")
     ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--solver", default="pcg", choices=["pcg", "ir"])
+    ap.add_argument("--formulation", default="ls", choices=["ls", "uw"],
+                    help="least squares (Sec. 4.3) or ultraweak (Sec. 4.4)")
     ap.add_argument("--inner-tol", type=float, default=1e-4)
     ap.add_argument("--batch", type=int, default=128, help="number of problems of the c4 workload")
     ap.add_argument("--train", type=int, default=10000, help="training solves of the c5 workload")
@@ -151,14 +153,14 @@ def sample_1d(prob, fn, l):
     return np.asarray(fn(x)) * np.ones_like(x)
 
 
-def build_problem(cfg, V, u0, prec, stream):
+def build_problem(cfg, V, u0, prec, stream, formulation="ls"):
     import numpy as np
     import torch
     import paper_2311_18461_gb300 as S
     d = cfg["d"]
     prob = S.Problem(d, cfg["n_el"], [cfg["p"]] * (d + 1), T=cfg["T"], nu=cfg["nu"],
                      prec_mode={"fp64": S.STST_PREC_FP64, "fp32": S.STST_PREC_FP32, "bf16": S.STST_PREC_BF16}[prec],
-                     stream=stream)
+                     stream=stream, formulation={"ls": S.STST_FORM_LS, "uw": S.STST_FORM_UW}[formulation])
     if V:
         cols = [sample_1d(prob, term[l - 1], l) for term in V for l in range(1, d + 1)]
         prob.set_potential(torch.tensor(np.concatenate(cols), dtype=torch.float64, device="cuda"), len(V))
@@ -468,7 +470,7 @@ def run_ours(args):
     cfg, V, u0 = workload(args.config)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        prob, b = build_problem(cfg, V, u0, args.prec, stream)
+        prob, b = build_problem(cfg, V, u0, args.prec, stream, args.formulation)
     tol = 1e-8
     x = prob.vec()
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > 129 MB L2
@@ -637,7 +639,8 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": {"fp64": "f64", "fp32": "f64+f32", "bf16": "f64+f32+bf16"}[args.prec],
         "data": "synthetic",
-        "config": {"workload": workload_name(args.config, cfg, tol),
+        "config": {"workload": workload_name(args.config, cfg, tol) + (", ultraweak formulation (Sec. 4.4)"
+                                                                       if args.formulation == "uw" else ""),
                    "n_dof": n_dof, "preconditioner": args.prec, "solver": args.solver,
                    "pcg_iterations": statistics.median(iters),
                    "step": "build_fd (setup) + pcg_solve from x0 = 0", "l2": "flushed (512 MB write) before each step",
@@ -662,7 +665,7 @@ def run_ours(args):
                           "seconds": 4.7142, "iterations": 8},
     }
     if rank == 0 and world == 1:
-        out["cpu_baseline"] = cpu_baseline(args.config, iters_full=None)
+        out["cpu_baseline"] = cpu_baseline(args.config, iters_full=None, formulation=args.formulation)
     if rank == 0:
         print(json.dumps(out), flush=True)
     prob.close()
@@ -678,7 +681,7 @@ def _oracle_threads():
         return os.cpu_count()
 
 
-def cpu_baseline(cfg_name, iters_full=None, sample_iters=2):
+def cpu_baseline(cfg_name, iters_full=None, sample_iters=2, formulation="ls"):
     """The oracle timed on this host: setup + `sample_iters` PCG iterations, extrapolated to the full count."""
     import numpy as np
     from inputs import CONFIGS, potential, initial_factors, product_fn
@@ -686,8 +689,12 @@ def cpu_baseline(cfg_name, iters_full=None, sample_iters=2):
     from oracle.system import Discretization
     cfg = CONFIGS[cfg_name]
     d = cfg["d"]
-    disc = Discretization(cfg["n_el"], [cfg["p"]] * (d + 1), T=cfg["T"], nu=cfg["nu"], potential=potential(cfg))
-    b, _ = rhs.rhs_initial(disc, None, product_fn(initial_factors(cfg)))
+    disc = Discretization(cfg["n_el"], [cfg["p"]] * (d + 1), T=cfg["T"], nu=cfg["nu"], potential=potential(cfg),
+                          formulation=formulation)
+    if formulation == "uw":
+        b = rhs.rhs_ultraweak(disc, None, product_fn(initial_factors(cfg)))
+    else:
+        b, _ = rhs.rhs_initial(disc, None, product_fn(initial_factors(cfg)))
     terms = disc.terms()
     if iters_full is None:
         F = fd.FastDiagonalization(disc)
@@ -715,8 +722,12 @@ def run_reference(args):
     from oracle.system import Discretization
     cfg = CONFIGS[args.config]
     d = cfg["d"]
-    disc = Discretization(cfg["n_el"], [cfg["p"]] * (d + 1), T=cfg["T"], nu=cfg["nu"], potential=potential(cfg))
-    b, _ = rhs.rhs_initial(disc, None, product_fn(initial_factors(cfg)))
+    disc = Discretization(cfg["n_el"], [cfg["p"]] * (d + 1), T=cfg["T"], nu=cfg["nu"], potential=potential(cfg),
+                          formulation=formulation)
+    if formulation == "uw":
+        b = rhs.rhs_ultraweak(disc, None, product_fn(initial_factors(cfg)))
+    else:
+        b, _ = rhs.rhs_initial(disc, None, product_fn(initial_factors(cfg)))
     F = fd.FastDiagonalization(disc)
     _, iters_full, _, _ = pcg.pcg(disc.apply, F.apply, b, tol=1e-8, maxit=200)
     vals = []

@@ -57,6 +57,16 @@ enum {
   STST_PREC_BF16 = 2  /* mode products on tensor cores, BF16 operands, FP32 accumulate */
 };
 
+/* Formulation (stst_create2). STST_FORM_LS: the least-squares method (Sec. 4.3): unknowns on the time
+ * basis without its first function, the initial datum enters by lifting. STST_FORM_UW: the ultraweak
+ * method (Sec. 4.4, Eq. uw-discrete-system): the same matrix (S B_j, S B_i) on the time basis without
+ * its last function (final conditions at T); the initial datum enters the right-hand side and the
+ * discrete solution is u_h = S z_h for the computed z_h. */
+enum {
+  STST_FORM_LS = 0,
+  STST_FORM_UW = 1
+};
+
 typedef struct stst_problem *stst_handle;
 
 /*
@@ -71,7 +81,11 @@ typedef struct stst_problem *stst_handle;
  *   stream     cudaStream_t used by every call of the handle (NULL: legacy default stream)
  * Assembles the 1D matrices on the device (Eq. time_mat, Eq. space_mat).
  * Allocates the handle's device memory. Errors: ERR_ARG, ERR_OOM, ERR_CUDA.
+ * stst_create is stst_create2 with formulation STST_FORM_LS; every other call works for both
+ * formulations (stst_rhs computes each one's right-hand side).
  */
+int stst_create2(stst_handle *h, int d, const int *n_el, const int *p, double T, double nu, int prec_mode,
+                 int formulation, void *stream);
 int stst_create(stst_handle *h, int d, const int *n_el, const int *p, double T, double nu, int prec_mode,
                 void *stream);
 
@@ -142,6 +156,9 @@ int stst_apply_prec(stst_handle h, const double *r, double *s);
  *   rhs    device, N_dof complex (output)
  *   c0     NULL or device, N_s complex: receives c (the lifted initial datum;
  *          the discrete solution is u_h = u_bar + b_1(t) sum_j c_j B_j(x)).
+ * For STST_FORM_UW handles (Sec. 4.4): rhs_i = int f conj(B_i) + i (u0, B_i(., 0)); the initial term
+ * sits on time index 0 (the only time function nonzero at t = 0) and nothing is lifted; c0 still
+ * receives M_s^{-1} (u0, B_j). The potential does not enter this right-hand side.
  */
 int stst_rhs(stst_handle h, const double *f_qp, const double *u0_qp, double *rhs, double *c0);
 

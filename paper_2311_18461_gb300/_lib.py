@@ -11,6 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 library_path = os.path.join(HERE, "libstst.so")
 
 STST_PREC_FP64, STST_PREC_FP32, STST_PREC_BF16 = 0, 1, 2
+STST_FORM_LS, STST_FORM_UW = 0, 1
 STATUS = {0: "OK", 1: "NOT_CONVERGED", 2: "BREAKDOWN", 3: "NOT_HPD", 4: "TIMEOUT", -1: "ERR_ARG",
           -2: "ERR_HANDLE", -3: "ERR_OOM", -4: "ERR_CUDA", -5: "ERR_STATE"}
 
@@ -38,6 +39,7 @@ def lib():
         IP, DP = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
         sig = {
             "stst_create": [ctypes.POINTER(P), I, IP, IP, D, D, I, P],
+            "stst_create2": [ctypes.POINTER(P), I, IP, IP, D, D, I, I, P],
             "stst_destroy": [P],
             "stst_sizes": [P, ctypes.POINTER(LL), IP],
             "stst_quadrature_points": [P, I, P],
@@ -134,6 +136,15 @@ def stst_create(d, n_el, p, T=1.0, nu=1.0, prec_mode=STST_PREC_FP64, stream=None
     pp = (ctypes.c_int * (d + 1))(*p)
     _chk(lib().stst_create(ctypes.byref(h), d, ne, pp, float(T), float(nu), int(prec_mode), _stream_ptr(stream)),
          "stst_create")
+    return h
+
+
+def stst_create2(d, n_el, p, T=1.0, nu=1.0, prec_mode=STST_PREC_FP64, formulation=STST_FORM_LS, stream=None):
+    ne = (ctypes.c_int * (d + 1))(*[int(v) for v in n_el])
+    pp = (ctypes.c_int * (d + 1))(*[int(v) for v in p])
+    h = ctypes.c_void_p()
+    _chk(lib().stst_create2(ctypes.byref(h), int(d), ne, pp, float(T), float(nu), int(prec_mode), int(formulation),
+                            _stream_ptr(stream)), "stst_create2")
     return h
 
 
@@ -351,7 +362,8 @@ def stst_pcg_solve_guarded(h, rhs, x, tol, maxit):
 class Problem:
     """Owns a handle; convenience around the C calls (allocation of device vectors via torch)."""
 
-    def __init__(self, d, n_el, p, T=1.0, nu=1.0, prec_mode=STST_PREC_FP64, stream=None, device="cuda"):
+    def __init__(self, d, n_el, p, T=1.0, nu=1.0, prec_mode=STST_PREC_FP64, stream=None, device="cuda",
+                 formulation=STST_FORM_LS):
         import torch
         self.torch = torch
         self.d = d
@@ -360,7 +372,8 @@ class Problem:
         self.p = list(p)
         self.n_el = list(n_el)
         self.device = device
-        self.h = stst_create(d, n_el, p, T, nu, prec_mode, stream)
+        self.formulation = formulation
+        self.h = stst_create2(d, n_el, p, T, nu, prec_mode, formulation, stream)
         self.n_dof, self.n = stst_sizes(self.h, d)
         self.N_s = self.n_dof // self.n[0]
 

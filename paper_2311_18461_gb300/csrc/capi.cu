@@ -437,7 +437,8 @@ void destroy_all(stst_problem *h) {
   delete h;
 }
 
-int create_impl(stst_problem *h, int d, const int *n_el, const int *p, double T, double nu, int prec_mode) {
+int create_impl(stst_problem *h, int d, const int *n_el, const int *p, double T, double nu, int prec_mode,
+                int formulation) {
   cudaStream_t st = h->stream;
   for (int l = 0; l <= d; ++l) {
     DirInfo &D = h->dir[l];
@@ -447,8 +448,11 @@ int create_impl(stst_problem *h, int d, const int *n_el, const int *p, double T,
     D.m = n_el[l] + p[l];
     D.n = (l == 0) ? D.m - 1 : D.m - 2;
     D.len = (l == 0) ? T : 1.0;
-    D.off = 1;
+    // time: the least-squares space drops the first function (initial condition), the ultraweak
+    // one the last (final condition); space: both ends (Dirichlet)
+    D.off = (l == 0 && formulation == STST_FORM_UW) ? 0 : 1;
   }
+  h->formulation = formulation;
   h->d = d;
   h->T = T;
   h->nu = nu;
@@ -576,7 +580,13 @@ const char *stst_strerror(int s) {
 
 int stst_create(stst_handle *out, int d, const int *n_el, const int *p, double T, double nu, int prec_mode,
                 void *stream) {
+  return stst_create2(out, d, n_el, p, T, nu, prec_mode, STST_FORM_LS, stream);
+}
+
+int stst_create2(stst_handle *out, int d, const int *n_el, const int *p, double T, double nu, int prec_mode,
+                 int formulation, void *stream) {
   if (!out || !n_el || !p) return STST_ERR_ARG;
+  if (formulation != STST_FORM_LS && formulation != STST_FORM_UW) return STST_ERR_ARG;
   *out = nullptr;
   if (d < 1 || d > STST_MAXD) return STST_ERR_ARG;
   if (!(T > 0.0) || !(nu > 0.0) || !std::isfinite(T) || !std::isfinite(nu)) return STST_ERR_ARG;
@@ -603,7 +613,7 @@ int stst_create(stst_handle *out, int d, const int *n_el, const int *p, double T
     h->own_stream = 1;
   }
   for (int l = 1; l <= d; ++l) h->mp_cfg[l] = modeprod_default(n_el[l] + p[l] - 2);
-  int s = create_impl(h, d, n_el, p, T, nu, prec_mode);
+  int s = create_impl(h, d, n_el, p, T, nu, prec_mode, formulation);
   if (s != STST_OK) {
     destroy_all(h);
     return s;

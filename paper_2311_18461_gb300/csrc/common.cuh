@@ -97,6 +97,7 @@ struct stst_problem {
   DirInfo dir[STST_MAXD + 1];
   double T, nu;
   int prec_mode;
+  int formulation;                 // STST_FORM_LS (least squares) or STST_FORM_UW (ultraweak)
   cudaStream_t stream;
   int own_stream;                  // stream created by the handle (caller passed NULL)
   long long N_s, N_dof;

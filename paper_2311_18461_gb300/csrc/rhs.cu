@@ -1,5 +1,6 @@
 // Right-hand side of the reduced system (Sec. 4.3) and the lifting of the initial datum (Sec. 2.2):
-//   rhs_i = int f conj(S_V B_i) - sum_j A_full(b_1 B_j, S_V B_i) c_j,  c = M_s^{-1} (u0, B_j).
+//   rhs_i = int f conj(S_V B_i) - sum_j A_full(b_1 B_j, S_V B_i) c_j,  c = M_s^{-1} (u0, B_j);
+// for the ultraweak formulation (Sec. 4.4): rhs_i = int f conj(B_i) + i (u0, B_i(., 0)).
 // Integrals are tensor Gauss sums evaluated as mode-by-mode contractions of the sampled data with
 // the basis tables; M_s^{-1} is applied mode by mode with the banded Cholesky factor of M_l; the
 // lifting is the Kronecker operator applied to c placed on the first (removed) time function.
@@ -35,6 +36,17 @@ __global__ void k_contract(const TI *__restrict__ in, double2 *__restrict__ out,
     ry += prev.y;
   }
   out[idx] = make_double2(rx, ry);
+}
+
+// Ultraweak initial term: rhs[(t = 0, j)] += i g_j (time fastest: index j n_t)
+__global__ void k_add_initial_uw(double2 *__restrict__ rhs, const double2 *__restrict__ g, int nt, long long Ns) {
+  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (j >= Ns) return;
+  double2 r = rhs[j * nt];
+  const double2 v = g[j];
+  r.x -= v.y;
+  r.y += v.x;
+  rhs[j * nt] = r;
 }
 
 // Solve M_l y = g along mode l in place (lines of length n with stride inner), banded Cholesky.
@@ -127,21 +139,27 @@ int rhs_compute(stst_problem *h, const double *f_qp, const double *u0_qp, double
     STST_CUDA(cudaMallocAsync(&W1, sizeof(double2) * sz, st));
     STST_CUDA(cudaMallocAsync(&W2, sizeof(double2) * sz, st));
     const long long Qs = szF / Q[0];
+    const bool uw = h->formulation == STST_FORM_UW;  // ultraweak: plain load int f conj(B_i)
     // time contractions (mode 0: inner 1, outer prod Q_l): T1 = -i int f b'_t, T0 = int f b_t
-    STST_TRY(contract(h, 0, (const double2 *)f_qp, T1, 1, Qs, 1, 0.0, -1.0, 0));
+    if (!uw) STST_TRY(contract(h, 0, (const double2 *)f_qp, T1, 1, Qs, 1, 0.0, -1.0, 0));
     STST_TRY(contract(h, 0, (const double2 *)f_qp, T0, 1, Qs, 0, 1.0, 0.0, 0));
     // spatial contractions. term list: (src, ders per mode, scale)
     struct Term { double2 *src; int der[STST_MAXD + 1]; double s; };
     std::vector<Term> terms;
-    Term t1 = {T1, {0, 0, 0, 0}, 1.0};
-    terms.push_back(t1);
-    for (int l = 1; l <= d; ++l) {
-      Term t = {T0, {0, 0, 0, 0}, -h->nu};
-      t.der[l] = 2;
-      terms.push_back(t);
+    if (uw) {
+      Term t0 = {T0, {0, 0, 0, 0}, 1.0};
+      terms.push_back(t0);
+    } else {
+      Term t1 = {T1, {0, 0, 0, 0}, 1.0};
+      terms.push_back(t1);
+      for (int l = 1; l <= d; ++l) {
+        Term t = {T0, {0, 0, 0, 0}, -h->nu};
+        t.der[l] = 2;
+        terms.push_back(t);
+      }
     }
     double2 *T0V = nullptr;
-    if (h->pot_rank > 0) {
+    if (h->pot_rank > 0 && !uw) {
       STST_CUDA(cudaMallocAsync(&FV, sizeof(double2) * szF, st));
       STST_CUDA(cudaMallocAsync(&T0V, sizeof(double2) * sz, st));
       k_mul_potential<<<grid_for(szF, 256), 256, 0, st>>>((const double2 *)f_qp, FV, Q[0], d, Q[1],
@@ -198,6 +216,10 @@ int rhs_compute(stst_problem *h, const double *f_qp, const double *u0_qp, double
       src = dst;
       cur ^= 1;
     }
+    if (h->formulation == STST_FORM_UW) {  // rhs += i (u0, B_j) on time index 0
+      k_add_initial_uw<<<grid_for(h->N_s, 256), 256, 0, st>>>((double2 *)rhs, C, n[0], h->N_s);
+      STST_CUDA(cudaGetLastError());
+    }
     for (int l = 1; l <= d; ++l) {
       long long inner = 1, outer = 1;
       for (int k = 1; k < l; ++k) inner *= n[k];
@@ -206,8 +228,9 @@ int rhs_compute(stst_problem *h, const double *f_qp, const double *u0_qp, double
       STST_CUDA(cudaGetLastError());
     }
     if (c0) STST_CUDA(cudaMemcpyAsync(c0, C, sizeof(double2) * h->N_s, cudaMemcpyDeviceToDevice, st));
-    // rhs -= A_full[:, (1, j)] c_j
-    STST_TRY(run_plan(h->lift_plan, C, rhs, 0, 1, rhs, nullptr, nullptr, nullptr, st));
+    // least squares: rhs -= A_full[:, (1, j)] c_j
+    if (h->formulation == STST_FORM_LS)
+      STST_TRY(run_plan(h->lift_plan, C, rhs, 0, 1, rhs, nullptr, nullptr, nullptr, st));
   } else if (c0) {
     STST_CUDA(cudaMemsetAsync(c0, 0, sizeof(double2) * h->N_s, st));
   }
@@ -311,18 +334,24 @@ extern "C" int stst_rhs_noalloc(stst_handle h, const double *f_qp, const double 
     double2 *T0V = h->pot_rank > 0 ? scratch + 4 * sz : nullptr;
     long long Qs = 1;
     for (int l = 1; l <= d; ++l) Qs *= Q[l];
-    STST_TRY(contract(h, 0, (const double2 *)f_qp, T1, 1, Qs, 1, 0.0, -1.0, 0));
+    const bool uw = h->formulation == STST_FORM_UW;  // ultraweak: plain load int f conj(B_i)
+    if (!uw) STST_TRY(contract(h, 0, (const double2 *)f_qp, T1, 1, Qs, 1, 0.0, -1.0, 0));
     STST_TRY(contract(h, 0, (const double2 *)f_qp, T0, 1, Qs, 0, 1.0, 0.0, 0));
     struct Term { double2 *src; int der[STST_MAXD + 1]; double s; };
     std::vector<Term> terms;
-    Term t1 = {T1, {0, 0, 0, 0}, 1.0};
-    terms.push_back(t1);
-    for (int l = 1; l <= d; ++l) {
-      Term t = {T0, {0, 0, 0, 0}, -h->nu};
-      t.der[l] = 2;
-      terms.push_back(t);
+    if (uw) {
+      Term t0 = {T0, {0, 0, 0, 0}, 1.0};
+      terms.push_back(t0);
+    } else {
+      Term t1 = {T1, {0, 0, 0, 0}, 1.0};
+      terms.push_back(t1);
+      for (int l = 1; l <= d; ++l) {
+        Term t = {T0, {0, 0, 0, 0}, -h->nu};
+        t.der[l] = 2;
+        terms.push_back(t);
+      }
     }
-    if (T0V) {
+    if (T0V && !uw) {
       const DirInfo &D = h->dir[0];
       long long tot = Qs * D.n;
       k_contract_time_pot<<<grid_for(tot, 128), 128, 0, st>>>((const double2 *)f_qp, T0V, h->tab[0], h->qwts[0], D.p,
@@ -373,6 +402,10 @@ extern "C" int stst_rhs_noalloc(stst_handle h, const double *f_qp, const double 
       src = dst;
       cur ^= 1;
     }
+    if (h->formulation == STST_FORM_UW) {  // rhs += i (u0, B_j) on time index 0
+      k_add_initial_uw<<<grid_for(h->N_s, 256), 256, 0, st>>>((double2 *)rhs, C, n[0], h->N_s);
+      STST_CUDA(cudaGetLastError());
+    }
     for (int l = 1; l <= d; ++l) {
       long long inner = 1, outer = 1;
       for (int k = 1; k < l; ++k) inner *= n[k];
@@ -381,7 +414,8 @@ extern "C" int stst_rhs_noalloc(stst_handle h, const double *f_qp, const double 
       STST_CUDA(cudaGetLastError());
     }
     if (c0) STST_CUDA(cudaMemcpyAsync(c0, C, sizeof(double2) * h->N_s, cudaMemcpyDeviceToDevice, st));
-    STST_TRY(run_plan(h->lift_plan, C, rhs, 0, 1, rhs, nullptr, nullptr, nullptr, st));
+    if (h->formulation == STST_FORM_LS)
+      STST_TRY(run_plan(h->lift_plan, C, rhs, 0, 1, rhs, nullptr, nullptr, nullptr, st));
   } else if (c0) {
     STST_CUDA(cudaMemsetAsync(c0, 0, sizeof(double2) * h->N_s, st));
   }

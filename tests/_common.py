@@ -12,10 +12,10 @@ def rel_err(a, b):
     return float(np.abs(a - b).max() / (den if den > 0 else 1.0))
 
 
-def oracle_disc(n_el, p, T=1.0, nu=1.0, potential=None):
+def oracle_disc(n_el, p, T=1.0, nu=1.0, potential=None, formulation="ls"):
     d = len(n_el) - 1
     pl = [p] * (d + 1) if isinstance(p, int) else list(p)
-    return Discretization(n_el, pl, T=T, nu=nu, potential=potential)
+    return Discretization(n_el, pl, T=T, nu=nu, potential=potential, formulation=formulation)
 
 
 def sample_potential(prob, terms):
