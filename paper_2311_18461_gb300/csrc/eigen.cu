@@ -32,18 +32,25 @@ __global__ void __launch_bounds__(512) k_eig_tridiag(const double *__restrict__ 
   float *bet = od + n;             // Householder beta_k
   float *pv = bet + n;             // work vector p
   float *wv = pv + n;              // work vector w
-  if (lu_smem) lu = wv + n;        // 3 n^2 floats of LU rows in shared memory when they fit
+  float *Ms = wv + n;              // n x (2p+1): the bands of M and L, staged once
+  float *Ls = Ms + n * (2 * p + 1);
+  if (lu_smem) lu = Ls + n * (2 * p + 1);  // 3 n^2 floats of LU rows in shared memory when they fit
   __shared__ float red[32];
   __shared__ float bc[4];
   const int tid = threadIdx.x, nth = blockDim.x;
   const int bw = 2 * p + 1;
+  for (int e = tid; e < n * bw; e += nth) {  // the serial steps below then read shared memory only
+    Ms[e] = (float)Mb[e];
+    Ls[e] = (float)Lb[e];
+  }
+  __syncthreads();
   // 1. banded Cholesky of M (thread 0)
   if (tid == 0) {
     for (int i = 0; i < n; ++i) {
       for (int k = 0; k <= p; ++k) {
         int j = i - p + k;
         if (j < 0) { C[i * (p + 1) + k] = 0.f; continue; }
-        float s = (float)Mb[i * bw + k];
+        float s = Ms[i * bw + k];
         for (int m = max(i - p, 0); m < j; ++m) s -= C[i * (p + 1) + (m - i + p)] * C[j * (p + 1) + (m - j + p)];
         if (j < i) C[i * (p + 1) + k] = s / C[j * (p + 1) + p];
         else {
@@ -57,7 +64,7 @@ __global__ void __launch_bounds__(512) k_eig_tridiag(const double *__restrict__ 
   // 2. Y = C^{-1} L (column j by thread j, into X), A = C^{-1} Y^T, symmetrized
   for (int j = tid; j < n; j += nth) {
     for (int i = 0; i < n; ++i) {
-      float s = (abs(i - j) <= p) ? (float)Lb[i * bw + (j - i + p)] : 0.f;
+      float s = (abs(i - j) <= p) ? Ls[i * bw + (j - i + p)] : 0.f;
       for (int m = max(i - p, 0); m < i; ++m) s -= C[i * (p + 1) + (m - i + p)] * X[m * ld + j];
       X[i * ld + j] = s / C[i * (p + 1) + p];
     }
@@ -259,7 +266,8 @@ __global__ void __launch_bounds__(512) k_eig_tridiag(const double *__restrict__ 
   __syncthreads();
   // 6. back-transform the eigenvectors: X <- H_0 H_1 ... H_{n-3} X, H_k = I - beta_k v_k v_k^T on rows
   //    k+1..; per reflection, s_j = beta_k v_k^T X[:, j] by eight lanes per column, then the rank-1 update
-  //    over all entries (pv, wv are free once the eigenvalues are in lam0)
+  //    over all entries (pv, wv are free once the eigenvalues are in lam0). Measured faster than one warp
+  //    per column (fewer serial steps per warp although it needs two block barriers per reflection).
   for (int k = n - 3; k >= 0; --k) {
     const float b = bet[k];
     if (b == 0.f) continue;  // uniform over the block
@@ -572,7 +580,8 @@ int fd_setup_launch(stst_problem *h) {
     if (src != l) continue;
     const int n = h->dir[l].n, p = h->dir[l].p;
     const BandMat &M = h->mats[l][0], &L = h->mats[l][1];
-    size_t sm = (2 * (size_t)n * (n + 1) + (size_t)n * (p + 1) + 5 * (size_t)n) * sizeof(float);
+    size_t sm = (2 * (size_t)n * (n + 1) + (size_t)n * (p + 1) + 5 * (size_t)n + 2 * (size_t)n * (2 * p + 1)) *
+                sizeof(float);
     const size_t sm_lu = sm + 3 * (size_t)n * n * sizeof(float);
     int dev = 0, optin = 0;
     STST_CUDA(cudaGetDevice(&dev));
