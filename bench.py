@@ -50,6 +50,10 @@ def parse():
     ap.add_argument("--config", default="c2")
     ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--solver", default="pcg", choices=["pcg", "ir"])
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="mode-product tiles: 1 measured per shape, 0 default, 10 rpt + cpt forced (stst_set_autotune)")
+    ap.add_argument("--time-solver", type=int, default=0,
+                    help="0 chosen per shape, 1 sequential, 2 segmented (stst_set_time_solver)")
     ap.add_argument("--formulation", default="ls", choices=["ls", "uw"],
                     help="least squares (Sec. 4.3) or ultraweak (Sec. 4.4)")
     ap.add_argument("--inner-tol", type=float, default=1e-4)
@@ -752,6 +756,9 @@ def main():
     else:
         from paper_2311_18461_gb300 import build
         build.build()
+        import paper_2311_18461_gb300 as S
+        S.stst_set_autotune(args.autotune)
+        S.stst_set_time_solver(args.time_solver)
         if args.config == "c4":
             run_batch(args)
         elif args.config == "c5":
