@@ -54,6 +54,8 @@ def parse():
                     help="mode-product tiles: 1 measured per shape, 0 default, 10 rpt + cpt forced (stst_set_autotune)")
     ap.add_argument("--time-solver", type=int, default=0,
                     help="0 chosen per shape, 1 sequential, 2 segmented (stst_set_time_solver)")
+    ap.add_argument("--cpu-baseline", default="on", choices=["on", "off"],
+                    help="time the oracle on the host cores (off: skip it, e.g. for the 3D workloads)")
     ap.add_argument("--formulation", default="ls", choices=["ls", "uw"],
                     help="least squares (Sec. 4.3) or ultraweak (Sec. 4.4)")
     ap.add_argument("--inner-tol", type=float, default=1e-4)
@@ -674,7 +676,7 @@ def run_ours(args):
         "paper_context": {"table": "Table 1, p=3, n_el=64, V=0 travelling wave, 1 CPU thread at 1 GHz",
                           "seconds": 4.7142, "iterations": 8},
     }
-    if rank == 0 and world == 1:
+    if rank == 0 and world == 1 and args.cpu_baseline == "on":
         cb = cpu_baseline(args.config, iters_full=None, formulation=args.formulation)
         x_ref = cb.pop("_x_ref", None)
         out["cpu_baseline"] = cb
