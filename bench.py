@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--solver", default="pcg", choices=["pcg", "ir"])
     ap.add_argument("--autotune", type=int, default=1,
                     help="mode-product tiles: 1 measured per shape, 0 default, 10 rpt + cpt forced (stst_set_autotune)")
+    ap.add_argument("--fused-transforms", type=int, default=0,
+                    help="d = 2, FP32 preconditioner: 0 chosen per shape, 1 separate mode products, 2 fused, "
+                         "11..14 fused with 1..4 CTAs per time index (stst_set_fused_transforms)")
     ap.add_argument("--time-solver", type=int, default=0,
                     help="0 chosen per shape, 1 sequential, 2 segmented (stst_set_time_solver)")
     ap.add_argument("--cpu-baseline", default="on", choices=["on", "off"],
@@ -685,6 +688,7 @@ def run_ours(args):
                                for l in range(1, cfg["d"] + 1)],
         "time_solver": dict(zip(("segments", "segment_len", "segmented"),
                                 S.stst_time_solver_info(prob.h, 0 if args.prec == "fp64" else 1))),
+        "fused_2d_transforms": S.stst_fused_transforms_info(prob.h),
         "kernels_ms_per_solve": {k: round(v[1], 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
         "kernel_launches_per_solve": {k: v[0] for k, v in prof.items()},
         "gpu_launches": int(sum(v[0] for v in prof.values())) * args.steps,
@@ -805,6 +809,7 @@ def main():
         import paper_2311_18461_gb300 as S
         S.stst_set_autotune(args.autotune)
         S.stst_set_time_solver(args.time_solver)
+        S.stst_set_fused_transforms(args.fused_transforms)
         if args.config == "c4":
             run_batch(args)
         elif args.config == "c5":

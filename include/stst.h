@@ -250,6 +250,20 @@ int stst_set_autotune(int mode);
  * segments (0 when the segmented kernel does not fit), their length, and whether it is used (host).
  */
 int stst_set_time_solver(int mode);
+/*
+ * stst_set_fused_transforms: for d = 2 with the FP32 preconditioner and n_1, n_2 <= 80, Algorithm 1
+ * steps 2 and 4 can each run as one kernel (S CTAs per time index take its n_1 x n_2 slab through
+ * both mode products in shared memory; the forward transform is split by rows, the backward one by
+ * columns) instead of two mode-product kernels. Mode 0 (default) chooses per shape when the
+ * preconditioner is built (separate kernels or a split S = 1..4, timed under autotune mode 1; else
+ * fused with the smallest S that gives two CTAs per SM); 1 = separate kernels; 2 = fused with that
+ * default split; 11..14 = fused with S = mode - 10 (the default split where S would leave a part
+ * empty). All give bitwise equal preconditioner outputs (same summation order and FP32
+ * intermediate). Process-wide, for handles whose preconditioner is built afterwards; STST_ERR_ARG for
+ * other modes. stst_fused_transforms_info: S of the handle, 0 when it uses separate kernels.
+ */
+int stst_set_fused_transforms(int mode);
+int stst_fused_transforms_info(stst_handle h, int *fused);
 int stst_time_solver_info(stst_handle h, int precision, int *segments, int *segment_len, int *segmented);
 /* Name and description of the CUDA error behind the calling thread's last STST_ERR_CUDA (static string). */
 const char *stst_last_cuda_error(void);

@@ -60,6 +60,8 @@ def lib():
             "stst_profile_read": [P, I, ctypes.c_char_p, I, ctypes.POINTER(LL), DP],
             "stst_set_autotune": [I],
             "stst_set_time_solver": [I],
+            "stst_set_fused_transforms": [I],
+            "stst_fused_transforms_info": [P, IP],
             "stst_time_solver_info": [P, I, IP, IP, IP],
             "stst_tile_info": [P, I, IP, IP, DP],
             "stst_ws_create": [ctypes.POINTER(P), I, IP, I, ctypes.c_ulonglong, P],
@@ -262,6 +264,16 @@ def stst_profile_read(h):
 
 def stst_set_autotune(mode):
     return _chk(lib().stst_set_autotune(int(mode)), "stst_set_autotune")
+
+
+def stst_set_fused_transforms(mode):
+    return _chk(lib().stst_set_fused_transforms(int(mode)), "stst_set_fused_transforms")
+
+
+def stst_fused_transforms_info(h):
+    f = ctypes.c_int()
+    _chk(lib().stst_fused_transforms_info(h, ctypes.byref(f)), "stst_fused_transforms_info")
+    return f.value
 
 
 def stst_set_time_solver(mode):

@@ -958,6 +958,212 @@ static int launch_timesolve(void *Y, const void *G, const R *D, int nt, long lon
 // The final mode product optionally accumulates per-CTA partials of Re<r, s> into dot_partials.
 // ------------------------------------------------------------------------------------------------
 
+// ------------------------------------------------------------------------------------------------
+// Fused 2D spatial transforms of Algorithm 1 (steps 2 and 4, d = 2, FP32): for one time index t the
+// spatial slab X_t (n1 x n2, X_t[i1][i2] = X[t + nt (i1 + n1 i2)]) goes through both mode products in
+// shared memory,
+//   forward:  Y_t = U1^T X_t U2   (mode 1, then mode 2),
+//   backward: Y_t = U1 X_t U2^T   (mode 2, then mode 1).
+// S CTAs share a time index: the forward transform is split by rows of Y_t (a CTA needs the columns of
+// U1 of its rows and all of X_t, and mode 2 stays within its rows), the backward one by columns of
+// Y_t (a CTA needs the rows of U2 of its columns). Every output is accumulated over its index in
+// ascending order from the FP32-rounded intermediate, as the separate mode products do, so the
+// results are bitwise equal to theirs.
+//
+// Each contraction o(a, b) = sum_i R(i, a) C(i, b) has a real factor R (a slice of U1 or U2, staged
+// so that R(i, a) = sR[i rs + a]) and a complex one C (slab or intermediate). Thread `item` = g Ra + a0
+// owns the outputs a = a0 + Ra k (k < NR) and b = NC g + q (q < NC), Ra = ceil(A / NR): consecutive
+// lanes read consecutive entries of R and mostly the same entries of C (broadcast), so a warp's
+// shared-memory reads per step are NR + NC wavefronts against 2 NR NC FMAs.
+// ------------------------------------------------------------------------------------------------
+#define FD2D_NR 4
+#define FD2D_NC 4
+#define FD2D_MAXN 80
+#define FD2D_MAXS 4
+
+template <int NR, int NC>
+__device__ __forceinline__ void fd2d_contract(const float *__restrict__ sR, int rs, int A,
+                                              const float2 *__restrict__ sC, int cs_i, int cs_b, int B, int K,
+                                              int a0, int Ra, int g, float ax[NR][NC], float ay[NR][NC]) {
+  int ra[NR], cb[NC];
+#pragma unroll
+  for (int k = 0; k < NR; ++k) ra[k] = min(a0 + Ra * k, A - 1);  // clamped: results past A are not stored
+#pragma unroll
+  for (int q = 0; q < NC; ++q) cb[q] = min(NC * g + q, B - 1) * cs_b;
+#pragma unroll
+  for (int k = 0; k < NR; ++k)
+#pragma unroll
+    for (int q = 0; q < NC; ++q) { ax[k][q] = 0.f; ay[k][q] = 0.f; }
+  for (int i = 0; i < K; ++i) {
+    const float *ri = sR + (long long)i * rs;
+    const float2 *ci = sC + (long long)i * cs_i;
+    float u[NR];
+    float2 xv[NC];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) u[k] = ri[ra[k]];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) xv[q] = ci[cb[q]];
+#pragma unroll
+    for (int k = 0; k < NR; ++k)
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        ax[k][q] += u[k] * xv[q].x;
+        ay[k][q] += u[k] * xv[q].y;
+      }
+  }
+}
+
+template <typename TI, typename TO>
+__global__ void __launch_bounds__(512) k_fd2d(const TI *__restrict__ X, TO *__restrict__ Y, const float *__restrict__ U1,
+                                              const float *__restrict__ U2, int n1, int n2, int nt, int backward,
+                                              const TO *__restrict__ dotvec, double *dot_partials, const int *done) {
+  constexpr int NR = FD2D_NR, NC = FD2D_NC;
+  if (done && *done) return;
+  extern __shared__ __align__(16) unsigned char fd_smem[];
+  __shared__ double sh[32];
+  const int t = blockIdx.x, S = gridDim.y, part = blockIdx.y;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int nsplit = backward ? n2 : n1, nother = backward ? n1 : n2;
+  const int mfull = (nsplit + S - 1) / S, p0 = part * mfull, m = min(mfull, nsplit - p0);
+  const int nmax = max(n1, n2);
+  float2 *sX = (float2 *)fd_smem;                    // slab, X_t[i1][i2] at i1 + n1 i2
+  float2 *sZ = sX + n1 * n2;                         // intermediate, mfull x nmax
+  float *sRa = (float *)(sZ + mfull * nmax);         // forward: U1 columns of the part; backward: U2 rows
+  float *sRb = sRa + (mfull * nmax + 3) / 4 * 4;     // forward: U2; backward: U1^T
+  // staging: the factors and an FP32 slab by cp.async (all copies in flight at once), an FP64 slab
+  // through registers in batches of independent loads (it is rounded to FP32 on the way)
+  if (!backward) {
+    for (int e = tid; e < n1 * m; e += nth) {        // sRa[i m + j] = U1[i][p0 + j]
+      const int i = e / m, j = e - i * m;
+      cp_async<4>(&sRa[e], &U1[i * n1 + p0 + j]);
+    }
+    for (int e = tid; e < n2 * n2; e += nth) cp_async<4>(&sRb[e], &U2[e]);
+  } else {
+    for (int e = tid; e < m * n2; e += nth) {        // sRa[c m + k] = U2[p0 + k][c]
+      const int k = e / n2, c = e - k * n2;
+      cp_async<4>(&sRa[c * m + k], &U2[(p0 + k) * n2 + c]);
+    }
+    for (int e = tid; e < n1 * n1; e += nth) {       // sRb[r n1 + j] = U1[j][r]
+      const int j = e / n1, r = e - j * n1;
+      cp_async<4>(&sRb[r * n1 + j], &U1[e]);
+    }
+  }
+  if constexpr (sizeof(TI) == sizeof(float2)) {
+    for (int e = tid; e < n1 * n2; e += nth) cp_async<8>(&sX[e], &X[t + (long long)nt * e]);
+  } else {
+    constexpr int BATCH = 8;  // independent loads in flight per thread
+    const int nn = n1 * n2;
+    for (int e0 = tid; e0 < nn; e0 += BATCH * nth) {
+      TI v[BATCH];
+#pragma unroll
+      for (int u = 0; u < BATCH; ++u) {
+        const int e = e0 + u * nth;
+        if (e < nn) v[u] = X[t + (long long)nt * e];
+      }
+#pragma unroll
+      for (int u = 0; u < BATCH; ++u) {
+        const int e = e0 + u * nth;
+        if (e < nn) sX[e] = make_float2((float)v[u].x, (float)v[u].y);
+      }
+    }
+  }
+  cp_async_commit();
+  cp_async_wait_all();
+  __syncthreads();
+  float ax[NR][NC], ay[NR][NC];
+  const int Ra1 = (m + NR - 1) / NR, Ra2 = (nother + NR - 1) / NR;
+  if (tid < Ra1 * ((nother + NC - 1) / NC)) {
+    const int a0 = tid % Ra1, g = tid / Ra1;
+    if (!backward)  // Z[j][c] = sum_i U1[i][p0 + j] X[i][c], stored at sZ[j + m c]
+      fd2d_contract<NR, NC>(sRa, m, m, sX, 1, n1, n2, n1, a0, Ra1, g, ax, ay);
+    else            // Z[r][k] = sum_c U2[p0 + k][c] X[r][c], stored at sZ[r + n1 k]
+      fd2d_contract<NR, NC>(sRa, m, m, sX, n1, 1, n1, n2, a0, Ra1, g, ax, ay);
+    const int zs = backward ? n1 : 1, zb = backward ? 1 : m;  // sZ index = a zs + b zb
+#pragma unroll
+    for (int k = 0; k < NR; ++k)
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        const int a = a0 + Ra1 * k, b = NC * g + q;
+        if (a < m && b < nother) sZ[a * zs + b * zb] = make_float2(ax[k][q], ay[k][q]);
+      }
+  }
+  __syncthreads();
+  double dacc = 0.0;
+  if (tid < Ra2 * ((m + NC - 1) / NC)) {
+    const int a0 = tid % Ra2, g = tid / Ra2;
+    if (!backward)  // Y[j][k] = sum_c U2[c][k] Z[j][c]
+      fd2d_contract<NR, NC>(sRb, n2, n2, sZ, m, 1, m, n2, a0, Ra2, g, ax, ay);
+    else            // Y[j][k] = sum_r U1[j][r] Z[r][k]
+      fd2d_contract<NR, NC>(sRb, n1, n1, sZ, 1, n1, m, n1, a0, Ra2, g, ax, ay);
+#pragma unroll
+    for (int k = 0; k < NR; ++k)
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        const int a = a0 + Ra2 * k, b = NC * g + q;
+        if (a < nother && b < m) {
+          const int i1 = backward ? a : p0 + b, i2 = backward ? p0 + b : a;
+          const long long idx = t + (long long)nt * (i1 + (long long)n1 * i2);
+          TO res;
+          res.x = ax[k][q];
+          res.y = ay[k][q];
+          Y[idx] = res;
+          if (dotvec) {
+            const TO dv = dotvec[idx];
+            dacc += (double)dv.x * (double)res.x + (double)dv.y * (double)res.y;
+          }
+        }
+      }
+  }
+  if (dot_partials) {
+    const double s2 = block_sum(dacc, sh);
+    if (tid == 0) dot_partials[t * S + part] = s2;
+  }
+}
+
+// items of the larger of the two contractions, at least 256 threads for the staging
+static int fd2d_threads(int m, int nother) {
+  const int i1 = ((m + FD2D_NR - 1) / FD2D_NR) * ((nother + FD2D_NC - 1) / FD2D_NC);
+  const int i2 = ((nother + FD2D_NR - 1) / FD2D_NR) * ((m + FD2D_NC - 1) / FD2D_NC);
+  const int nth = ((i1 > i2 ? i1 : i2) + 31) / 32 * 32;
+  return nth < 256 ? 256 : nth;
+}
+
+static size_t fd2d_smem(int n1, int n2, int S) {
+  const int nmax = n1 > n2 ? n1 : n2, mfull = (nmax + S - 1) / S;
+  return sizeof(float2) * ((size_t)n1 * n2 + (size_t)mfull * nmax) +
+         sizeof(float) * (((size_t)mfull * nmax + 3) / 4 * 4 + (size_t)nmax * nmax);
+}
+
+// S parts of a time index are usable when none of them is empty along either split dimension
+static bool fd2d_split_ok(int n1, int n2, int S) {
+  return (S - 1) * ((n1 + S - 1) / S) < n1 && (S - 1) * ((n2 + S - 1) / S) < n2;
+}
+
+bool fd2d_fits(const stst_problem *h) {
+  if (h->d != 2 || h->dir[1].n > FD2D_MAXN || h->dir[2].n > FD2D_MAXN) return false;
+  if ((long long)h->n_t() * FD2D_MAXS > STST_MAXPART) return false;
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return fd2d_smem(h->dir[1].n, h->dir[2].n, 1) <= (size_t)optin;
+}
+
+template <typename TI, typename TO>
+static int launch_fd2d(const TI *X, TO *Y, const stst_problem *h, int backward, const TO *dotvec, double *partials,
+                       const int *done, cudaStream_t s, int S) {
+  const int n1 = h->dir[1].n, n2 = h->dir[2].n, nt = h->n_t();
+  if (S < 1 || S > FD2D_MAXS || !fd2d_split_ok(n1, n2, S)) return STST_ERR_ARG;
+  const int m = backward ? (n2 + S - 1) / S : (n1 + S - 1) / S;
+  const int nth = fd2d_threads(m, backward ? n1 : n2);
+  const size_t sm = fd2d_smem(n1, n2, S);
+  STST_PROF("modeprod2d_f32", s);
+  STST_TRY(ensure_dyn_smem((const void *)k_fd2d<TI, TO>, sm));
+  k_fd2d<TI, TO><<<dim3(nt, S), nth, sm, s>>>(X, Y, h->U32[1], h->U32[2], n1, n2, nt, backward, dotvec, partials,
+                                              done);
+  STST_CUDA(cudaGetLastError());
+  return STST_OK;
+}
+
 // time solve of the preconditioner: segmented (parallel in time) or sequential, as chosen per handle
 template <typename R>
 static int time_solve(stst_problem *h, void *Y, const int *done, cudaStream_t st) {
@@ -1057,6 +1263,17 @@ int fd_apply(stst_problem *h, const double *r, double *s, int precision, const v
     return STST_OK;
   }
   // FP32
+  if (h->fd2d) {  // both spatial mode products of each transform in one kernel (d = 2)
+    float2 *y32 = (float2 *)bufA;
+    const int S = h->fd2d;
+    if (in32) STST_TRY((launch_fd2d<float2, float2>((const float2 *)in32, y32, h, 0, nullptr, nullptr, done, st, S)));
+    else STST_TRY((launch_fd2d<double2, float2>((const double2 *)r, y32, h, 0, nullptr, nullptr, done, st, S)));
+    STST_TRY(time_solve<float>(h, (void *)y32, done, st));
+    if (out32)
+      return launch_fd2d<float2, float2>(y32, (float2 *)out32, h, 1, (const float2 *)dotvec, dot_partials, done, st,
+                                         S);
+    return launch_fd2d<float2, double2>(y32, (double2 *)s, h, 1, (const double2 *)dotvec, dot_partials, done, st, S);
+  }
   float2 *bufs[2] = {(float2 *)bufA, (float2 *)bufB};
   int cur = 0;
   const float2 *src32 = nullptr;
@@ -1104,6 +1321,7 @@ int fd_apply(stst_problem *h, const double *r, double *s, int precision, const v
 int fd_partials_count(stst_problem *h) {
   long long ncols = h->N_dof / h->dir[1].n;
   if (h->prec_mode == STST_PREC_BF16) return tc_partials_count(ncols);
+  if (h->fd2d && h->prec_mode == STST_PREC_FP32) return h->n_t() * h->fd2d;
   const dim3 g = modeprod_grid(h->dir[1].n, ncols, h->mp_cfg[1]);
   return (int)(g.x * g.y);
 }
@@ -1173,11 +1391,102 @@ static int tune_ts(stst_problem *h) {
   return STST_OK;
 }
 
+// ---- choice between fused and separate 2D transforms (FP32 preconditioner, d = 2) -------------------
+// h->fd2d = number S of CTAs per time index of the fused kernel, 0 for the separate mode products.
+// Measured (autotune mode 1): a forward plus a backward transform of each variant timed on work
+// vectors, cached per (n_t, n_1, n_2). Otherwise S is the smallest split giving two CTAs per SM.
+int g_fd2d_mode = 0;  // 0 chosen per shape, 1 separate kernels, 2 fused where it fits, 10 + S fused with split S
+static std::map<std::tuple<int, int, int>, int> g_fd2d_cache;
+
+static int fd2d_default_split(const stst_problem *h) {
+  int S = 1;
+  while (S < FD2D_MAXS && (long long)h->n_t() * S < 2 * 152 && fd2d_split_ok(h->dir[1].n, h->dir[2].n, S + 1)) ++S;
+  return S;
+}
+
+static int tune_fd2d(stst_problem *h) {
+  h->fd2d = 0;
+  if (h->prec_mode != STST_PREC_FP32 || !fd2d_fits(h) || g_fd2d_mode == 1) return STST_OK;
+  if (g_fd2d_mode > 10 && fd2d_split_ok(h->dir[1].n, h->dir[2].n, g_fd2d_mode - 10)) {
+    h->fd2d = g_fd2d_mode - 10;
+    return STST_OK;
+  }
+  if (g_fd2d_mode >= 2 || g_tune_enabled != 1) {
+    h->fd2d = fd2d_default_split(h);
+    return STST_OK;
+  }
+  const auto key = std::make_tuple(h->n_t(), h->dir[1].n, h->dir[2].n);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_fd2d_cache.find(key);
+    if (it != g_fd2d_cache.end()) {
+      h->fd2d = it->second;
+      return STST_OK;
+    }
+  }
+  cudaStream_t st = h->stream;
+  float2 *X = (float2 *)h->w_t1, *Y = (float2 *)h->w_t1 + h->N_dof;  // two FP32 vectors in one FP64 one
+  float2 *Z = (float2 *)h->w_t2;
+  STST_CUDA(cudaMemsetAsync(h->w_t1, 0, sizeof(double) * 2 * h->N_dof, st));
+  long long inner[3], outer[3];
+  inner[1] = h->n_t();
+  outer[1] = h->N_dof / (inner[1] * h->dir[1].n);
+  inner[2] = inner[1] * h->dir[1].n;
+  outer[2] = h->N_dof / (inner[2] * h->dir[2].n);
+  cudaEvent_t e0, e1;
+  STST_CUDA(cudaEventCreate(&e0));
+  STST_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int choice = 0, status = STST_OK;
+  for (int S = 0; S <= FD2D_MAXS && status == STST_OK; ++S) {
+    if (S > 0 && !fd2d_split_ok(h->dir[1].n, h->dir[2].n, S)) continue;
+    auto run = [&]() -> int {
+      if (S > 0) {
+        STST_TRY((launch_fd2d<float2, float2>(X, Y, h, 0, nullptr, nullptr, nullptr, st, S)));
+        return launch_fd2d<float2, float2>(Y, X, h, 1, nullptr, nullptr, nullptr, st, S);
+      }
+      STST_TRY((launch_modeprod<float, float2, float2>(X, Z, h->U32[1], h->dir[1].n, inner[1], outer[1], 0, nullptr,
+                                                       nullptr, nullptr, st, h->mp_cfg[1])));
+      STST_TRY((launch_modeprod<float, float2, float2>(Z, Y, h->U32[2], h->dir[2].n, inner[2], outer[2], 0, nullptr,
+                                                       nullptr, nullptr, st, h->mp_cfg[2])));
+      STST_TRY((launch_modeprod<float, float2, float2>(Y, Z, h->U32[2], h->dir[2].n, inner[2], outer[2], 1, nullptr,
+                                                       nullptr, nullptr, st, h->mp_cfg[2])));
+      return launch_modeprod<float, float2, float2>(Z, X, h->U32[1], h->dir[1].n, inner[1], outer[1], 1, nullptr,
+                                                    nullptr, nullptr, st, h->mp_cfg[1]);
+    };
+    for (int w = 0; w < 2 && status == STST_OK; ++w) status = run();
+    cudaEventRecord(e0, st);
+    for (int w = 0; w < 5 && status == STST_OK; ++w) status = run();
+    cudaEventRecord(e1, st);
+    const cudaError_t es = cudaEventSynchronize(e1);
+    if (es != cudaSuccess) {
+      stst_last_cuda = es;
+      status = STST_ERR_CUDA;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (status == STST_OK && ms < best) {
+      best = ms;
+      choice = S;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  STST_TRY(status);
+  h->fd2d = choice;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_fd2d_cache[key] = choice;
+  }
+  return STST_OK;
+}
+
 int tune_modeprod(stst_problem *h) {
   if (h->tuned) return STST_OK;
   STST_TRY(tune_mp_tiles(h));
   STST_TRY(tune_ts<float>(h));
   if (h->prec_mode == STST_PREC_FP64) STST_TRY(tune_ts<double>(h));
+  STST_TRY(tune_fd2d(h));
   h->tuned = 1;
   return STST_OK;
 }

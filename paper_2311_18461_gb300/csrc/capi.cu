@@ -782,6 +782,18 @@ int stst_set_autotune(int mode) {
   return STST_OK;
 }
 
+int stst_set_fused_transforms(int mode) {
+  if (mode < 0 || (mode > 2 && (mode < 11 || mode > 14))) return STST_ERR_ARG;
+  g_fd2d_mode = mode;
+  return STST_OK;
+}
+
+int stst_fused_transforms_info(stst_handle h, int *fused) {
+  STST_TRY(check(h));
+  if (fused) *fused = h->fd2d;
+  return STST_OK;
+}
+
 int stst_set_time_solver(int mode) {
   if (mode < 0 || mode > 2) return STST_ERR_ARG;
   g_ts_mode = mode;

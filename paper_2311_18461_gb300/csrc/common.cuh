@@ -124,6 +124,7 @@ struct stst_problem {
   MpCfg mp_cfg[STST_MAXD + 1];     // mode-product tile per direction (autotuned or default)
   float mp_us[STST_MAXD + 1];      // its measured time per launch (0: not measured)
   int tuned;
+  int fd2d;                        // fused 2D spatial transforms in the FP32 preconditioner (d = 2)
   int eig_src[STST_MAXD + 1];
   double *U[STST_MAXD + 1];
   float *U32[STST_MAXD + 1];
@@ -224,6 +225,8 @@ MpCfg modeprod_default(int n);
 int tune_modeprod(stst_problem *h);  // times the mode-product tiles once per shape (outside graph capture)
 extern int g_tune_enabled;
 extern int g_ts_mode;
+extern int g_fd2d_mode;
+bool fd2d_fits(const stst_problem *h);
 
 // tensor-core mode products (modeprod_tc.cu)
 int launch_u_to_bf16(const double *U, int n, __nv_bfloat16 *out, cudaStream_t s);

@@ -76,16 +76,46 @@ __global__ void k_copy_vec(const T *__restrict__ a, T *__restrict__ b, long long
     b[i] = a[i];
 }
 
+// Vector updates: UPT elements per thread per pass (indices i0 + 256 u). The first pass's operands
+// are loaded before the scalar reductions, so the latency of the vector loads overlaps that of the
+// partial sums. Every CTA reduces the same partials, so the grid stays at two CTAs per SM: measured
+// on the 2D p = 3 64^2 x 64 solve, one pass over the vector with 545 CTAs cost 10 us more per
+// iteration than 304 CTAs looping twice.
+#define UPT 2
+int update_grid(long long n) {
+  long long g = (n + 256 * UPT - 1) / (256 * UPT);
+  if (g > 2 * 152) g = 2 * 152;
+  return g < 1 ? 1 : (int)g;
+}
+
 // alpha = rho / <p, q> (every CTA reduces the same partials in the same order; CTA 0 records it),
 // then x += alpha p; r -= alpha q; partials of ||r||^2 and (flexible) Re<r, z_old>
 // rho = <r, z> is reduced from the partials of the latest preconditioner application (prz_in), so no
 // CTA of this kernel reads a scalar that another CTA of it writes.
 template <typename T>
-__global__ void k_update_xr(T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p, const T *__restrict__ q,
-                            const T *__restrict__ zold, PcgCtl *ctl, long long n, double *prr, double *prz,
-                            const double *ppq, int npq, const double *prz_in, int nrz_in) {
+__global__ void __launch_bounds__(256) k_update_xr(T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p,
+                                                   const T *__restrict__ q, const T *__restrict__ zold, PcgCtl *ctl,
+                                                   long long n, double *prr, double *prz, const double *ppq, int npq,
+                                                   const double *prz_in, int nrz_in) {
   if (ctl->done) return;
   __shared__ double sh[32];
+  const long long stride = (long long)gridDim.x * 256 * UPT;
+  long long i0 = (long long)blockIdx.x * 256 * UPT + threadIdx.x;
+  T pv[UPT], qv[UPT], xv[UPT], rv[UPT], zv[UPT];
+  auto load = [&](long long base) {
+#pragma unroll
+    for (int u = 0; u < UPT; ++u) {
+      const long long i = base + 256 * u;
+      if (i < n) {
+        pv[u] = p[i];
+        qv[u] = q[i];
+        xv[u] = x[i];
+        rv[u] = r[i];
+        if (zold) zv[u] = zold[i];
+      }
+    }
+  };
+  if (i0 < n) load(i0);
   const double pq = reduce_partials(ppq, npq, sh);
   const double rho = reduce_partials(prz_in, nrz_in, sh);
   const bool bad = !(pq > 0.0) || !isfinite(pq);
@@ -97,19 +127,22 @@ __global__ void k_update_xr(T *__restrict__ x, T *__restrict__ r, const T *__res
     if (bad) ctl->status = STST_BREAKDOWN;  // the check kernel ends the loop
   }
   double arr = 0.0, arz = 0.0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    T pv = p[i], qv = q[i], xv = x[i], rv = r[i];
-    xv.x += alpha * pv.x;
-    xv.y += alpha * pv.y;
-    rv.x -= alpha * qv.x;
-    rv.y -= alpha * qv.y;
-    x[i] = xv;
-    r[i] = rv;
-    arr += (double)rv.x * rv.x + (double)rv.y * rv.y;
-    if (zold) {
-      T zv = zold[i];
-      arz += (double)zv.x * rv.x + (double)zv.y * rv.y;
+  for (; i0 < n; i0 += stride) {
+#pragma unroll
+    for (int u = 0; u < UPT; ++u) {
+      const long long i = i0 + 256 * u;
+      if (i < n) {
+        xv[u].x += alpha * pv[u].x;
+        xv[u].y += alpha * pv[u].y;
+        rv[u].x -= alpha * qv[u].x;
+        rv[u].y -= alpha * qv[u].y;
+        x[i] = xv[u];
+        r[i] = rv[u];
+        arr += (double)rv[u].x * rv[u].x + (double)rv[u].y * rv[u].y;
+        if (zold) arz += (double)zv[u].x * rv[u].x + (double)zv[u].y * rv[u].y;
+      }
     }
+    if (i0 + stride < n) load(i0 + stride);
   }
   double s = block_sum_d(arr, sh);
   if (threadIdx.x == 0) prr[blockIdx.x] = s;
@@ -153,21 +186,41 @@ __global__ void k_pcg_check(PcgCtl *ctl, const double *prr, int nrr, const doubl
 // rho_old (written by k_update_xr) and rz_old (written by the check kernel) come from earlier
 // kernels; this kernel writes no scalar that its own CTAs read.
 template <typename T>
-__global__ void k_update_p(T *__restrict__ p, const T *__restrict__ z, PcgCtl *ctl, long long n, const double *prz,
-                           int nrz) {
+__global__ void __launch_bounds__(256) k_update_p(T *__restrict__ p, const T *__restrict__ z, PcgCtl *ctl, long long n,
+                                                  const double *prz, int nrz) {
   if (ctl->done) return;
   __shared__ double sh[32];
+  const long long stride = (long long)gridDim.x * 256 * UPT;
+  long long i0 = (long long)blockIdx.x * 256 * UPT + threadIdx.x;
+  T pv[UPT], zv[UPT];
+  auto load = [&](long long base) {
+#pragma unroll
+    for (int u = 0; u < UPT; ++u) {
+      const long long i = base + 256 * u;
+      if (i < n) {
+        pv[u] = p[i];
+        zv[u] = z[i];
+      }
+    }
+  };
+  if (i0 < n) load(i0);
   const double rho_old = ctl->rho, rz_old = ctl->rz_old;
   const int flexible = ctl->flexible;
   const double rho_new = reduce_partials(prz, nrz, sh);
   const bool bad = !(rho_new > 0.0) || !isfinite(rho_new);
   const double beta = bad ? 0.0 : (flexible ? (rho_new - rz_old) / rho_old : rho_new / rho_old);
   if (bad && blockIdx.x == 0 && threadIdx.x == 0) ctl->status = STST_BREAKDOWN;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    T pv = p[i], zv = z[i];
-    pv.x = zv.x + beta * pv.x;
-    pv.y = zv.y + beta * pv.y;
-    p[i] = pv;
+  for (; i0 < n; i0 += stride) {
+#pragma unroll
+    for (int u = 0; u < UPT; ++u) {
+      const long long i = i0 + 256 * u;
+      if (i < n) {
+        pv[u].x = zv[u].x + beta * pv[u].x;
+        pv[u].y = zv[u].y + beta * pv[u].y;
+        p[i] = pv[u];
+      }
+    }
+    if (i0 + stride < n) load(i0 + stride);
   }
 }
 
@@ -177,7 +230,7 @@ __global__ void k_update_p(T *__restrict__ p, const T *__restrict__ z, PcgCtl *c
 int pcg_body(stst_problem *h, cudaGraphConditionalHandle cond, int use_cond) {
   cudaStream_t st = h->stream;
   const long long N = h->N_dof;
-  const int g = reduction_grid(N);
+  const int g = reduction_grid(N), gu = update_grid(N);
   const int prec = h->prec_mode;  // STST_PREC_* equals fd_apply's precision code
   double *P = h->partials;
   double *pA = P, *pB = P + STST_MAXPART, *pC = P + 2 * STST_MAXPART, *pD = P + 3 * STST_MAXPART;
@@ -187,13 +240,13 @@ int pcg_body(stst_problem *h, cudaGraphConditionalHandle cond, int use_cond) {
   // q = A p, partials <p, q>
   STST_TRY(run_plan(h->sys_plan, h->w_p, h->w_q, 0, 0, nullptr, h->w_p, pD, done, st));
   // alpha; x, r update (+ Re<r_new, z_old> for the flexible beta)
-  { STST_PROF("pcg_update_xr", st); k_update_xr<double2><<<g, 256, 0, st>>>((double2 *)h->w_x, (double2 *)h->w_r, (const double2 *)h->w_p,
+  { STST_PROF("pcg_update_xr", st); k_update_xr<double2><<<gu, 256, 0, st>>>((double2 *)h->w_x, (double2 *)h->w_r, (const double2 *)h->w_p,
                                           (const double2 *)h->w_q, flexible ? (const double2 *)h->w_z : nullptr,
                                           h->ctl, N, pB, pC, pD, g, pA, nrz); }
-  { STST_PROF("pcg_scalar", st); k_pcg_check<<<1, 1024, 0, st>>>(h->ctl, pB, g, flexible ? pC : nullptr, flexible ? g : 0, cond, use_cond); }
+  { STST_PROF("pcg_scalar", st); k_pcg_check<<<1, 1024, 0, st>>>(h->ctl, pB, gu, flexible ? pC : nullptr, flexible ? gu : 0, cond, use_cond); }
   // z = P^{-1} r, partials <r, z>
   STST_TRY(fd_apply(h, h->w_r, h->w_z, prec, h->w_r, pA, done, h->w_t1, h->w_t2));
-  { STST_PROF("pcg_update_p", st); k_update_p<double2><<<g, 256, 0, st>>>((double2 *)h->w_p, (const double2 *)h->w_z, h->ctl, N, pA, nrz); }
+  { STST_PROF("pcg_update_p", st); k_update_p<double2><<<gu, 256, 0, st>>>((double2 *)h->w_p, (const double2 *)h->w_z, h->ctl, N, pA, nrz); }
   STST_CUDA(cudaGetLastError());
   return STST_OK;
 }
@@ -349,20 +402,20 @@ __global__ void k_x_from_f32(double2 *__restrict__ x, const float2 *__restrict__
 static int inner_body(stst_problem *h, cudaGraphConditionalHandle cond, int use_cond) {
   cudaStream_t st = h->stream;
   const long long N = h->N_dof;
-  const int g = reduction_grid(N);
+  const int g = reduction_grid(N), gu = update_grid(N);
   double *P = h->partials;
   double *pA = P, *pB = P + STST_MAXPART, *pC = P + 2 * STST_MAXPART, *pD = P + 3 * STST_MAXPART;
   const int *done = &h->ctl2->done;
   const int nrz = fd_partials_count(h);
   STST_TRY(run_plan(h->sys_plan, h->v_p, h->v_q, 1, 0, nullptr, h->v_p, pD, done, st));
   { STST_PROF("pcg_update_xr", st);
-    k_update_xr<float2><<<g, 256, 0, st>>>((float2 *)h->v_d, (float2 *)h->v_r, (const float2 *)h->v_p,
-                                           (const float2 *)h->v_q, (const float2 *)h->v_z, h->ctl2, N, pB, pC,
-                                           pD, g, pA, nrz); }
-  { STST_PROF("pcg_scalar", st); k_pcg_check<<<1, 1024, 0, st>>>(h->ctl2, pB, g, pC, g, cond, use_cond); }
+    k_update_xr<float2><<<gu, 256, 0, st>>>((float2 *)h->v_d, (float2 *)h->v_r, (const float2 *)h->v_p,
+                                            (const float2 *)h->v_q, (const float2 *)h->v_z, h->ctl2, N, pB, pC,
+                                            pD, g, pA, nrz); }
+  { STST_PROF("pcg_scalar", st); k_pcg_check<<<1, 1024, 0, st>>>(h->ctl2, pB, gu, pC, gu, cond, use_cond); }
   STST_TRY(fd_apply(h, nullptr, nullptr, h->prec_mode == STST_PREC_BF16 ? 2 : 1, h->v_r, pA, done, h->w_t1, h->w_t2, h->v_z, h->v_r));
   { STST_PROF("pcg_update_p", st);
-    k_update_p<float2><<<g, 256, 0, st>>>((float2 *)h->v_p, (const float2 *)h->v_z, h->ctl2, N, pA, nrz); }
+    k_update_p<float2><<<gu, 256, 0, st>>>((float2 *)h->v_p, (const float2 *)h->v_z, h->ctl2, N, pA, nrz); }
   STST_CUDA(cudaGetLastError());
   return STST_OK;
 }

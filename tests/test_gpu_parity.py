@@ -290,6 +290,7 @@ def test_mode_product_tiles_agree_bitwise(prec):
     import paper_2311_18461_gb300 as P
     outs = {}
     P.stst_set_time_solver(1)  # the same time solve for every tile
+    P.stst_set_fused_transforms(1)  # separate mode products, so that every tile runs
     try:
         for mode in (0, 12, 14, 22, 24, 32, 34, 42, 44, 1):
             P.stst_set_autotune(mode)
@@ -302,10 +303,55 @@ def test_mode_product_tiles_agree_bitwise(prec):
     finally:
         P.stst_set_autotune(1)
         P.stst_set_time_solver(0)
+        P.stst_set_fused_transforms(0)
     ref = outs[0][0]
     for mode, (o, tiles) in outs.items():
         assert np.array_equal(o, ref), (mode, tiles)
     assert outs[12][1][0][:2] == (16, 32) and outs[44][1][1][:2] == (32, 128)
+
+
+@pytest.mark.parametrize("n_el,p", [([5, 40, 70], 3), ([9, 16, 78], [2, 3, 3]), ([3, 1, 5], 2), ([70, 30, 31], 2)])
+def test_fused_2d_transforms_bitwise(n_el, p):
+    """The fused 2D transform kernel (both spatial mode products of Algorithm 1 steps 2 and 4 in one
+    kernel) gives bitwise the same preconditioner output as the two separate mode-product kernels; PCG
+    with either takes the same iterations (only the order of the dot-product partial sums differs)."""
+    out = {}
+    try:
+        for mode in (1, 2, 11, 12, 13, 14):
+            S.stst_set_fused_transforms(mode)
+            prob = S.Problem(2, n_el, p, prec_mode=S.STST_PREC_FP32)
+            prob.build_fd()
+            fused = S.stst_fused_transforms_info(prob.h)
+            z = to_np(prob.apply_prec(to_dev(random_complex(prob.n_dof, 31))))
+            x, st, it, rr = prob.pcg(to_dev(random_complex(prob.n_dof, 32)), tol=1e-10, maxit=300)
+            out[mode] = (z, fused, st, it, to_np(x))
+            prob.close()
+    finally:
+        S.stst_set_fused_transforms(0)
+    assert out[1][1] == 0 and out[2][1] >= 1 and out[11][1] == 1
+    assert all(out[10 + k][1] in (k, out[2][1]) for k in (2, 3, 4))  # the default where k leaves a part empty
+    for mode in (2, 11, 12, 13, 14):
+        assert np.array_equal(out[1][0], out[mode][0]), (mode, out[mode][1])
+        assert out[1][2] == 0 and out[mode][2] == 0 and abs(out[1][3] - out[mode][3]) <= 1
+        assert rel_err(out[mode][4], out[1][4]) < 1e-8
+
+
+def test_fused_2d_transforms_only_where_they_apply():
+    """Not used with the FP64 or BF16 preconditioners, for d != 2, or when a spatial size exceeds 80."""
+    try:
+        S.stst_set_fused_transforms(2)
+        for n_el, p, prec in [([4, 6, 7], 2, S.STST_PREC_FP64), ([4, 6, 7], 2, S.STST_PREC_BF16),
+                              ([4, 6], 2, S.STST_PREC_FP32), ([3, 4, 5, 6], 2, S.STST_PREC_FP32),
+                              ([4, 90, 6], 2, S.STST_PREC_FP32)]:
+            prob = S.Problem(len(n_el) - 1, n_el, p, prec_mode=prec)
+            prob.build_fd()
+            assert S.stst_fused_transforms_info(prob.h) == 0, (n_el, prec)
+            prob.close()
+    finally:
+        S.stst_set_fused_transforms(0)
+    for bad in (3, 10, 15, -1):
+        with pytest.raises(S.StstError):
+            S.stst_set_fused_transforms(bad)
 
 
 @pytest.mark.gpu
