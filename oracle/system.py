@@ -103,11 +103,23 @@ class Discretization:
                 f[l] = sp[l]["K2"].T
                 f[k] = sp[k]["K2"]
                 out.append((nu ** 2, f))
-        # nu L_s (x) (W + W^*)
+        # nu L_s (x) (W + W^*): the cross terms (i d_t u, -nu Delta v) + (-nu Delta u, i d_t v) after
+        # integrating by parts in space, which needs u and v to vanish on the boundary. With the
+        # unrestricted spatial functions (the lifting of boundary data, Sec. 2.2: f - S u_lift) the
+        # terms stay as they are: -i nu K_t (x) K2_l^T + i nu K_t^T (x) K2_l (K2^T[i,j] = int b_j b''_i).
         for l in range(1, d + 1):
-            f = [Wsym] + M[1:]
-            f[l] = sp[l]["L"]
-            out.append((nu, f))
+            if full_space:
+                Kt = self.full[0]["K"] if full_time else restrict_time(self.full[0]["K"], self.formulation)
+                f = [Kt] + M[1:]
+                f[l] = sp[l]["K2"].T
+                out.append((-1j * nu, f))
+                f = [Kt.T] + M[1:]
+                f[l] = sp[l]["K2"]
+                out.append((1j * nu, f))
+            else:
+                f = [Wsym] + M[1:]
+                f[l] = sp[l]["L"]
+                out.append((nu, f))
         if with_potential and self.potential:
             V = self.potential
             R = len(V)
