@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--solver", default="pcg", choices=["pcg", "ir"])
     ap.add_argument("--autotune", type=int, default=1,
                     help="mode-product tiles: 1 measured per shape, 0 default, 10 rpt + cpt forced (stst_set_autotune)")
+    ap.add_argument("--tw-p", type=int, default=3, help="degree of the travelling-wave workload (--config tw)")
+    ap.add_argument("--tw-nel", type=int, default=64, help="elements per direction of --config tw")
     ap.add_argument("--fused-transforms", type=int, default=0,
                     help="d = 2, FP32 preconditioner: 0 chosen per shape, 1 separate mode products, 2 fused, "
                          "11..14 fused with 1..4 CTAs per time index (stst_set_fused_transforms)")
@@ -161,10 +163,37 @@ def traffic_for(kernel):
         return None
 
 
+# Table 1 of the paper (P-hat-CG on the travelling wave, 1e-8 from x0 = 0, one CPU thread at 1 GHz):
+# (p, n_el) -> (iterations, seconds including the preconditioner setup)
+TABLE1 = {(2, 8): (7, 0.0426), (2, 16): (7, 0.0659), (2, 32): (7, 0.2992), (2, 64): (7, 2.7304),
+          (3, 8): (8, 0.0302), (3, 16): (9, 0.0982), (3, 32): (8, 0.4703), (3, 64): (8, 4.7142),
+          (4, 8): (10, 0.0427), (4, 16): (10, 0.2289), (4, 32): (10, 1.2329), (4, 64): (10, 9.0219)}
+TW = {"p": 3, "n_el": 64}  # set from --tw-p / --tw-nel
+
+
 def workload(cfg_name):
     from inputs import CONFIGS, potential, initial_factors
-    cfg = CONFIGS[cfg_name]
+    cfg = dict(CONFIGS[cfg_name])
+    if cfg_name == "tw":
+        cfg["p"] = TW["p"]
+        cfg["n_el"] = [TW["n_el"]] * 3
     return cfg, potential(cfg), initial_factors(cfg)
+
+
+def tw_rhs(prob):
+    """Right-hand side of the travelling wave: its forcing and its Dirichlet and initial values (from u
+    on the whole space-time grid) through stst_rhs_lift; the grids are built on the device."""
+    import torch
+    from inputs import travelling_wave
+    u_fn, f_fn = travelling_wave(xp=torch)
+    g = [prob.quad_points(l) for l in range(3)]
+    t, x1, x2 = g[0].view(1, 1, -1), g[1].view(1, -1, 1), g[2].view(-1, 1, 1)
+    u_qp = u_fn(t, x1, x2).to(torch.complex128).contiguous().view(-1)
+    f_qp = f_fn(t, x1, x2).to(torch.complex128).contiguous().view(-1)
+    b = prob.rhs_lift(f_qp, u_qp)
+    torch.cuda.synchronize()
+    del u_qp, f_qp
+    return b
 
 
 def sample_1d(prob, fn, l):
@@ -184,6 +213,8 @@ def build_problem(cfg, V, u0, prec, stream, formulation="ls"):
     if V:
         cols = [sample_1d(prob, term[l - 1], l) for term in V for l in range(1, d + 1)]
         prob.set_potential(torch.tensor(np.concatenate(cols), dtype=torch.float64, device="cuda"), len(V))
+    if u0 is None:  # the travelling wave
+        return prob, tw_rhs(prob)
     grids = [prob.quad_points(l).cpu().numpy() for l in range(1, d + 1)]
     U = np.ones([1] * d, dtype=complex)
     for l, g in enumerate(u0):
@@ -200,7 +231,9 @@ def workload_name(name, cfg, tol):
     d = cfg["d"]
     space = "x".join(str(v) for v in cfg["n_el"][1:])
     pot = {None: "V=0", "harmonic": "harmonic V in [0,10]", "bump": "Gaussian bump V"}[cfg["potential"]]
-    u0 = "sin(pi x) initial datum" if cfg["u0"] == "sine" else "windowed Gaussian wavepacket u0"
+    u0 = {"sine": "sin(pi x) initial datum", "travelling_wave":
+          "travelling wave of Sec. 6.2 with its forcing, Dirichlet and initial values"}.get(cfg["u0"],
+                                                                                         "windowed Gaussian wavepacket u0")
     return (f"{name}: {d}D+t p={cfg['p']} {space} x {cfg['n_el'][0]} elements, {pot}, {u0}, complex128, "
             f"tol {tol:g}")
 
@@ -669,7 +702,8 @@ def run_ours(args):
         "ms_per_step": ms,
         "higher_is_better": False,
         "scaling": "weak",
-        "vs_baseline": None,
+        "vs_baseline": (ms / 1e3 / TABLE1[(cfg["p"], cfg["n_el"][0])][1]
+                        if args.config == "tw" and (cfg["p"], cfg["n_el"][0]) in TABLE1 else None),
         "dtype": {"fp64": "f64", "fp32": "f64+f32", "bf16": "f64+f32+bf16"}[args.prec],
         "data": "synthetic",
         "config": {"workload": workload_name(args.config, cfg, tol) + (", ultraweak formulation (Sec. 4.4)"
@@ -695,8 +729,13 @@ def run_ours(args):
         "roofline": roof,
         "clocks": clocks,
         "e2e": {"value": e2e_ms / 1e3, "unit": "s", "h2d_bytes_per_step": 16 * n_dof, "d2h_bytes_per_step": 16 * n_dof},
-        "paper_context": {"table": "Table 1, p=3, n_el=64, V=0 travelling wave, 1 CPU thread at 1 GHz",
-                          "seconds": 4.7142, "iterations": 8},
+        "paper_context": ({"table": f"Table 1, p={cfg['p']}, n_el={cfg['n_el'][0]}, this travelling wave, 1 CPU "
+                                    f"thread at 1 GHz (vs_baseline = value / seconds)",
+                           "seconds": TABLE1[(cfg["p"], cfg["n_el"][0])][1],
+                           "iterations": TABLE1[(cfg["p"], cfg["n_el"][0])][0]}
+                          if args.config == "tw" and (cfg["p"], cfg["n_el"][0]) in TABLE1 else
+                          {"table": "Table 1, p=3, n_el=64, V=0 travelling wave, 1 CPU thread at 1 GHz",
+                           "seconds": 4.7142, "iterations": 8}),
     }
     if rank == 0 and world == 1 and args.cpu_baseline == "on":
         cb = cpu_baseline(args.config, iters_full=None, formulation=args.formulation)
@@ -727,20 +766,29 @@ def _oracle_threads():
         return os.cpu_count()
 
 
-def cpu_baseline(cfg_name, iters_full=None, sample_iters=2, formulation="ls"):
-    """The oracle timed on this host: setup + `sample_iters` PCG iterations, extrapolated to the full count."""
-    import numpy as np
-    from inputs import CONFIGS, potential, initial_factors, product_fn
-    from oracle import fd, pcg, rhs
+def oracle_problem(cfg_name, formulation="ls"):
+    """The oracle's discretisation and right-hand side of a workload."""
+    from inputs import potential, initial_factors, product_fn, travelling_wave
+    from oracle import rhs
     from oracle.system import Discretization
-    cfg = CONFIGS[cfg_name]
+    cfg, _, _ = workload(cfg_name)
     d = cfg["d"]
     disc = Discretization(cfg["n_el"], [cfg["p"]] * (d + 1), T=cfg["T"], nu=cfg["nu"], potential=potential(cfg),
                           formulation=formulation)
-    if formulation == "uw":
+    if cfg["u0"] == "travelling_wave":
+        u_fn, f_fn = travelling_wave()
+        b, _ = rhs.full_lifting(disc, u_fn, f_fn)
+    elif formulation == "uw":
         b = rhs.rhs_ultraweak(disc, None, product_fn(initial_factors(cfg)))
     else:
         b, _ = rhs.rhs_initial(disc, None, product_fn(initial_factors(cfg)))
+    return cfg, disc, b
+
+
+def cpu_baseline(cfg_name, iters_full=None, sample_iters=2, formulation="ls"):
+    """The oracle timed on this host: setup + `sample_iters` PCG iterations, extrapolated to the full count."""
+    from oracle import fd, pcg
+    cfg, disc, b = oracle_problem(cfg_name, formulation)
     terms = disc.terms()
     x_ref = None
     if iters_full is None:
@@ -769,19 +817,9 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import numpy as np
-    from inputs import CONFIGS, potential, initial_factors, product_fn
-    from oracle import fd, pcg, rhs
-    from oracle.system import Discretization
-    cfg = CONFIGS[args.config]
-    d = cfg["d"]
+    from oracle import fd, pcg
     formulation = args.formulation
-    disc = Discretization(cfg["n_el"], [cfg["p"]] * (d + 1), T=cfg["T"], nu=cfg["nu"], potential=potential(cfg),
-                          formulation=formulation)
-    if formulation == "uw":
-        b = rhs.rhs_ultraweak(disc, None, product_fn(initial_factors(cfg)))
-    else:
-        b, _ = rhs.rhs_initial(disc, None, product_fn(initial_factors(cfg)))
+    cfg, disc, b = oracle_problem(args.config, formulation)
     F = fd.FastDiagonalization(disc)
     _, iters_full, _, _ = pcg.pcg(disc.apply, F.apply, b, tol=cfg.get("tol", 1e-8), maxit=200)
     vals = []
@@ -801,6 +839,7 @@ def run_reference(args):
 
 def main():
     args = parse()
+    TW["p"], TW["n_el"] = args.tw_p, args.tw_nel
     if args.impl == "reference":
         run_reference(args)
     else:

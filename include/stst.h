@@ -163,6 +163,27 @@ int stst_apply_prec(stst_handle h, const double *r, double *s);
 int stst_rhs(stst_handle h, const double *f_qp, const double *u0_qp, double *rhs, double *c0);
 
 /*
+ * stst_rhs_lift: right-hand side with general (non-homogeneous) Dirichlet and initial data, the
+ * lifting of Sec. 2.2 with the data taken from a function u given on the whole space-time cylinder
+ * (as in the experiments of Sec. 6, whose exact solutions supply their boundary values):
+ *   G = (M_t^{-1} x M_1^{-1} x ... x M_d^{-1}) (u, B)  over ALL basis functions (no boundary conditions),
+ *   g_h = the part of G on the basis functions nonzero at t = 0 or on the spatial boundary
+ *         (time index 0, spatial indices 0 and m_l - 1; zero elsewhere),
+ *   rhs_i = (f - S_V g_h, S_V B_i), i.e. int f conj(S_V B_i) - sum_j A_full(B_j, B_i) g_j.
+ * The discrete solution is u_h = u_bar + g_h (u_bar the reduced solution on the interior functions).
+ *   f_qp  NULL (f = 0) or device complex array on the space-time quadrature grid (layout of stst_rhs)
+ *   u_qp  device complex array on the same grid: the function whose boundary and initial values are
+ *         imposed (required)
+ *   rhs   device, N_dof complex (output)
+ *   xd    NULL or device complex array of prod_l m_l entries, m_l = n_el_l + p_l the full number of
+ *         basis functions per direction, time fastest: receives g_h's coefficients on the full basis.
+ * Least-squares handles only (STST_ERR_ARG for STST_FORM_UW or u_qp == NULL). Allocates stream-ordered
+ * temporaries of a few grid-sized arrays (STST_ERR_OOM if that fails); stream-ordered, returns
+ * without waiting.
+ */
+int stst_rhs_lift(stst_handle h, const double *f_qp, const double *u_qp, double *rhs, double *xd);
+
+/*
  * stst_rhs_noalloc: the same right-hand side as stst_rhs, computed without
  * taking any device memory at call time. (The paper has no counterpart: this
  * is an interface for callers that cannot allocate.) stst_rhs with a forcing

@@ -12,6 +12,8 @@ stand in for them exactly; sizes follow the 2D+t performance study, Table 1):
   c3p2 / c3p4   3D+t, p=2 / 4, 32^3 x 64 elements, V = 0 or a Gaussian bump, wavepacket (seed 1)
   c4     128 2D+t instances, n_el in {16..96}^2 x {16..96}, p in {2,3,4}, seeded per instance (4 + i)
   c5     2D+t, p=3, 48^2 x 48, harmonic V, wavepackets with drawn centre/width/momentum/phase
+  tw     the travelling wave of the paper's performance study (Sec. 6.2, Table 1): 2D+t, V = 0,
+         u = a exp(-i (|x|^2 + t^2) / w^2), w = 0.2, with its Dirichlet and initial values imposed
 """
 import math
 
@@ -25,6 +27,7 @@ CONFIGS = {
     "c3p2_bump": dict(d=3, n_el=[64, 32, 32, 32], p=2, T=1.0, nu=1.0, potential="bump", u0=("wavepacket", 1), tol=1e-8),
     "c3p4_bump": dict(d=3, n_el=[64, 32, 32, 32], p=4, T=1.0, nu=1.0, potential="bump", u0=("wavepacket", 1), tol=1e-8),
     "c5": dict(d=2, n_el=[48, 48, 48], p=3, T=1.0, nu=1.0, potential="harmonic", u0=("wavepacket", 5), tol=1e-8),
+    "tw": dict(d=2, n_el=[64, 64, 64], p=3, T=1.0, nu=1.0, potential=None, u0="travelling_wave", tol=1e-8),
 }
 
 
@@ -102,8 +105,10 @@ def wavepacket_factors(par):
 
 
 def initial_factors(cfg, seed_offset=0):
-    """Separable factors of u0 for a workload."""
+    """Separable factors of u0 for a workload (None for the travelling wave: its data come from u)."""
     d = cfg["d"]
+    if cfg["u0"] == "travelling_wave":
+        return None
     if cfg["u0"] == "sine":
         return [lambda x: np.sin(np.pi * np.asarray(x)) + 0j for _ in range(d)]
     kind, seed = cfg["u0"]
@@ -138,3 +143,24 @@ def c4_instances(n=128):
 def random_complex(n, seed):
     rng = np.random.default_rng(seed)
     return rng.standard_normal(n) + 1j * rng.standard_normal(n)
+
+
+# ---- the travelling wave of the performance study (Sec. 6.2, Table 1) ------------------------------
+TW_OMEGA = 0.2
+
+
+def travelling_wave(omega=TW_OMEGA, xp=np):
+    """(u, f) for u = a exp(-i (x_1^2 + x_2^2 + t^2) / w^2), a = (2 / w^2)^(1/4), and the forcing the
+    paper prints for it, f = i u_t - Delta u = a (4i / w^2 + 4 |x|^2 / w^4 + 2 t / w^2) exp(...) (nu = 1).
+    xp: the array module the callables use (numpy, or torch for device grids)."""
+    a = (2.0 / omega ** 2) ** 0.25
+    w2 = omega ** 2
+
+    def u(t, x1, x2):
+        return a * xp.exp(-1j * (x1 ** 2 + x2 ** 2 + t ** 2) / w2)
+
+    def f(t, x1, x2):
+        r2 = x1 ** 2 + x2 ** 2
+        return a * (4j / w2 + 4 * r2 / w2 ** 2 + 2 * t / w2) * xp.exp(-1j * (r2 + t ** 2) / w2)
+
+    return u, f

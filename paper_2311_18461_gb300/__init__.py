@@ -9,7 +9,7 @@ library needs the built extension and raises if it is missing.
 from ._lib import (StstError, lib, library_path, stst_create, stst_create2, STST_FORM_LS, STST_FORM_UW,
                    stst_destroy, stst_strerror, stst_sizes, stst_quadrature_points, stst_assemble_1d,
                    stst_set_potential, stst_build_fd, stst_apply_sys, stst_apply_prec, stst_rhs,
-                   stst_rhs_noalloc, stst_pcg_solve, stst_ir_solve, stst_profile, stst_profile_read,
+                   stst_rhs_noalloc, stst_rhs_lift, stst_pcg_solve, stst_ir_solve, stst_profile, stst_profile_read,
                    stst_plan_info, stst_batch_create, stst_batch_solve, stst_batch_destroy, stst_set_autotune,
                    stst_set_time_solver, stst_set_fused_transforms, stst_fused_transforms_info,
                    stst_time_solver_info, stst_last_cuda_error, stst_tile_info, stst_ws_create,
@@ -21,7 +21,7 @@ from ._lib import (StstError, lib, library_path, stst_create, stst_create2, STST
 __all__ = ["StstError", "lib", "library_path", "stst_create", "stst_create2", "STST_FORM_LS", "STST_FORM_UW",
            "stst_destroy", "stst_strerror", "stst_sizes", "stst_quadrature_points", "stst_assemble_1d",
            "stst_set_potential", "stst_build_fd", "stst_apply_sys", "stst_apply_prec", "stst_rhs",
-           "stst_rhs_noalloc", "stst_pcg_solve", "stst_ir_solve", "stst_profile", "stst_profile_read",
+           "stst_rhs_noalloc", "stst_rhs_lift", "stst_pcg_solve", "stst_ir_solve", "stst_profile", "stst_profile_read",
            "stst_plan_info", "stst_batch_create", "stst_batch_solve", "stst_batch_destroy",
            "stst_set_autotune", "stst_set_time_solver", "stst_set_fused_transforms",
            "stst_fused_transforms_info", "stst_time_solver_info", "stst_last_cuda_error", "stst_tile_info",

@@ -50,6 +50,7 @@ def lib():
             "stst_apply_prec": [P, P, P],
             "stst_rhs": [P, P, P, P, P],
             "stst_rhs_noalloc": [P, P, P, P, P],
+            "stst_rhs_lift": [P, P, P, P, P],
             "stst_pcg_solve": [P, P, P, D, I, IP, DP],
             "stst_ir_solve": [P, P, P, D, I, D, I, IP, IP, DP],
             "stst_profile": [P, I],
@@ -194,6 +195,10 @@ def stst_rhs(h, f_qp, u0_qp, rhs, c0):
 
 def stst_rhs_noalloc(h, f_qp, u0_qp, rhs, c0):
     return _chk(lib().stst_rhs_noalloc(h, _ptr(f_qp), _ptr(u0_qp), _ptr(rhs), _ptr(c0)), "stst_rhs_noalloc")
+
+
+def stst_rhs_lift(h, f_qp, u_qp, rhs, xd):
+    return _chk(lib().stst_rhs_lift(h, _ptr(f_qp), _ptr(u_qp), _ptr(rhs), _ptr(xd)), "stst_rhs_lift")
 
 
 def stst_pcg_solve(h, rhs, x, tol, maxit):
@@ -430,6 +435,19 @@ class Problem:
         c0 = self.torch.zeros(self.N_s, dtype=self.torch.complex128, device=self.device) if want_c0 else None
         stst_rhs(self.h, f_qp, u0_qp, b, c0)
         return (b, c0) if want_c0 else b
+
+    def rhs_lift(self, f_qp, u_qp, want_xd=False):
+        """Right-hand side with the Dirichlet and initial values of u_qp imposed (stst_rhs_lift); with
+        want_xd also the lifting's coefficients on the full basis (prod_l (n_el_l + p_l), time fastest)."""
+        b = self.vec()
+        xd = None
+        if want_xd:
+            m_tot = 1
+            for l in range(self.d + 1):
+                m_tot *= self.n_el[l] + self.p[l]
+            xd = self.torch.zeros(m_tot, dtype=self.torch.complex128, device=self.device)
+        stst_rhs_lift(self.h, f_qp, u_qp, b, xd)
+        return (b, xd) if want_xd else b
 
     def pcg(self, rhs, x=None, tol=1e-8, maxit=200):
         x = self.vec() if x is None else x

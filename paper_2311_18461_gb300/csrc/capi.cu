@@ -842,6 +842,12 @@ int stst_rhs(stst_handle h, const double *f_qp, const double *u0_qp, double *rhs
   return rhs_compute(h, f_qp, u0_qp, rhs, c0);
 }
 
+int stst_rhs_lift(stst_handle h, const double *f_qp, const double *u_qp, double *rhs, double *xd) {
+  STST_TRY(check(h));
+  ApiScope scope(h);
+  return rhs_lift_compute(h, f_qp, u_qp, rhs, xd);
+}
+
 int stst_pcg_solve(stst_handle h, const double *rhs, double *x, double tol, int maxit, int *iters, double *relres) {
   STST_TRY(check(h));
   ApiScope scope(h);

@@ -207,6 +207,7 @@ int fd_apply(stst_problem *h, const double *r, double *s, int precision, const v
              const int *done, void *f32_scratch_a, void *f32_scratch_b, float *out32 = nullptr,
              const float *in32 = nullptr);
 int rhs_compute(stst_problem *h, const double *f_qp, const double *u0_qp, double *rhs, double *c0);
+int rhs_lift_compute(stst_problem *h, const double *f_qp, const double *u_qp, double *rhs, double *xd);
 
 int pcg_run(stst_problem *h, const double *rhs, double *x, double tol, int maxit, int *iters, double *relres);
 int ir_run(stst_problem *h, const double *rhs, double *x, double tol, int maxit, double inner_tol,

@@ -238,6 +238,218 @@ int rhs_compute(stst_problem *h, const double *f_qp, const double *u0_qp, double
 }
 
 // ------------------------------------------------------------------------------------------------
+// Right-hand side with general Dirichlet and initial data (the lifting of Sec. 2.2, with the data taken
+// from a function u given on the whole space-time cylinder, as in the experiments of Sec. 6):
+//   G = (M_t^{-1} x M_1^{-1} x ... x M_d^{-1}) (u, B)   the L2 projection of u onto the full tensor
+//       spline space (all basis functions, no boundary conditions);
+//   g_h keeps the coefficients of G on the basis functions that do not vanish at t = 0 or on the
+//       spatial boundary (time index 0, spatial indices 0 and m_l - 1), zero elsewhere;
+//   rhs_i = (f - S_V g_h, S_V B_i), i.e. the load of f minus the method's bilinear form between the
+//       lifting and the test functions.
+// S_V g_h is evaluated at the tensor Gauss points of the load and integrated by the load's own rule,
+// which is exact for these piecewise polynomials (the potential uses that rule in the system matrices
+// too), so the result equals the load minus the full-basis Kronecker operator applied to g_h.
+// ------------------------------------------------------------------------------------------------
+
+// out[o, q, c] = (sre + i sim) sum_{a = 0..p} d^der b_{e(q)+a}(x_q) in[o, e(q)+a, c]  (+ out if accumulate);
+// the input runs over all m = n_el + p basis functions of the mode, the output over its Q points.
+__global__ void k_eval_mode(const double2 *__restrict__ in, double2 *__restrict__ out, const double *__restrict__ tab,
+                            int p, int nq, int m, int Q, long long inner, long long outer, int der, double sre,
+                            double sim, int accumulate) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= outer * Q * inner) return;
+  const long long c = idx % inner;
+  const long long t = idx / inner;
+  const int q = (int)(t % Q);
+  const long long o = t / Q;
+  const int e = q / nq;
+  double ax = 0.0, ay = 0.0;
+  for (int a = 0; a <= p; ++a) {
+    const double b = tab[((long long)q * (p + 1) + a) * 3 + der];
+    const double2 v = in[(o * m + e + a) * inner + c];
+    ax += b * v.x;
+    ay += b * v.y;
+  }
+  double rx = sre * ax - sim * ay, ry = sre * ay + sim * ax;
+  if (accumulate) {
+    const double2 prev = out[idx];
+    rx += prev.x;
+    ry += prev.y;
+  }
+  out[idx] = make_double2(rx, ry);
+}
+
+// keep the coefficients of the basis functions that are nonzero at t = 0 or on the spatial boundary
+__global__ void k_mask_lift(double2 *__restrict__ G, int d, int m0, int m1, int m2, int m3, long long total) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  long long r = idx;
+  const int it = (int)(r % m0);
+  r /= m0;
+  bool keep = it == 0;
+  const int ms[3] = {m1, m2, m3};
+  for (int l = 0; l < d; ++l) {
+    const int i = (int)(r % ms[l]);
+    r /= ms[l];
+    keep = keep || i == 0 || i == ms[l] - 1;
+  }
+  if (!keep) G[idx] = make_double2(0.0, 0.0);
+}
+
+// out += s a
+__global__ void k_axpy_c(double2 *__restrict__ out, const double2 *__restrict__ a, double s, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double2 o = out[i];
+  const double2 v = a[i];
+  o.x += s * v.x;
+  o.y += s * v.y;
+  out[i] = o;
+}
+
+int rhs_lift_compute(stst_problem *h, const double *f_qp, const double *u_qp, double *rhs, double *xd) {
+  if (h->formulation != STST_FORM_LS || !u_qp || !rhs) return STST_ERR_ARG;
+  cudaStream_t st = h->stream;
+  const int d = h->d;
+  int Q[STST_MAXD + 1], m[STST_MAXD + 1];
+  long long Qtot = 1, Mtot = 1;
+  for (int l = 0; l <= d; ++l) {
+    Q[l] = h->dir[l].Q();
+    m[l] = h->dir[l].m;
+    Qtot *= Q[l];
+    Mtot *= m[l];
+  }
+  // every intermediate tensor has at most Qtot entries (m_l <= Q_l: at least p + 1 points per element)
+  std::vector<void *> owned;
+  auto get = [&](void **ptr, size_t bytes) -> int {
+    cudaError_t e = cudaMallocAsync(ptr, bytes, st);
+    if (e != cudaSuccess) {
+      stst_last_cuda = e;
+      return STST_ERR_OOM;
+    }
+    owned.push_back(*ptr);
+    return STST_OK;
+  };
+  auto release = [&]() {
+    for (void *q : owned) cudaFreeAsync(q, st);
+  };
+  int status = STST_OK;
+  do {
+    double2 *A, *B, *G, *SG;
+    if ((status = get((void **)&A, sizeof(double2) * Qtot)) != STST_OK) break;
+    if ((status = get((void **)&B, sizeof(double2) * Qtot)) != STST_OK) break;
+    if ((status = get((void **)&G, sizeof(double2) * Mtot)) != STST_OK) break;
+    if ((status = get((void **)&SG, sizeof(double2) * Qtot)) != STST_OK) break;
+    double *Mf[STST_MAXD + 1], *Cf[STST_MAXD + 1];
+    for (int l = 0; l <= d && status == STST_OK; ++l) {
+      const DirInfo &D = h->dir[l];
+      if ((status = get((void **)&Mf[l], sizeof(double) * D.m * (2 * D.p + 1))) != STST_OK) break;
+      if ((status = get((void **)&Cf[l], sizeof(double) * D.m * (D.p + 1))) != STST_OK) break;
+      if ((status = launch_assemble_band(MK_M, D.p, D.n_el, D.len, D.nq, 0, D.m, D.m, nullptr, Mf[l], st)) != STST_OK)
+        break;
+      BandMat bm;
+      bm.d = Mf[l];
+      bm.n = D.m;
+      bm.p = D.p;
+      status = launch_mass_cholesky(bm, Cf[l], h->flags, st);
+    }
+    if (status != STST_OK) break;
+    // (u, B) over all basis functions, mode by mode
+    long long ext[STST_MAXD + 1];
+    for (int l = 0; l <= d; ++l) ext[l] = Q[l];
+    const double2 *src = (const double2 *)u_qp;
+    double2 *bufs[2] = {A, B};
+    int cur = 0;
+    for (int l = 0; l <= d && status == STST_OK; ++l) {
+      long long inner = 1, outer = 1;
+      for (int k = 0; k < l; ++k) inner *= ext[k];
+      for (int k = l + 1; k <= d; ++k) outer *= ext[k];
+      double2 *dst = (l == d) ? G : bufs[cur];
+      const DirInfo &D = h->dir[l];
+      const long long total = outer * D.m * inner;
+      k_contract<double2><<<grid_for(total, 128), 128, 0, st>>>(src, dst, h->tab[l], h->qwts[l], D.p, D.nq, D.n_el,
+                                                                 0, D.m, D.Q(), inner, outer, 0, 1.0, 0.0, 0);
+      if (cudaGetLastError() != cudaSuccess) status = STST_ERR_CUDA;
+      ext[l] = D.m;
+      src = dst;
+      cur ^= 1;
+    }
+    if (status != STST_OK) break;
+    // G = M^{-1} (u, B) with the full mass matrix of every direction
+    for (int l = 0; l <= d; ++l) {
+      long long inner = 1, outer = 1;
+      for (int k = 0; k < l; ++k) inner *= m[k];
+      for (int k = l + 1; k <= d; ++k) outer *= m[k];
+      k_mass_solve<<<grid_for(inner * outer, 128), 128, 0, st>>>(G, Cf[l], m[l], h->dir[l].p, inner, outer);
+    }
+    k_mask_lift<<<grid_for(Mtot, 256), 256, 0, st>>>(G, d, m[0], d >= 1 ? m[1] : 1, d >= 2 ? m[2] : 1,
+                                                     d >= 3 ? m[3] : 1, Mtot);
+    if (cudaGetLastError() != cudaSuccess) {
+      status = STST_ERR_CUDA;
+      break;
+    }
+    if (xd) {
+      const cudaError_t e = cudaMemcpyAsync(xd, G, sizeof(double2) * Mtot, cudaMemcpyDeviceToDevice, st);
+      if (e != cudaSuccess) {
+        stst_last_cuda = e;
+        status = STST_ERR_CUDA;
+        break;
+      }
+    }
+    // SG = -S_V g_h at the quadrature points: -i d_t g + nu sum_l d_l^2 g - V g
+    struct EvalTerm { int der[STST_MAXD + 1]; double sre, sim; bool pot; };
+    std::vector<EvalTerm> terms;
+    terms.push_back({{1, 0, 0, 0}, 0.0, -1.0, false});
+    for (int l = 1; l <= d; ++l) {
+      EvalTerm t = {{0, 0, 0, 0}, h->nu, 0.0, false};
+      t.der[l] = 2;
+      terms.push_back(t);
+    }
+    if (h->pot_rank > 0) terms.push_back({{0, 0, 0, 0}, 1.0, 0.0, true});
+    for (size_t k = 0; k < terms.size() && status == STST_OK; ++k) {
+      const EvalTerm &t = terms[k];
+      for (int l = 0; l <= d; ++l) ext[l] = m[l];
+      const double2 *s2 = G;
+      int c2 = 0;
+      for (int l = 0; l <= d && status == STST_OK; ++l) {
+        long long inner = 1, outer = 1;
+        for (int j = 0; j < l; ++j) inner *= ext[j];
+        for (int j = l + 1; j <= d; ++j) outer *= ext[j];
+        const bool last = l == d;
+        double2 *dst = (last && !t.pot) ? SG : bufs[c2];
+        const DirInfo &D = h->dir[l];
+        const long long total = outer * D.Q() * inner;
+        k_eval_mode<<<grid_for(total, 128), 128, 0, st>>>(s2, dst, h->tab[l], D.p, D.nq, D.m, D.Q(), inner, outer,
+                                                          t.der[l], last ? t.sre : 1.0, last ? t.sim : 0.0,
+                                                          (last && !t.pot && k > 0) ? 1 : 0);
+        if (cudaGetLastError() != cudaSuccess) status = STST_ERR_CUDA;
+        ext[l] = D.Q();
+        s2 = dst;
+        c2 ^= 1;
+      }
+      if (t.pot && status == STST_OK) {  // SG -= V g_h
+        double2 *E0 = (double2 *)s2, *FV = bufs[c2];
+        k_mul_potential<<<grid_for(Qtot, 256), 256, 0, st>>>(E0, FV, Q[0], d, Q[1], d >= 2 ? Q[2] : 1,
+                                                              d >= 3 ? Q[3] : 1, h->pot_rank, h->pot_bufs[0], Qtot);
+        k_axpy_c<<<grid_for(Qtot, 256), 256, 0, st>>>(SG, FV, -1.0, Qtot);
+        if (cudaGetLastError() != cudaSuccess) status = STST_ERR_CUDA;
+      }
+    }
+    if (status != STST_OK) break;
+    if (f_qp) {
+      k_axpy_c<<<grid_for(Qtot, 256), 256, 0, st>>>(SG, (const double2 *)f_qp, 1.0, Qtot);
+      if (cudaGetLastError() != cudaSuccess) {
+        status = STST_ERR_CUDA;
+        break;
+      }
+    }
+    status = rhs_compute(h, (const double *)SG, nullptr, rhs, nullptr);
+  } while (false);
+  release();
+  return status;
+}
+
+// ------------------------------------------------------------------------------------------------
 // Allocation-free variant of stst_rhs (stst_rhs_noalloc). Its temporaries live in one file-scope
 // device array of fixed size instead of memory taken from the allocator at call time. The array is
 // part of the module: every GPU that loads this library holds it until the process exits. All calls
