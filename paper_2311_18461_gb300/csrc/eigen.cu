@@ -13,15 +13,121 @@
 #include <type_traits>
 
 // ------------------------------------------------------------------------------------------------
-// FP32 first approximation on one CTA (n <= 128): with M = C C^T (banded Cholesky) the pencil becomes
-// the symmetric matrix A = C^{-1} L C^{-T}; Householder reflections reduce A to tridiagonal T,
-// bisection on Sturm counts gives every eigenvalue of T (thread j finds the j-th smallest),
-// inverse iteration with partial pivoting gives its eigenvector, the reflections are applied back
-// and U0 = C^{-T} Q. Outputs U0 (row-major n x n, column j = eigenvector j) and lam0 ascending.
+// FP32 first approximation (n <= 128) in three kernels. With M = C C^T (banded Cholesky) the pencil
+// becomes the symmetric matrix A = C^{-1} L C^{-T}; Householder reflections reduce A to tridiagonal T
+// (k_eig_tridiag, one CTA: the reduction is a chain of dependent steps). Every eigenvalue of T is then
+// found by multisection on Sturm counts, one warp per eigenvalue (k_eig_values), and every eigenvector
+// by inverse iteration with partial pivoting, the reflections applied back and U0 = C^{-T} Q, one warp
+// per eigenvalue or cluster of close eigenvalues (k_eig_vectors): these steps are independent across
+// the eigenvalues, so they run on ceil(n / 4) CTAs at once.
+// Scratch (floats, EigScratch): the reflectors (column k holds v_k on rows k+1..), the diagonal and
+// off-diagonal of T, the betas, the band of C, the eigenvalues of T and the eigenvectors of T.
 // ------------------------------------------------------------------------------------------------
+// C C^T = M for the band of M (n x (2P+1), row-major) into C (n x (P+1), C[i(P+1)+k] = C_{i,i-P+k}),
+// one thread; rows i-1 .. i-P of C stay in registers (W[r] = row i-1-r), so the recurrence runs on
+// register operands. A non-positive pivot sets bit 0 of *flags.
+template <int P>
+__device__ void eig_band_cholesky(const float *Ms, float *C, int n, int *flags) {
+  constexpr int BW = 2 * P + 1;
+  float W[P][P + 1];
+#pragma unroll
+  for (int r = 0; r < P; ++r)
+#pragma unroll
+    for (int k = 0; k <= P; ++k) W[r][k] = 0.f;
+  for (int i = 0; i < n; ++i) {
+    float row[P + 1];
+    float mrow[P + 1];
+#pragma unroll
+    for (int k = 0; k <= P; ++k) mrow[k] = Ms[i * BW + k];
+#pragma unroll
+    for (int k = 0; k <= P; ++k) {
+      const int j = i - P + k;  // column of entry k
+      float s = mrow[k];
+      // s -= sum_{m < j} C[i][m] C[j][m]: entry kk of row i is column i-P+kk, row j is W[P-1-k] there
+#pragma unroll
+      for (int kk = 0; kk < k; ++kk) {
+        const int e = kk - k + P;  // index of column i-P+kk in row j's band
+        if (k < P && e >= 0) s -= row[kk] * W[P - 1 - k][e];
+        if (k == P) s -= row[kk] * row[kk];
+      }
+      if (j < 0) {
+        row[k] = 0.f;
+      } else if (k < P) {
+        row[k] = s / W[P - 1 - k][P];
+      } else {
+        if (!(s > 0.f)) {
+          atomicOr(flags, 1);
+          s = 1.f;
+        }
+        row[P] = sqrtf(s);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k <= P; ++k) C[i * (P + 1) + k] = row[k];
+#pragma unroll
+    for (int r = P - 1; r > 0; --r)
+#pragma unroll
+      for (int k = 0; k <= P; ++k) W[r][k] = W[r - 1][k];
+#pragma unroll
+    for (int k = 0; k <= P; ++k) W[0][k] = row[k];
+  }
+}
+
+// Column of Z = C^{-1} B by forward substitution (C lower banded, C[i(P+1)+k] = C_{i,i-P+k}), the last P
+// values in registers; B's entry in row i is bval(i), Z's row i goes to out[i * ostride].
+template <int P, typename F>
+__device__ void eig_lower_solve(const float *C, const float *rinv, int n, F bval, float *out, int ostride) {
+  float win[P];  // win[r] = z_{i-1-r}
+#pragma unroll
+  for (int r = 0; r < P; ++r) win[r] = 0.f;
+  for (int i = 0; i < n; ++i) {
+    float s = bval(i);
+#pragma unroll
+    for (int r = 0; r < P; ++r)
+      if (i - 1 - r >= 0) s -= C[i * (P + 1) + (P - 1 - r)] * win[r];
+    const float z = s * rinv[i];
+    out[i * ostride] = z;
+#pragma unroll
+    for (int r = P - 1; r > 0; --r) win[r] = win[r - 1];
+    win[0] = z;
+  }
+}
+
+// x <- C^{-T} x by back substitution in place, the last P solved values in registers.
+template <int P>
+__device__ void eig_upper_solve(const float *C, const float *rinv, int n, float *x) {
+  float win[P];  // win[r] = x_{i+1+r} (solved)
+#pragma unroll
+  for (int r = 0; r < P; ++r) win[r] = 0.f;
+  for (int i = n - 1; i >= 0; --i) {
+    float t = x[i];
+#pragma unroll
+    for (int r = 0; r < P; ++r)
+      if (i + 1 + r < n) t -= C[(i + 1 + r) * (P + 1) + (P - 1 - r)] * win[r];
+    const float xi = t * rinv[i];
+    x[i] = xi;
+#pragma unroll
+    for (int r = P - 1; r > 0; --r) win[r] = win[r - 1];
+    win[0] = xi;
+  }
+}
+
+struct EigScratch {
+  float *H, *dg, *od, *bet, *C, *pv, *Xt;
+  __host__ __device__ EigScratch(float *base, int n, int p) {
+    H = base;
+    dg = H + n * n;
+    od = dg + n;
+    bet = od + n;
+    C = bet + n;
+    pv = C + n * (p + 1);
+    Xt = pv + n;
+  }
+  static size_t floats(int n, int p) { return 2 * (size_t)n * n + 4 * (size_t)n + (size_t)n * (p + 1); }
+};
+
 __global__ void __launch_bounds__(512) k_eig_tridiag(const double *__restrict__ Mb, const double *__restrict__ Lb,
-                                                     int n, int p, double *U0, double *lam0, float *lu, int *flags,
-                                                     int lu_smem) {
+                                                     int n, int p, float *scratch, int *flags) {
   extern __shared__ __align__(16) float sm[];
   const int ld = n + 1;
   float *A = sm;                   // n x ld: matrix, then Householder vectors below the diagonal
@@ -31,11 +137,9 @@ __global__ void __launch_bounds__(512) k_eig_tridiag(const double *__restrict__ 
   float *od = dg + n;              // off-diagonal of T (od[k] = T[k+1][k])
   float *bet = od + n;             // Householder beta_k
   float *pv = bet + n;             // work vector p
-  float *wv = pv + n;              // work vector w
+  float *wv = pv + n;              // reciprocal diagonal of C
   float *Ms = wv + n;              // n x (2p+1): the bands of M and L, staged once
   float *Ls = Ms + n * (2 * p + 1);
-  if (lu_smem) lu = Ls + n * (2 * p + 1);  // 3 n^2 floats of LU rows in shared memory when they fit
-  __shared__ float red[32];
   __shared__ float bc[4];
   const int tid = threadIdx.x, nth = blockDim.x;
   const int bw = 2 * p + 1;
@@ -44,37 +148,35 @@ __global__ void __launch_bounds__(512) k_eig_tridiag(const double *__restrict__ 
     Ls[e] = (float)Lb[e];
   }
   __syncthreads();
-  // 1. banded Cholesky of M (thread 0)
+  // 1. banded Cholesky of M (thread 0, the last P rows of C in registers)
   if (tid == 0) {
-    for (int i = 0; i < n; ++i) {
-      for (int k = 0; k <= p; ++k) {
-        int j = i - p + k;
-        if (j < 0) { C[i * (p + 1) + k] = 0.f; continue; }
-        float s = Ms[i * bw + k];
-        for (int m = max(i - p, 0); m < j; ++m) s -= C[i * (p + 1) + (m - i + p)] * C[j * (p + 1) + (m - j + p)];
-        if (j < i) C[i * (p + 1) + k] = s / C[j * (p + 1) + p];
-        else {
-          if (!(s > 0.f)) { atomicOr(flags, 1); s = 1.f; }
-          C[i * (p + 1) + p] = sqrtf(s);
-        }
-      }
+    switch (p) {
+#define CASE(PP) case PP: eig_band_cholesky<PP>(Ms, C, n, flags); break;
+      CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+#undef CASE
+      default: atomicOr(flags, 1);
     }
   }
   __syncthreads();
-  // 2. Y = C^{-1} L (column j by thread j, into X), A = C^{-1} Y^T, symmetrized
+  // 2. Y = C^{-1} L (column j by thread j, into X), A = C^{-1} Y^T, symmetrized; the recurrences keep
+  //    the last p values in registers and multiply by reciprocal diagonals (wv holds them here)
+  for (int i = tid; i < n; i += nth) wv[i] = 1.f / C[i * (p + 1) + p];
+  __syncthreads();
   for (int j = tid; j < n; j += nth) {
-    for (int i = 0; i < n; ++i) {
-      float s = (abs(i - j) <= p) ? Ls[i * bw + (j - i + p)] : 0.f;
-      for (int m = max(i - p, 0); m < i; ++m) s -= C[i * (p + 1) + (m - i + p)] * X[m * ld + j];
-      X[i * ld + j] = s / C[i * (p + 1) + p];
+    auto lval = [&](int i) { return (abs(i - j) <= p) ? Ls[i * bw + (j - i + p)] : 0.f; };
+    switch (p) {
+#define CASE(PP) case PP: eig_lower_solve<PP>(C, wv, n, lval, X + j, ld); break;
+      CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+#undef CASE
     }
   }
   __syncthreads();
   for (int j = tid; j < n; j += nth) {
-    for (int i = 0; i < n; ++i) {
-      float s = X[j * ld + i];
-      for (int m = max(i - p, 0); m < i; ++m) s -= C[i * (p + 1) + (m - i + p)] * A[m * ld + j];
-      A[i * ld + j] = s / C[i * (p + 1) + p];
+    auto yval = [&](int i) { return X[j * ld + i]; };
+    switch (p) {
+#define CASE(PP) case PP: eig_lower_solve<PP>(C, wv, n, yval, A + j, ld); break;
+      CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+#undef CASE
     }
   }
   __syncthreads();
@@ -85,7 +187,9 @@ __global__ void __launch_bounds__(512) k_eig_tridiag(const double *__restrict__ 
       A[j * ld + i] = a;
     }
   __syncthreads();
-  // 3. Householder tridiagonalization: step k zeroes column k below the subdiagonal
+  // 3. Householder tridiagonalization: step k zeroes column k below the subdiagonal. Three barriers a
+  //    step: the reflector (warp 0), p = beta A v (eight lanes per row), then every warp forms
+  //    k = beta p.v / 2 itself and the rank-2 update uses w = p - k v on the fly.
   for (int k = 0; k + 2 < n; ++k) {
     const int m = n - k - 1;  // length of x = A[k+1.., k]
     if (tid < 32) {
@@ -100,20 +204,16 @@ __global__ void __launch_bounds__(512) k_eig_tridiag(const double *__restrict__ 
         float nx = sqrtf(s);
         float alpha = (x0 >= 0.f) ? -nx : nx;
         float vtv = s - x0 * x0 + (x0 - alpha) * (x0 - alpha);
-        bc[0] = alpha;
-        bc[1] = (nx > 0.f && vtv > 0.f) ? 2.f / vtv : 0.f;
-        bc[2] = x0 - alpha;
+        const float beta = (nx > 0.f && vtv > 0.f) ? 2.f / vtv : 0.f;
+        bc[1] = beta;
+        dg[k] = A[k * ld + k];
+        od[k] = (beta > 0.f) ? alpha : x0;
+        bet[k] = beta;
+        A[(k + 1) * ld + k] = x0 - alpha;  // v_0 (the rest of v is the column itself)
       }
     }
     __syncthreads();
-    const float alpha = bc[0], beta = bc[1];
-    if (tid == 0) {
-      dg[k] = A[k * ld + k];
-      od[k] = (beta > 0.f) ? alpha : A[(k + 1) * ld + k];
-      bet[k] = beta;
-      A[(k + 1) * ld + k] = bc[2];  // v_0 (the rest of v is the column itself)
-    }
-    __syncthreads();
+    const float beta = bc[1];
     if (beta > 0.f) {
       // p = beta * A_sub v: eight lanes per row, combined by shuffles within each group of eight
       for (int base = 0; base < m; base += nth >> 3) {
@@ -127,23 +227,18 @@ __global__ void __launch_bounds__(512) k_eig_tridiag(const double *__restrict__ 
         if (q == 0 && i < m) pv[i] = beta * s;
       }
       __syncthreads();
-      if (tid < 32) {
-        float s = 0.f;
-        for (int i = tid; i < m; i += 32) s += pv[i] * A[(k + 1 + i) * ld + k];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (tid == 0) bc[3] = 0.5f * beta * s;
-      }
-      __syncthreads();
-      const float kk = bc[3];
-      for (int i = tid; i < m; i += nth) wv[i] = pv[i] - kk * A[(k + 1 + i) * ld + k];
-      __syncthreads();
+      float s = 0.f;
+      for (int i = (tid & 31); i < m; i += 32) s += pv[i] * A[(k + 1 + i) * ld + k];
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      const float kk = 0.5f * beta * s;
       for (int e = tid; e < m * m; e += nth) {
         int i = e / m, j = e - (e / m) * m;
-        float vi = A[(k + 1 + i) * ld + k], vj = A[(k + 1 + j) * ld + k];
-        A[(k + 1 + i) * ld + (k + 1 + j)] -= vi * wv[j] + wv[i] * vj;
+        const float vi = A[(k + 1 + i) * ld + k], vj = A[(k + 1 + j) * ld + k];
+        const float wi = pv[i] - kk * vi, wj = pv[j] - kk * vj;
+        A[(k + 1 + i) * ld + (k + 1 + j)] -= vi * wj + wi * vj;
       }
-      __syncthreads();
     }
+    __syncthreads();  // also when beta = 0: bc[1] is rewritten by the next step
   }
   if (tid == 0) {
     if (n >= 2) {
@@ -154,73 +249,142 @@ __global__ void __launch_bounds__(512) k_eig_tridiag(const double *__restrict__ 
     dg[n - 1] = A[(n - 1) * ld + (n - 1)];
   }
   __syncthreads();
-  // 4. eigenvalues of T by multisection on Sturm counts: warp w finds the j-th smallest eigenvalue
-  //    for j = w, w + 16, ...; its 32 lanes count at 32 shifts, shrinking the bracket 33-fold a step
+  // hand T, the reflectors and C to the eigenvector kernels
+  EigScratch sc(scratch, n, p);
+  for (int e = tid; e < n * n; e += nth) {  // column-major: H[k n + i] = (v_k)_i
+    const int k = e / n, i = e - (e / n) * n;
+    sc.H[e] = (i > k) ? A[i * ld + k] : 0.f;
+  }
+  for (int i = tid; i < n; i += nth) {
+    sc.dg[i] = dg[i];
+    sc.od[i] = od[i];
+    sc.bet[i] = bet[i];
+  }
+  for (int e = tid; e < n * (p + 1); e += nth) sc.C[e] = C[e];
+}
+
+// Gershgorin interval of T, widened by 1e-3 of its span (every lane returns it)
+__device__ void eig_bounds(const float *dg, const float *od, int n, float *lo, float *hi) {
+  const int lane = threadIdx.x & 31;
   float glo = 1e30f, ghi = -1e30f;
-  for (int i = 0; i < n; ++i) {
-    float r = (i > 0 ? fabsf(od[i - 1]) : 0.f) + (i < n - 1 ? fabsf(od[i]) : 0.f);
+  for (int i = lane; i < n; i += 32) {
+    const float r = (i > 0 ? fabsf(od[i - 1]) : 0.f) + (i < n - 1 ? fabsf(od[i]) : 0.f);
     glo = fminf(glo, dg[i] - r);
     ghi = fmaxf(ghi, dg[i] + r);
   }
+  for (int o = 16; o > 0; o >>= 1) {
+    glo = fminf(glo, __shfl_xor_sync(0xffffffffu, glo, o));
+    ghi = fmaxf(ghi, __shfl_xor_sync(0xffffffffu, ghi, o));
+  }
   const float span = fmaxf(ghi - glo, 1e-30f);
-  glo -= 1e-3f * span;
-  ghi += 1e-3f * span;
-  {
-    const int warp = tid >> 5, lane = tid & 31, nwarps = nth >> 5;
-    for (int j = warp; j < n; j += nwarps) {
-      float lo = glo, hi = ghi;
-      for (int step = 0; step < 12; ++step) {
-        if (!(hi - lo > 2e-7f * fmaxf(fabsf(lo), fabsf(hi)))) break;
-        const float w = (hi - lo) / 33.f;
-        const float sig = lo + (lane + 1) * w;
-        int cnt = 0;
-        float q = dg[0] - sig;
-        cnt += (q < 0.f);
-        for (int i = 1; i < n; ++i) {
-          if (fabsf(q) < 1e-30f) q = -1e-30f;
-          q = dg[i] - sig - __fdividef(od[i - 1] * od[i - 1], q);
-          cnt += (q < 0.f);
-        }
-        // first lane whose shift has more than j eigenvalues below it brackets eigenvalue j
-        const unsigned above = __ballot_sync(0xffffffffu, cnt > j);
-        const int l = above ? (__ffs(above) - 1) : 32;
-        const float nlo = (l == 0) ? lo : lo + l * w;
-        const float nhi = (l == 32) ? hi : lo + (l + 1) * w;
-        lo = nlo;
-        hi = nhi;
-      }
-      if (lane == 0) pv[j] = 0.5f * (lo + hi);
-    }
+  *lo = glo - 1e-3f * span;
+  *hi = ghi + 1e-3f * span;
+}
+
+// Eigenvalue j of T (ascending) for warp j: its 32 lanes count at 32 shifts per step (Sturm counts of
+// T - sigma I), shrinking the bracket 33-fold, until it is 2e-7 relative.
+__global__ void __launch_bounds__(128) k_eig_values(float *scratch, int n, int p, double *lam0) {
+  EigScratch sc(scratch, n, p);
+  __shared__ float sd[128], so[128];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    sd[i] = sc.dg[i];
+    so[i] = sc.od[i];
   }
   __syncthreads();
-  // 5. eigenvectors by inverse iteration on T - lam I (LU with partial pivoting, 3 sweeps).
-  //    Eigenvalues closer than 1e-5 * span to their predecessor form a cluster (the boundary outlier
-  //    modes of the B-spline pencils come in nearly degenerate symmetric / antisymmetric pairs); the
-  //    cluster's first thread computes all its vectors in turn and orthogonalizes each sweep against
-  //    the vectors already found, so the cluster's subspace is spanned rather than one vector twice.
+  const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (j >= n) return;
+  float lo, hi;
+  eig_bounds(sd, so, n, &lo, &hi);
+  for (int step = 0; step < 12; ++step) {
+    if (!(hi - lo > 2e-7f * fmaxf(fabsf(lo), fabsf(hi)))) break;
+    const float w = (hi - lo) / 33.f;
+    const float sig = lo + (lane + 1) * w;
+    int cnt = 0;
+    float q = sd[0] - sig;
+    cnt += (q < 0.f);
+    for (int i = 1; i < n; ++i) {
+      if (fabsf(q) < 1e-30f) q = -1e-30f;
+      q = sd[i] - sig - __fdividef(so[i - 1] * so[i - 1], q);
+      cnt += (q < 0.f);
+    }
+    // first lane whose shift has more than j eigenvalues below it brackets eigenvalue j
+    const unsigned above = __ballot_sync(0xffffffffu, cnt > j);
+    const int l = above ? (__ffs(above) - 1) : 32;
+    const float nlo = (l == 0) ? lo : lo + l * w;
+    const float nhi = (l == 32) ? hi : lo + (l + 1) * w;
+    lo = nlo;
+    hi = nhi;
+  }
+  if (lane == 0) {
+    const float v = 0.5f * (lo + hi);
+    sc.pv[j] = v;
+    lam0[j] = (double)v;
+  }
+}
+
+// sum over the warp (every lane returns it)
+__device__ __forceinline__ float warp_sum_f(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Eigenvectors. Eigenvalues closer than 1e-5 * span to their predecessor form a cluster (the boundary
+// outlier modes of the B-spline pencils come in nearly degenerate symmetric / antisymmetric pairs); the
+// warp of the cluster's first eigenvalue computes all its vectors in turn, orthogonalizing each sweep
+// against the ones already found, so the cluster's subspace is spanned rather than one vector twice.
+// Inverse iteration on T - lam I (LU with partial pivoting, 2 sweeps) runs on lane 0 (a serial
+// recurrence); normalization, orthogonalization, the back-transform X <- H_0 ... H_{n-3} X and the
+// final C^{-T} solve use the whole warp or registers. Shared memory: the reflectors (n x n), T and the
+// reciprocal diagonal of C, staged once per CTA, plus 4n floats per warp (the vector and the LU rows).
+__global__ void __launch_bounds__(128) k_eig_vectors(float *scratch, int n, int p, double *U0) {
+  EigScratch sc(scratch, n, p);
+  extern __shared__ __align__(16) float es[];
+  float *H = es;                      // n x n reflectors, column-major (H[k n + i] = (v_k)_i)
+  float *dg = H + n * n, *od = dg + n, *bet = od + n, *pv = bet + n, *rinv = pv + n;
+  float *C = rinv + n;                // n x (p+1)
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float *x = C + n * (p + 1) + warp * 4 * n;  // this warp's vector
+  float *U = x + n;                           // and its LU rows (3 per row)
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) H[e] = sc.H[e];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    dg[i] = sc.dg[i];
+    od[i] = sc.od[i];
+    bet[i] = sc.bet[i];
+    pv[i] = sc.pv[i];
+  }
+  for (int e = threadIdx.x; e < n * (p + 1); e += blockDim.x) C[e] = sc.C[e];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) rinv[i] = 1.f / sc.C[i * (p + 1) + p];
+  __syncthreads();
+  const int j = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (j >= n) return;
+  float glo, ghi;
+  eig_bounds(dg, od, n, &glo, &ghi);
+  const float span = (ghi - glo) / 1.002f;
   const float ctol = 1e-5f * span;
-  for (int j = tid; j < n; j += nth) {
-    lam0[j] = (double)pv[j];
-    if (j > 0 && pv[j] - pv[j - 1] <= ctol) continue;  // not the first of its cluster
-    int e = j + 1;
-    while (e < n && pv[e] - pv[e - 1] <= ctol) ++e;
-    float *Uj = lu + (size_t)j * 3 * n;  // this thread's 3n floats of LU storage
-    for (int a = j; a < e; ++a) {
-      const float lam = pv[a];
-      const float sh = lam + ((a & 1) ? 1e-7f : -1e-7f) * span;
-      for (int i = 0; i < n; ++i) X[i * ld + a] = 1.f + 0.01f * (float)((i * 7 + a * 13) % 17);
-      for (int sweep = 0; sweep < 3; ++sweep) {
-        // factor and forward-solve together; row i of U is (a0, a1, a2) on columns i, i+1, i+2
+  if (j > 0 && pv[j] - pv[j - 1] <= ctol) return;  // not the first of its cluster
+  int e = j + 1;
+  while (e < n && pv[e] - pv[e - 1] <= ctol) ++e;
+  for (int a = j; a < e; ++a) {
+    const float sh = pv[a] + ((a & 1) ? 1e-7f : -1e-7f) * span;
+    for (int i = lane; i < n; i += 32) x[i] = 1.f + 0.01f * (float)((i * 7 + a * 13) % 17);
+    __syncwarp();
+    for (int sweep = 0; sweep < 2; ++sweep) {
+      if (lane == 0) {
+        // factor and forward-solve together; row i of U is (a0, a1, a2) on columns i, i+1, i+2.
+        // The next row's entries are read one iteration ahead (before this row's stores), so the
+        // loads overlap the recurrence.
         float a0 = dg[0] - sh, a1 = (n > 1) ? od[0] : 0.f, a2 = 0.f;
-        float rhs = X[0 * ld + a];
+        float rhs = x[0];
+        float psub = (n > 1) ? od[0] : 0.f, pdia = (n > 1) ? dg[1] - sh : 0.f;
+        float psup = (n > 2) ? od[1] : 0.f, prhs = (n > 1) ? x[1] : 0.f;
         for (int i = 0; i < n; ++i) {
           const bool has_next = (i + 1 < n);
-          float nsub = 0.f, ndia = 0.f, nsup = 0.f, nrhs = 0.f;
-          if (has_next) {
-            nsub = od[i];
-            ndia = dg[i + 1] - sh;
-            nsup = (i + 2 < n) ? od[i + 1] : 0.f;
-            nrhs = X[(i + 1) * ld + a];
+          float nsub = psub, ndia = pdia, nsup = psup, nrhs = prhs;
+          if (i + 2 < n) {
+            psub = od[i + 1];
+            pdia = dg[i + 2] - sh;
+            psup = (i + 3 < n) ? od[i + 2] : 0.f;
+            prhs = x[i + 2];
           }
           if (has_next && fabsf(nsub) > fabsf(a0)) {  // partial pivoting on column i
             float t0 = a0, t1 = a1, t2 = a2, tr = rhs;
@@ -228,82 +392,98 @@ __global__ void __launch_bounds__(512) k_eig_tridiag(const double *__restrict__ 
             nsub = t0; ndia = t1; nsup = t2; nrhs = tr;
           }
           if (fabsf(a0) < 1e-30f) a0 = 1e-30f;
-          Uj[3 * i + 0] = a0;
-          Uj[3 * i + 1] = a1;
-          Uj[3 * i + 2] = a2;
-          X[i * ld + a] = rhs;
+          U[3 * i + 0] = a0;
+          U[3 * i + 1] = a1;
+          U[3 * i + 2] = a2;
+          x[i] = rhs;
           if (has_next) {
-            const float f = nsub / a0;
+            const float f = __fdividef(nsub, a0);
             const float na0 = ndia - f * a1, na1 = nsup - f * a2, nr = nrhs - f * rhs;
             a0 = na0; a1 = na1; a2 = 0.f; rhs = nr;
           }
         }
         float x1 = 0.f, x2 = 0.f;
+        float qx = x[n - 1], q0 = U[3 * (n - 1)], q1 = U[3 * (n - 1) + 1], q2 = U[3 * (n - 1) + 2];
         for (int i = n - 1; i >= 0; --i) {
-          const float u0 = Uj[3 * i], u1 = Uj[3 * i + 1], u2 = Uj[3 * i + 2];
-          const float xi = (X[i * ld + a] - u1 * x1 - u2 * x2) / u0;
-          X[i * ld + a] = xi;
+          const float cx = qx, c0 = q0, c1 = q1, c2 = q2;
+          if (i > 0) {
+            qx = x[i - 1];
+            q0 = U[3 * (i - 1)];
+            q1 = U[3 * (i - 1) + 1];
+            q2 = U[3 * (i - 1) + 2];
+          }
+          const float xi = __fdividef(cx - c1 * x1 - c2 * x2, c0);
+          x[i] = xi;
           x2 = x1;
           x1 = xi;
         }
-        // normalize (2-norm, scaled first against overflow), then orthogonalize against the cluster
-        float mx = 0.f;
-        for (int i = 0; i < n; ++i) mx = fmaxf(mx, fabsf(X[i * ld + a]));
-        const float sc = mx > 0.f ? 1.f / mx : 1.f;
-        for (int i = 0; i < n; ++i) X[i * ld + a] *= sc;
-        for (int b2 = j; b2 < a; ++b2) {
-          float dot = 0.f;
-          for (int i = 0; i < n; ++i) dot += X[i * ld + a] * X[i * ld + b2];
-          for (int i = 0; i < n; ++i) X[i * ld + a] -= dot * X[i * ld + b2];
-        }
-        float nr2 = 0.f;
-        for (int i = 0; i < n; ++i) nr2 += X[i * ld + a] * X[i * ld + a];
-        const float inv = nr2 > 0.f ? rsqrtf(nr2) : 1.f;
-        for (int i = 0; i < n; ++i) X[i * ld + a] *= inv;
+      }
+      __syncwarp();
+      // normalize (max-norm first, against overflow), orthogonalize against the cluster's earlier
+      // vectors (columns j.. a-1 of Xt), normalize in the 2-norm
+      float mx = 0.f;
+      for (int i = lane; i < n; i += 32) mx = fmaxf(mx, fabsf(x[i]));
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      const float scl = mx > 0.f ? 1.f / mx : 1.f;
+      for (int i = lane; i < n; i += 32) x[i] *= scl;
+      __syncwarp();
+      for (int b2 = j; b2 < a; ++b2) {
+        float dot = 0.f;
+        for (int i = lane; i < n; i += 32) dot += x[i] * sc.Xt[(size_t)b2 * n + i];
+        dot = warp_sum_f(dot);
+        for (int i = lane; i < n; i += 32) x[i] -= dot * sc.Xt[(size_t)b2 * n + i];
+        __syncwarp();
+      }
+      float nr2 = 0.f;
+      for (int i = lane; i < n; i += 32) nr2 += x[i] * x[i];
+      nr2 = warp_sum_f(nr2);
+      const float inv = nr2 > 0.f ? rsqrtf(nr2) : 1.f;
+      for (int i = lane; i < n; i += 32) x[i] *= inv;
+      __syncwarp();
+    }
+    for (int i = lane; i < n; i += 32) sc.Xt[(size_t)a * n + i] = x[i];  // for the cluster's later vectors
+    // back-transform: x <- H_0 H_1 ... H_{n-3} x, H_k = I - beta_k v_k v_k^T on rows k+1.., with x in
+    // registers (lane holds rows lane + 32 r) and v_k read as consecutive words
+    float xr[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) xr[r] = (lane + 32 * r < n) ? x[lane + 32 * r] : 0.f;
+    for (int k = n - 3; k >= 0; --k) {
+      const float b = bet[k];
+      if (b == 0.f) continue;
+      const float *vk = H + k * n;
+      float s = 0.f;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int i = lane + 32 * r;
+        if (i > k && i < n) s += vk[i] * xr[r];
+      }
+      s = b * warp_sum_f(s);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int i = lane + 32 * r;
+        if (i > k && i < n) xr[r] -= s * vk[i];
       }
     }
-  }
-  __syncthreads();
-  // 6. back-transform the eigenvectors: X <- H_0 H_1 ... H_{n-3} X, H_k = I - beta_k v_k v_k^T on rows
-  //    k+1..; per reflection, s_j = beta_k v_k^T X[:, j] by eight lanes per column, then the rank-1 update
-  //    over all entries (pv, wv are free once the eigenvalues are in lam0). Measured faster than one warp
-  //    per column (fewer serial steps per warp although it needs two block barriers per reflection).
-  for (int k = n - 3; k >= 0; --k) {
-    const float b = bet[k];
-    if (b == 0.f) continue;  // uniform over the block
-    for (int base = 0; base < n; base += nth >> 3) {
-      const int j = base + (tid >> 3), q = tid & 7;
-      float sj = 0.f;
-      if (j < n)
-        for (int i = k + 1 + q; i < n; i += 8) sj += A[i * ld + k] * X[i * ld + j];
-      sj += __shfl_xor_sync(0xffffffffu, sj, 1);
-      sj += __shfl_xor_sync(0xffffffffu, sj, 2);
-      sj += __shfl_xor_sync(0xffffffffu, sj, 4);
-      if (q == 0 && j < n) wv[j] = b * sj;
+    // normalize (2-norm) and U0 = C^{-T} x by back substitution (lane 0: a serial recurrence)
+    float s2 = 0.f;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) s2 += xr[r] * xr[r];
+    s2 = warp_sum_f(s2);
+    const float inv2 = rsqrtf(fmaxf(s2, 1e-30f));
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      if (lane + 32 * r < n) x[lane + 32 * r] = xr[r] * inv2;
+    __syncwarp();
+    if (lane == 0) {
+      switch (p) {
+#define CASE(PP) case PP: eig_upper_solve<PP>(C, rinv, n, x); break;
+        CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+#undef CASE
+      }
     }
-    __syncthreads();
-    const int rows = n - k - 1;
-    for (int e = tid; e < rows * n; e += nth) {
-      const int i = k + 1 + e / n, j = e - (e / n) * n;
-      X[i * ld + j] -= wv[j] * A[i * ld + k];
-    }
-    __syncthreads();
-  }
-  for (int j = tid; j < n; j += nth) {
-    // normalize (2-norm) and U0 = C^{-T} x : back substitution
-    float s = 0.f;
-    for (int i = 0; i < n; ++i) s += X[i * ld + j] * X[i * ld + j];
-    float inv = rsqrtf(fmaxf(s, 1e-30f));
-    for (int i = n - 1; i >= 0; --i) {
-      float t = X[i * ld + j] * inv;
-      for (int m = i + 1; m <= min(i + p, n - 1); ++m) t -= C[m * (p + 1) + (i - m + p)] * X[m * ld + j];
-      X[i * ld + j] = t / C[i * (p + 1) + p];
-    }
-  }
-  __syncthreads();
-  for (int e = tid; e < n * n; e += nth) {
-    int i = e / n, j = e - (e / n) * n;
-    U0[e] = (double)X[i * ld + j];
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) U0[(size_t)i * n + a] = (double)x[i];
+    __syncwarp();
   }
 }
 
@@ -580,18 +760,21 @@ int fd_setup_launch(stst_problem *h) {
     if (src != l) continue;
     const int n = h->dir[l].n, p = h->dir[l].p;
     const BandMat &M = h->mats[l][0], &L = h->mats[l][1];
-    size_t sm = (2 * (size_t)n * (n + 1) + (size_t)n * (p + 1) + 5 * (size_t)n + 2 * (size_t)n * (2 * p + 1)) *
-                sizeof(float);
-    const size_t sm_lu = sm + 3 * (size_t)n * n * sizeof(float);
-    int dev = 0, optin = 0;
-    STST_CUDA(cudaGetDevice(&dev));
-    STST_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    const int lu_smem = sm_lu <= (size_t)optin ? 1 : 0;
-    if (lu_smem) sm = sm_lu;
+    const size_t sm = (2 * (size_t)n * (n + 1) + (size_t)n * (p + 1) + 5 * (size_t)n + 2 * (size_t)n * (2 * p + 1)) *
+                      sizeof(float);
+    float *scratch = (float *)h->oa_work;  // the refinement's 6 n_max^2 doubles hold EigScratch
+    int nmax = 1;
+    for (int k = 1; k <= d; ++k) nmax = std::max(nmax, h->dir[k].n);
+    if (EigScratch::floats(n, p) > 12 * (size_t)nmax * nmax) return STST_ERR_ARG;
     STST_TRY(ensure_dyn_smem((const void *)k_eig_tridiag, sm));
     { STST_PROF("eig_tridiag_f32", st);
-    k_eig_tridiag<<<1, 512, sm, st>>>(M.d, L.d, n, p, h->U[l], h->lam[l], (float *)h->oa_work, h->flags,
-                                      lu_smem); }
+    k_eig_tridiag<<<1, 512, sm, st>>>(M.d, L.d, n, p, scratch, h->flags); }
+    STST_CUDA(cudaGetLastError());
+    const int eg = (n + 3) / 4;  // four warps (eigenvalues) per CTA
+    { STST_PROF("eig_values_f32", st); k_eig_values<<<eg, 128, 0, st>>>(scratch, n, p, h->lam[l]); }
+    const size_t smv = ((size_t)n * n + 5 * (size_t)n + (size_t)n * (p + 1) + 16 * (size_t)n) * sizeof(float);
+    STST_TRY(ensure_dyn_smem((const void *)k_eig_vectors, smv));
+    { STST_PROF("eig_vectors_f32", st); k_eig_vectors<<<eg, 128, smv, st>>>(scratch, n, p, h->U[l]); }
     STST_CUDA(cudaGetLastError());
     double *X = h->U[l], *PM = h->oa_work, *PL = PM + n * n, *R = PL + n * n, *S = R + n * n, *E = S + n * n,
            *Xn = E + n * n;
