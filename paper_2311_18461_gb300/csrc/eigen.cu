@@ -548,7 +548,7 @@ __global__ void k_oa_E(const double *__restrict__ R, const double *__restrict__ 
 __global__ void k_oa_cluster(const double *__restrict__ Lb, int n, int p, double *X, double *lam, double *Y) {
   __shared__ int cs, ce;
   __shared__ double red[32];
-  __shared__ double rot[2];
+  __shared__ double rot[3];
   const int tid = threadIdx.x, bw = 2 * p + 1;
   int start = 0;
   while (true) {
@@ -577,6 +577,7 @@ __global__ void k_oa_cluster(const double *__restrict__ Lb, int n, int p, double
     }
     __syncthreads();
     for (int sweep = 0; sweep < 8; ++sweep) {
+      if (tid == 0) rot[2] = 0.0;  // set when a rotation of this sweep is not the identity
       for (int a = c0; a < c1; ++a)
         for (int b = a + 1; b < c1; ++b) {
           // block entries S_aa, S_bb, S_ab
@@ -601,7 +602,9 @@ __global__ void k_oa_cluster(const double *__restrict__ Lb, int n, int p, double
               C += red[w + 16];
             }
             double c = 1.0, sn = 0.0;
-            if (C != 0.0) {
+            // converged pairs (off-diagonal at rounding level) keep the identity
+            if (fabs(C) > 1e-15 * sqrt(fabs(A * B)) + 1e-300) {
+              rot[2] = 1.0;
               const double th = (B - A) / (2.0 * C);
               const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
               c = 1.0 / sqrt(t * t + 1.0);
@@ -621,6 +624,8 @@ __global__ void k_oa_cluster(const double *__restrict__ Lb, int n, int p, double
           }
           __syncthreads();
         }
+      if (rot[2] == 0.0) break;  // a sweep without rotations: the block is diagonal (uniform: shared)
+      __syncthreads();           // every thread has read rot[2] before the next sweep resets it
     }
     // eigenvalues of the rotated columns: lam_c = x_c^T L x_c
     for (int c = c0; c < c1; ++c) {
