@@ -272,10 +272,11 @@ int stst_set_autotune(int mode);
  */
 int stst_set_time_solver(int mode);
 /*
- * stst_set_fused_transforms: for d = 2 with the FP32 preconditioner and n_1, n_2 <= 80, Algorithm 1
- * steps 2 and 4 can each run as one kernel (S CTAs per time index take its n_1 x n_2 slab through
- * both mode products in shared memory; the forward transform is split by rows, the backward one by
- * columns) instead of two mode-product kernels. Mode 0 (default) chooses per shape when the
+ * stst_set_fused_transforms: for d = 2 or 3 with the FP32 preconditioner and n_1, n_2 <= 80, the mode
+ * products of directions 1 and 2 in Algorithm 1 steps 2 and 4 can run as one kernel (S CTAs per slab
+ * (t, i_3) take its n_1 x n_2 slab through both products in shared memory; the forward transform is
+ * split by rows, the backward one by columns) instead of two mode-product kernels; direction 3 stays
+ * a mode-product kernel. Mode 0 (default) chooses per shape when the
  * preconditioner is built (separate kernels or a split S = 1..4, timed under autotune mode 1; else
  * fused with the smallest S that gives two CTAs per SM); 1 = separate kernels; 2 = fused with that
  * default split; 11..14 = fused with S = mode - 10 (the default split where S would leave a part

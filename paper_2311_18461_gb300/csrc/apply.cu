@@ -250,27 +250,28 @@ __global__ void __launch_bounds__(256) k_modeprod(const TI *__restrict__ X, TO *
                                                   const TO *__restrict__ dotvec, double *dot_partials,
                                                   const int *done) {
   using T = typename C2<R>::T;
-  constexpr int CW = 8 * CPT, RB = 32 * RPT;
+  constexpr int CW = 8 * CPT, RB = 32 * RPT, RBP = RB + 1;  // U rows padded: the transposed staging
+                                                            // (backward) writes stride RBP, no bank conflicts
   if (done && *done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R *sU = (R *)smem_raw;                                             // n x RB
-  T *sX = (T *)(smem_raw + ((n * RB * sizeof(R) + 15) / 16) * 16);  // n x CW
+  R *sU = (R *)smem_raw;                                              // n x RBP
+  T *sX = (T *)(smem_raw + ((n * RBP * sizeof(R) + 15) / 16) * 16);  // n x CW
   __shared__ double sh[32];
   const long long col0 = (long long)blockIdx.x * CW;
   const int j0 = blockIdx.y * RB;
-  // U slice: sU[i*RB + jj] = coefficient of x_i in y_{j0+jj}; source reads are coalesced either way
+  // U slice: sU[i*RBP + jj] = coefficient of x_i in y_{j0+jj}; source reads are coalesced either way
   if (!backward) {
     for (int e = threadIdx.x; e < n * RB; e += 256) {  // (i, jj), jj fastest: source U[i][j0 + jj]
       const int i = e / RB, jj = e - i * RB;
-      if (j0 + jj < n) cp_async<sizeof(R)>(&sU[e], &U[(long long)i * n + j0 + jj]);
-      else sU[e] = (R)0;
+      if (j0 + jj < n) cp_async<sizeof(R)>(&sU[i * RBP + jj], &U[(long long)i * n + j0 + jj]);
+      else sU[i * RBP + jj] = (R)0;
     }
   } else {
     int e = threadIdx.x, jj = e / n, i = e - (e / n) * n;  // (jj, i), i fastest: source U[j0 + jj][i]
     const int dj = 256 / n, di = 256 - (256 / n) * n;
     for (; e < n * RB; e += 256) {
-      if (j0 + jj < n) cp_async<sizeof(R)>(&sU[i * RB + jj], &U[(long long)(j0 + jj) * n + i]);
-      else sU[i * RB + jj] = (R)0;
+      if (j0 + jj < n) cp_async<sizeof(R)>(&sU[i * RBP + jj], &U[(long long)(j0 + jj) * n + i]);
+      else sU[i * RBP + jj] = (R)0;
       i += di;
       jj += dj;
       if (i >= n) { i -= n; ++jj; }
@@ -336,7 +337,7 @@ __global__ void __launch_bounds__(256) k_modeprod(const TI *__restrict__ X, TO *
     }
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
-      const R u = sU[i * RB + rg + 32 * r];
+      const R u = sU[i * RBP + rg + 32 * r];
 #pragma unroll
       for (int c = 0; c < CPT; ++c) {
         ax[r][c] += u * xv[c].x;
@@ -373,7 +374,7 @@ __global__ void __launch_bounds__(256) k_modeprod(const TI *__restrict__ X, TO *
 }
 
 static size_t modeprod_smem(int n, MpCfg c, size_t rsize) {
-  return ((n * 32 * c.rpt * rsize + 15) / 16) * 16 + (size_t)n * 8 * c.cpt * 2 * rsize;
+  return ((n * (32 * c.rpt + 1) * rsize + 15) / 16) * 16 + (size_t)n * 8 * c.cpt * 2 * rsize;
 }
 
 static dim3 modeprod_grid(int n, long long ncols, MpCfg c) {
@@ -1021,7 +1022,9 @@ __global__ void __launch_bounds__(512) k_fd2d(const TI *__restrict__ X, TO *__re
   if (done && *done) return;
   extern __shared__ __align__(16) unsigned char fd_smem[];
   __shared__ double sh[32];
-  const int t = blockIdx.x, S = gridDim.y, part = blockIdx.y;
+  // slab (t, i3): X_t[i1][i2] at base + nt (i1 + n1 i2), base = t + nt n1 n2 i3 (i3 = 0 for d = 2)
+  const int t = blockIdx.x % nt, S = gridDim.y, part = blockIdx.y;
+  const long long base = t + (long long)nt * n1 * n2 * (blockIdx.x / nt);
   const int tid = threadIdx.x, nth = blockDim.x;
   const int nsplit = backward ? n2 : n1, nother = backward ? n1 : n2;
   const int mfull = (nsplit + S - 1) / S, p0 = part * mfull, m = min(mfull, nsplit - p0);
@@ -1049,7 +1052,7 @@ __global__ void __launch_bounds__(512) k_fd2d(const TI *__restrict__ X, TO *__re
     }
   }
   if constexpr (sizeof(TI) == sizeof(float2)) {
-    for (int e = tid; e < n1 * n2; e += nth) cp_async<8>(&sX[e], &X[t + (long long)nt * e]);
+    for (int e = tid; e < n1 * n2; e += nth) cp_async<8>(&sX[e], &X[base + (long long)nt * e]);
   } else {
     constexpr int BATCH = 8;  // independent loads in flight per thread
     const int nn = n1 * n2;
@@ -1058,7 +1061,7 @@ __global__ void __launch_bounds__(512) k_fd2d(const TI *__restrict__ X, TO *__re
 #pragma unroll
       for (int u = 0; u < BATCH; ++u) {
         const int e = e0 + u * nth;
-        if (e < nn) v[u] = X[t + (long long)nt * e];
+        if (e < nn) v[u] = X[base + (long long)nt * e];
       }
 #pragma unroll
       for (int u = 0; u < BATCH; ++u) {
@@ -1102,7 +1105,7 @@ __global__ void __launch_bounds__(512) k_fd2d(const TI *__restrict__ X, TO *__re
         const int a = a0 + Ra2 * k, b = NC * g + q;
         if (a < nother && b < m) {
           const int i1 = backward ? a : p0 + b, i2 = backward ? p0 + b : a;
-          const long long idx = t + (long long)nt * (i1 + (long long)n1 * i2);
+          const long long idx = base + (long long)nt * (i1 + (long long)n1 * i2);
           TO res;
           res.x = ax[k][q];
           res.y = ay[k][q];
@@ -1116,7 +1119,7 @@ __global__ void __launch_bounds__(512) k_fd2d(const TI *__restrict__ X, TO *__re
   }
   if (dot_partials) {
     const double s2 = block_sum(dacc, sh);
-    if (tid == 0) dot_partials[t * S + part] = s2;
+    if (tid == 0) dot_partials[(long long)blockIdx.x * S + part] = s2;
   }
 }
 
@@ -1139,9 +1142,12 @@ static bool fd2d_split_ok(int n1, int n2, int S) {
   return (S - 1) * ((n1 + S - 1) / S) < n1 && (S - 1) * ((n2 + S - 1) / S) < n2;
 }
 
+// number of slabs (t, i3) the fused kernel runs over: n_t for d = 2, n_t n_3 for d = 3
+static long long fd2d_slabs(const stst_problem *h) { return (long long)h->n_t() * (h->d == 3 ? h->dir[3].n : 1); }
+
 bool fd2d_fits(const stst_problem *h) {
-  if (h->d != 2 || h->dir[1].n > FD2D_MAXN || h->dir[2].n > FD2D_MAXN) return false;
-  if ((long long)h->n_t() * FD2D_MAXS > STST_MAXPART) return false;
+  if ((h->d != 2 && h->d != 3) || h->dir[1].n > FD2D_MAXN || h->dir[2].n > FD2D_MAXN) return false;
+  if (fd2d_slabs(h) * FD2D_MAXS > STST_MAXPART || fd2d_slabs(h) > 0x7fffffffLL) return false;
   int dev = 0, optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -1158,8 +1164,8 @@ static int launch_fd2d(const TI *X, TO *Y, const stst_problem *h, int backward, 
   const size_t sm = fd2d_smem(n1, n2, S);
   STST_PROF("modeprod2d_f32", s);
   STST_TRY(ensure_dyn_smem((const void *)k_fd2d<TI, TO>, sm));
-  k_fd2d<TI, TO><<<dim3(nt, S), nth, sm, s>>>(X, Y, h->U32[1], h->U32[2], n1, n2, nt, backward, dotvec, partials,
-                                              done);
+  k_fd2d<TI, TO><<<dim3((unsigned)fd2d_slabs(h), S), nth, sm, s>>>(X, Y, h->U32[1], h->U32[2], n1, n2, nt, backward,
+                                                                   dotvec, partials, done);
   STST_CUDA(cudaGetLastError());
   return STST_OK;
 }
@@ -1263,12 +1269,21 @@ int fd_apply(stst_problem *h, const double *r, double *s, int precision, const v
     return STST_OK;
   }
   // FP32
-  if (h->fd2d) {  // both spatial mode products of each transform in one kernel (d = 2)
+  if (h->fd2d) {  // modes 1 and 2 of each transform in one kernel per (t, i3) slab; mode 3 (d = 3) separate
     float2 *y32 = (float2 *)bufA;
     const int S = h->fd2d;
     if (in32) STST_TRY((launch_fd2d<float2, float2>((const float2 *)in32, y32, h, 0, nullptr, nullptr, done, st, S)));
     else STST_TRY((launch_fd2d<double2, float2>((const double2 *)r, y32, h, 0, nullptr, nullptr, done, st, S)));
-    STST_TRY(time_solve<float>(h, (void *)y32, done, st));
+    if (d == 3) {
+      float2 *z32 = (float2 *)bufB;
+      STST_TRY((launch_modeprod<float, float2, float2>(y32, z32, h->U32[3], h->dir[3].n, inner[3], outer[3], 0,
+                                                       nullptr, nullptr, done, st, h->mp_cfg[3])));
+      STST_TRY(time_solve<float>(h, (void *)z32, done, st));
+      STST_TRY((launch_modeprod<float, float2, float2>(z32, y32, h->U32[3], h->dir[3].n, inner[3], outer[3], 1,
+                                                       nullptr, nullptr, done, st, h->mp_cfg[3])));
+    } else {
+      STST_TRY(time_solve<float>(h, (void *)y32, done, st));
+    }
     if (out32)
       return launch_fd2d<float2, float2>(y32, (float2 *)out32, h, 1, (const float2 *)dotvec, dot_partials, done, st,
                                          S);
@@ -1321,7 +1336,7 @@ int fd_apply(stst_problem *h, const double *r, double *s, int precision, const v
 int fd_partials_count(stst_problem *h) {
   long long ncols = h->N_dof / h->dir[1].n;
   if (h->prec_mode == STST_PREC_BF16) return tc_partials_count(ncols);
-  if (h->fd2d && h->prec_mode == STST_PREC_FP32) return h->n_t() * h->fd2d;
+  if (h->fd2d && h->prec_mode == STST_PREC_FP32) return (int)(fd2d_slabs(h) * h->fd2d);
   const dim3 g = modeprod_grid(h->dir[1].n, ncols, h->mp_cfg[1]);
   return (int)(g.x * g.y);
 }
@@ -1400,7 +1415,7 @@ static std::map<std::tuple<int, int, int>, int> g_fd2d_cache;
 
 static int fd2d_default_split(const stst_problem *h) {
   int S = 1;
-  while (S < FD2D_MAXS && (long long)h->n_t() * S < 2 * 152 && fd2d_split_ok(h->dir[1].n, h->dir[2].n, S + 1)) ++S;
+  while (S < FD2D_MAXS && fd2d_slabs(h) * S < 2 * 152 && fd2d_split_ok(h->dir[1].n, h->dir[2].n, S + 1)) ++S;
   return S;
 }
 

@@ -310,16 +310,18 @@ def test_mode_product_tiles_agree_bitwise(prec):
     assert outs[12][1][0][:2] == (16, 32) and outs[44][1][1][:2] == (32, 128)
 
 
-@pytest.mark.parametrize("n_el,p", [([5, 40, 70], 3), ([9, 16, 78], [2, 3, 3]), ([3, 1, 5], 2), ([70, 30, 31], 2)])
+@pytest.mark.parametrize("n_el,p", [([5, 40, 70], 3), ([9, 16, 78], [2, 3, 3]), ([3, 1, 5], 2), ([70, 30, 31], 2),
+                                    ([5, 12, 9, 7], [2, 3, 2, 2]), ([4, 30, 6, 40], [3, 2, 3, 2])])
 def test_fused_2d_transforms_bitwise(n_el, p):
-    """The fused 2D transform kernel (both spatial mode products of Algorithm 1 steps 2 and 4 in one
-    kernel) gives bitwise the same preconditioner output as the two separate mode-product kernels; PCG
-    with either takes the same iterations (only the order of the dot-product partial sums differs)."""
+    """The fused transform kernel (the mode products of directions 1 and 2 of Algorithm 1 steps 2 and 4
+    in one kernel per (t, x_3) slab; direction 3 separate when d = 3) gives bitwise the same
+    preconditioner output as the separate mode-product kernels; PCG with either takes the same
+    iterations (only the order of the dot-product partial sums differs)."""
     out = {}
     try:
         for mode in (1, 2, 11, 12, 13, 14):
             S.stst_set_fused_transforms(mode)
-            prob = S.Problem(2, n_el, p, prec_mode=S.STST_PREC_FP32)
+            prob = S.Problem(len(n_el) - 1, n_el, p, prec_mode=S.STST_PREC_FP32)
             prob.build_fd()
             fused = S.stst_fused_transforms_info(prob.h)
             z = to_np(prob.apply_prec(to_dev(random_complex(prob.n_dof, 31))))
@@ -337,11 +339,11 @@ def test_fused_2d_transforms_bitwise(n_el, p):
 
 
 def test_fused_2d_transforms_only_where_they_apply():
-    """Not used with the FP64 or BF16 preconditioners, for d != 2, or when a spatial size exceeds 80."""
+    """Not used with the FP64 or BF16 preconditioners, for d = 1, or when n_1 or n_2 exceeds 80."""
     try:
         S.stst_set_fused_transforms(2)
         for n_el, p, prec in [([4, 6, 7], 2, S.STST_PREC_FP64), ([4, 6, 7], 2, S.STST_PREC_BF16),
-                              ([4, 6], 2, S.STST_PREC_FP32), ([3, 4, 5, 6], 2, S.STST_PREC_FP32),
+                              ([4, 6], 2, S.STST_PREC_FP32), ([3, 4, 90, 6], 2, S.STST_PREC_FP32),
                               ([4, 90, 6], 2, S.STST_PREC_FP32)]:
             prob = S.Problem(len(n_el) - 1, n_el, p, prec_mode=prec)
             prob.build_fd()
