@@ -250,9 +250,10 @@ int stst_batch_destroy(stst_batch b);
 /*
  * stst_set_autotune: mode 1 (the default) makes stst_build_fd and stst_batch_create time the candidate
  * tiles of the SIMT mode products (8 cpt columns with cpt in {2, 4}, 32 rpt output rows with rpt in 1..4,
- * per CTA) once per problem shape and precision, keeping the fastest (cached for the process); mode 0 uses
- * the fixed default (32 columns, all rows of the mode up to 128 per CTA); mode 10 rpt + cpt forces that
- * tile where it fits in shared memory. Results do not depend on the tile (each output is summed in the
+ * per CTA; with the FP32 preconditioner also a wide tile of 256 columns x 32 rows, 8 rows x 4 columns
+ * per thread) once per problem shape and precision, keeping the fastest (cached for the process); mode 0
+ * uses the fixed default (32 columns, all rows of the mode up to 128 per CTA); mode 10 rpt + cpt forces
+ * that tile, mode 132 the wide one (FP32 preconditioner), where it fits in shared memory. Results do not depend on the tile (each output is summed in the
  * same order); the grouping of the PCG dot-product partials does. Process-wide, for handles whose
  * preconditioner is built afterwards. STST_ERR_ARG for other modes.
  * stst_tile_info: the tile of direction dir (1..d) of the handle: columns and output rows per CTA

@@ -316,53 +316,103 @@ __global__ void __launch_bounds__(256) k_modeprod(const TI *__restrict__ X, TO *
     cp_async_wait_all();
   }
   __syncthreads();
-  const int cg = threadIdx.x & 7, rg = threadIdx.x >> 3;
-  R ax[RPT][CPT], ay[RPT][CPT];
-#pragma unroll
-  for (int r = 0; r < RPT; ++r)
-#pragma unroll
-    for (int c = 0; c < CPT; ++c) { ax[r][c] = 0; ay[r][c] = 0; }
-  for (int i = 0; i < n; ++i) {
-    T xv[CPT];
-    if constexpr (sizeof(T) == 8) {  // float2 columns: 16-byte reads
-      const float4 *q = reinterpret_cast<const float4 *>(&sX[i * CW + cg * CPT]);
-#pragma unroll
-      for (int h2 = 0; h2 < CPT / 2; ++h2) {
-        const float4 a = q[h2];
-        xv[2 * h2].x = a.x; xv[2 * h2].y = a.y; xv[2 * h2 + 1].x = a.z; xv[2 * h2 + 1].y = a.w;
-      }
-    } else {
-#pragma unroll
-      for (int c = 0; c < CPT; ++c) xv[c] = sX[i * CW + cg * CPT + c];
-    }
-#pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-      const R u = sU[i * RBP + rg + 32 * r];
-#pragma unroll
-      for (int c = 0; c < CPT; ++c) {
-        ax[r][c] += u * xv[c].x;
-        ay[r][c] += u * xv[c].y;
-      }
-    }
-  }
   double dacc = 0.0;
+  if constexpr (CPT == 32) {
+    // wide tile (n <= ~100, FP32): 32 rows x 256 columns per CTA. Warp w owns rows 8 rg .. 8 rg + 7
+    // (rg = w / 2) and column group cgp = 32 (w % 2) + lane; a thread accumulates those 8 rows x the
+    // columns cgp + 64 q (q < 4). A step reads 8 U values as warp broadcasts and 4 x values of
+    // consecutive columns for 64 FMAs per thread (the one-row tiles read about one wavefront per FMA).
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rgw = warp >> 1, cgp = ((warp & 1) << 5) + lane;
+    R ax[8][4], ay[8][4];
 #pragma unroll
-  for (int c = 0; c < CPT; ++c) {
-    const long long col = col0 + cg * CPT + c;
-    if (col >= ncols) continue;
-    const long long o = col / inner, cin = col % inner;
+    for (int r = 0; r < 8; ++r)
 #pragma unroll
-    for (int r = 0; r < RPT; ++r) {
-      const int j = j0 + rg + 32 * r;
-      if (j < n) {
-        const long long idx = (o * n + j) * inner + cin;
-        TO res;
-        res.x = ax[r][c];
-        res.y = ay[r][c];
-        Y[idx] = res;
-        if (dotvec) {
-          TO dv = dotvec[idx];
-          dacc += (double)dv.x * (double)res.x + (double)dv.y * (double)res.y;
+      for (int q = 0; q < 4; ++q) { ax[r][q] = 0; ay[r][q] = 0; }
+    for (int i = 0; i < n; ++i) {
+      R u[8];
+      T xv[4];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) u[r] = sU[i * RBP + 8 * rgw + r];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) xv[q] = sX[i * CW + cgp + 64 * q];
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          ax[r][q] += u[r] * xv[q].x;
+          ay[r][q] += u[r] * xv[q].y;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const long long col = col0 + cgp + 64 * q;
+      if (col >= ncols) continue;
+      const long long o = col / inner, cin = col % inner;
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int j = j0 + 8 * rgw + r;
+        if (j < n) {
+          const long long idx = (o * n + j) * inner + cin;
+          TO res;
+          res.x = ax[r][q];
+          res.y = ay[r][q];
+          Y[idx] = res;
+          if (dotvec) {
+            TO dv = dotvec[idx];
+            dacc += (double)dv.x * (double)res.x + (double)dv.y * (double)res.y;
+          }
+        }
+      }
+    }
+  } else {
+    const int cg = threadIdx.x & 7, rg = threadIdx.x >> 3;
+    R ax[RPT][CPT], ay[RPT][CPT];
+  #pragma unroll
+    for (int r = 0; r < RPT; ++r)
+  #pragma unroll
+      for (int c = 0; c < CPT; ++c) { ax[r][c] = 0; ay[r][c] = 0; }
+    for (int i = 0; i < n; ++i) {
+      T xv[CPT];
+      if constexpr (sizeof(T) == 8) {  // float2 columns: 16-byte reads
+        const float4 *q = reinterpret_cast<const float4 *>(&sX[i * CW + cg * CPT]);
+  #pragma unroll
+        for (int h2 = 0; h2 < CPT / 2; ++h2) {
+          const float4 a = q[h2];
+          xv[2 * h2].x = a.x; xv[2 * h2].y = a.y; xv[2 * h2 + 1].x = a.z; xv[2 * h2 + 1].y = a.w;
+        }
+      } else {
+  #pragma unroll
+        for (int c = 0; c < CPT; ++c) xv[c] = sX[i * CW + cg * CPT + c];
+      }
+  #pragma unroll
+      for (int r = 0; r < RPT; ++r) {
+        const R u = sU[i * RBP + rg + 32 * r];
+  #pragma unroll
+        for (int c = 0; c < CPT; ++c) {
+          ax[r][c] += u * xv[c].x;
+          ay[r][c] += u * xv[c].y;
+        }
+      }
+    }
+  #pragma unroll
+    for (int c = 0; c < CPT; ++c) {
+      const long long col = col0 + cg * CPT + c;
+      if (col >= ncols) continue;
+      const long long o = col / inner, cin = col % inner;
+  #pragma unroll
+      for (int r = 0; r < RPT; ++r) {
+        const int j = j0 + rg + 32 * r;
+        if (j < n) {
+          const long long idx = (o * n + j) * inner + cin;
+          TO res;
+          res.x = ax[r][c];
+          res.y = ay[r][c];
+          Y[idx] = res;
+          if (dotvec) {
+            TO dv = dotvec[idx];
+            dacc += (double)dv.x * (double)res.x + (double)dv.y * (double)res.y;
+          }
         }
       }
     }
@@ -396,11 +446,14 @@ static int launch_modeprod(const TI *X, TO *Y, const R *U, int n, long long inne
     return STST_OK;
   };
   int st = STST_ERR_ARG;
-  const int key = cfg.rpt * 10 + cfg.cpt;
+  const int key = cfg.rpt * 100 + cfg.cpt;
   switch (key) {
-#define CASE(RR, CC) case RR * 10 + CC: st = go(k_modeprod<R, TI, TO, RR, CC>); break;
+#define CASE(RR, CC) case RR * 100 + CC: st = go(k_modeprod<R, TI, TO, RR, CC>); break;
     CASE(1, 2) CASE(1, 4) CASE(2, 2) CASE(2, 4) CASE(3, 2) CASE(3, 4) CASE(4, 2) CASE(4, 4)
 #undef CASE
+    case 132:  // the wide tile, FP32 only
+      if constexpr (sizeof(R) == 4) st = go(k_modeprod<R, TI, TO, 1, 32>);
+      break;
     default: break;
   }
   STST_TRY(st);
@@ -453,11 +506,14 @@ static int tune_one(stst_problem *h, int l, long long inner, long long outer, Mp
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   int status = STST_OK;
   const int maxr = (n + 31) / 32;
-  for (int rpt = 1; rpt <= 4 && rpt <= maxr && status == STST_OK; ++rpt)
-    for (int cpt = 2; cpt <= 4 && status == STST_OK; cpt += 2) {
-      MpCfg c;
-      c.cpt = cpt;
-      c.rpt = rpt;
+  // candidates: one- to four-row tiles of 16 or 32 columns, and (FP32) the wide 32 x 256 tile
+  std::vector<MpCfg> cands;
+  for (int rpt = 1; rpt <= 4 && rpt <= maxr; ++rpt)
+    for (int cpt = 2; cpt <= 4; cpt += 2) cands.push_back(MpCfg{cpt, rpt});
+  if (sizeof(R) == 4) cands.push_back(MpCfg{32, 1});
+  for (const MpCfg &c : cands) {
+    if (status != STST_OK) break;
+    {
       if (modeprod_smem(n, c, sizeof(R)) > (size_t)optin) continue;
       for (int w = 0; w < 2 && status == STST_OK; ++w)
         status = launch_modeprod<R, T, T>(X, Y, U, n, inner, outer, 0, nullptr, nullptr, nullptr, st, c);
@@ -479,6 +535,7 @@ static int tune_one(stst_problem *h, int l, long long inner, long long outer, Mp
         cand = c;
       }
     }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   STST_TRY(status);
@@ -495,8 +552,13 @@ static int tune_mp_tiles(stst_problem *h) {
   if (h->prec_mode == STST_PREC_BF16 || g_tune_enabled != 1) {
     for (int l = 1; l <= h->d; ++l) {
       h->mp_cfg[l] = modeprod_default(h->dir[l].n);
-      const int rpt = g_tune_enabled / 10, cpt = g_tune_enabled % 10;  // a forced tile (10 rpt + cpt)
-      if (rpt >= 1 && rpt <= 4 && (cpt == 2 || cpt == 4)) {
+      // a forced tile: 10 rpt + cpt, or 132 for the wide tile (FP32 preconditioner only)
+      int rpt = g_tune_enabled / 10, cpt = g_tune_enabled % 10;
+      if (g_tune_enabled == 132 && h->prec_mode == STST_PREC_FP32) {
+        rpt = 1;
+        cpt = 32;
+      }
+      if (rpt >= 1 && rpt <= 4 && (cpt == 2 || cpt == 4 || cpt == 32)) {
         MpCfg c;
         c.cpt = cpt;
         c.rpt = rpt;

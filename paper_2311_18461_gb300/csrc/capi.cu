@@ -777,7 +777,7 @@ const char *stst_last_cuda_error(void) {
 
 int stst_set_autotune(int mode) {
   const int rpt = mode / 10, cpt = mode % 10;
-  if (mode != 0 && mode != 1 && !(rpt >= 1 && rpt <= 4 && (cpt == 2 || cpt == 4))) return STST_ERR_ARG;
+  if (mode != 0 && mode != 1 && mode != 132 && !(rpt >= 1 && rpt <= 4 && (cpt == 2 || cpt == 4))) return STST_ERR_ARG;
   g_tune_enabled = mode;
   return STST_OK;
 }

@@ -292,7 +292,7 @@ def test_mode_product_tiles_agree_bitwise(prec):
     P.stst_set_time_solver(1)  # the same time solve for every tile
     P.stst_set_fused_transforms(1)  # separate mode products, so that every tile runs
     try:
-        for mode in (0, 12, 14, 22, 24, 32, 34, 42, 44, 1):
+        for mode in (0, 12, 14, 22, 24, 32, 34, 42, 44, 132, 1):
             P.stst_set_autotune(mode)
             prob = P.Problem(2, [5, 40, 70], 3, prec_mode=prec)  # n_l = 41 and 71
             prob.build_fd()
@@ -308,6 +308,8 @@ def test_mode_product_tiles_agree_bitwise(prec):
     for mode, (o, tiles) in outs.items():
         assert np.array_equal(o, ref), (mode, tiles)
     assert outs[12][1][0][:2] == (16, 32) and outs[44][1][1][:2] == (32, 128)
+    if prec == S.STST_PREC_FP32:  # the wide 32-row x 256-column tile (FP32 only)
+        assert outs[132][1][0][:2] == (256, 32) and outs[132][1][1][:2] == (256, 32)
 
 
 @pytest.mark.parametrize("n_el,p", [([5, 40, 70], 3), ([9, 16, 78], [2, 3, 3]), ([3, 1, 5], 2), ([70, 30, 31], 2),
