@@ -60,7 +60,7 @@ struct PassK {
 };
 
 template <typename R, int P>
-__global__ void __launch_bounds__(256) k_pass(const __grid_constant__ PassK k) {
+__global__ void __launch_bounds__(512) k_pass(const __grid_constant__ PassK k) {
   using T = typename C2<R>::T;
   if (k.done && *k.done) return;
   __shared__ double sh[32];
@@ -131,10 +131,10 @@ __global__ void __launch_bounds__(256) k_pass(const __grid_constant__ PassK k) {
 }
 
 template <typename R>
-static int launch_pass_t(const PassK &k, int p, int grid, cudaStream_t s) {
+static int launch_pass_t(const PassK &k, int p, int grid, cudaStream_t s, int threads = 256) {
   STST_PROF(sizeof(R) == 8 ? "pass_f64" : "pass_f32", s);
   switch (p) {
-#define CASE(PP) case PP: k_pass<R, PP><<<grid, 256, 0, s>>>(k); break;
+#define CASE(PP) case PP: k_pass<R, PP><<<grid, threads, 0, s>>>(k); break;
     CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
 #undef CASE
     default: return STST_ERR_ARG;
@@ -225,7 +225,11 @@ int run_plan(const Plan &plan, const void *x, void *y, int precision, int epi, c
       grid = grid_for(total, 256);
       if (grid > 152 * 16) grid = 152 * 16;
     }
-    int st = precision == 1 ? launch_pass_t<float>(k, pp.p, grid, s) : launch_pass_t<double>(k, pp.p, grid, s);
+    // the final level's grid is capped (its per-CTA partials are reduced by every consumer CTA): it runs
+    // 512-thread CTAs, twice the warps per SM for the same number of partials
+    const int threads = (ip == np - 1) ? 512 : 256;
+    int st = precision == 1 ? launch_pass_t<float>(k, pp.p, grid, s, threads)
+                            : launch_pass_t<double>(k, pp.p, grid, s, threads);
     if (st != STST_OK) return st;
   }
   return STST_OK;
