@@ -212,8 +212,11 @@ int stst_rhs_noalloc(stst_handle h, const double *f_qp, const double *u0_qp, dou
  * ||rhs - A x_k||_2 <= tol ||rhs||_2 (recursive residual) or after maxit
  * iterations. With a low-precision preconditioner the Polak-Ribiere
  * (flexible) beta is used. iters, relres: host outputs (may be NULL).
- * Needs build_fd. Returns OK, NOT_CONVERGED or BREAKDOWN. The loop runs as
- * one CUDA graph with a device-side while condition: the host waits once.
+ * Needs build_fd. Returns OK, NOT_CONVERGED or BREAKDOWN, or TIMEOUT when a
+ * bounded device-side wait expired since the last solve (the BF16 tensor-core
+ * mode products wait on their MMAs' completion barrier; the flag is then
+ * cleared). The loop runs as one CUDA graph with a device-side while
+ * condition: the host waits once.
  */
 int stst_pcg_solve(stst_handle h, const double *rhs, double *x, double tol, int maxit, int *iters, double *relres);
 
@@ -222,7 +225,8 @@ int stst_pcg_solve(stst_handle h, const double *rhs, double *x, double tol, int 
  * residual rhs - A x and FP64 update x += d around an inner FP32 PCG on
  * A d = r (FP32 mat-vec, FP32/BF16 preconditioner, inner tolerance inner_tol).
  * Stops when the FP64 relative residual <= tol or after maxit outer steps.
- * iters receives the total inner iterations, outer the outer steps.
+ * iters receives the total inner iterations, outer the outer steps. Returns
+ * as stst_pcg_solve (TIMEOUT included).
  */
 int stst_ir_solve(stst_handle h, const double *rhs, double *x, double tol, int maxit, double inner_tol,
                   int inner_maxit, int *iters, int *outer, double *relres);

@@ -320,6 +320,16 @@ static int build_pcg_graph(stst_problem *h) {
   return STST_OK;
 }
 
+// Waits for the stream and reads the handle's bounded-wait flag (flags[1], bit 2: the tensor-core mode
+// product gave up waiting for its MMAs) into flags_host[1], clearing it on the device for the next call.
+static int take_timeout_flag(stst_problem *h) {
+  cudaStream_t st = h->stream;
+  STST_CUDA(cudaMemcpyAsync(h->flags_host + 1, h->flags + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+  STST_CUDA(cudaMemsetAsync(h->flags + 1, 0, sizeof(int), st));
+  STST_CUDA(cudaStreamSynchronize(st));
+  return STST_OK;
+}
+
 int pcg_run(stst_problem *h, const double *rhs, double *x, double tol, int maxit, int *iters, double *relres) {
   cudaStream_t st = h->stream;
   const size_t bytes = sizeof(double) * 2 * (size_t)h->N_dof;
@@ -348,10 +358,11 @@ int pcg_run(stst_problem *h, const double *rhs, double *x, double tol, int maxit
   }
   STST_CUDA(cudaMemcpyAsync(x, h->w_x, bytes, cudaMemcpyDeviceToDevice, st));
   STST_CUDA(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(PcgCtl), cudaMemcpyDeviceToHost, st));
-  STST_CUDA(cudaStreamSynchronize(st));
+  STST_TRY(take_timeout_flag(h));
   const PcgCtl &c = *h->ctl_host;
   if (iters) *iters = c.it;
   if (relres) *relres = c.ff > 0 ? sqrt(c.rr / c.ff) : 0.0;
+  if (h->flags_host[1] & 4) return STST_TIMEOUT;
   if (c.status != STST_OK) return c.status;
   if (!c.done) return STST_NOT_CONVERGED;
   return STST_OK;
@@ -517,10 +528,11 @@ int ir_run(stst_problem *h, const double *rhs, double *x, double tol, int maxit,
     { STST_PROF("ir_update", st); k_x_from_f32<<<g, 256, 0, st>>>((double2 *)h->w_x, (const float2 *)h->v_d, h->ctl, N); }
   }
   STST_CUDA(cudaMemcpyAsync(x, h->w_x, bytes, cudaMemcpyDeviceToDevice, st));
-  STST_CUDA(cudaStreamSynchronize(st));
+  STST_TRY(take_timeout_flag(h));
   const PcgCtl &c = h->ctl_host[0];
   if (iters) *iters = total_inner;
   if (outer) *outer = k;
   if (relres) *relres = c.ff > 0 ? sqrt(c.rr / c.ff) : 0.0;
+  if (h->flags_host[1] & 4) return STST_TIMEOUT;
   return status;
 }
