@@ -41,6 +41,7 @@ __global__ void k_batch_ctl(PcgCtl *ctl, const BatchParams *bp, int flexible) {
     ctl->it = 0;
     ctl->done = 0;
     ctl->status = STST_OK;
+    ctl->x0_zero = 1;  // cleared by pcg_init if the initial guess has a nonzero entry
   }
 }
 

@@ -87,7 +87,8 @@ struct MpCfg {
 struct PcgCtl {
   double ff, rr, rho, pq, alpha, beta, rz_old, tol2;
   int it, maxit, done, status;
-  int flexible, pad;
+  int flexible;
+  int x0_zero;  // 1 until a nonzero entry of the initial guess is seen (the host and the batch set it to 1)
 };
 
 // ---- handle -------------------------------------------------------------------------------------

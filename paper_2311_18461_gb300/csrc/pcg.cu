@@ -251,6 +251,32 @@ int pcg_body(stst_problem *h, cudaGraphConditionalHandle cond, int use_cond) {
   return STST_OK;
 }
 
+// Clears ctl->x0_zero if any entry of the initial guess is nonzero (benign race: every writer stores 0).
+__global__ void k_x0_zero_check(const double2 *__restrict__ x, long long n, PcgCtl *ctl) {
+  bool nz = false;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double2 v = x[i];
+    nz = nz || v.x != 0.0 || v.y != 0.0;
+  }
+  if (__syncthreads_or(nz) && threadIdx.x == 0) ctl->x0_zero = 0;
+}
+
+// For a zero initial guess: r = f and the per-CTA partials of ||r||^2, in the launch shape and order of
+// the residual mat-vec's final level (512 threads, the same grid), which is skipped then.
+__global__ void __launch_bounds__(512) k_resid_from_zero(const PcgCtl *ctl, const double2 *__restrict__ f,
+                                                         double2 *__restrict__ r, long long n, double *prr) {
+  if (!ctl->x0_zero) return;
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double2 v = f[i];
+    r[i] = v;
+    acc += (double)v.x * v.x + (double)v.y * v.y;
+  }
+  const double s = block_sum_d(acc, sh);
+  if (threadIdx.x == 0) prr[blockIdx.x] = s;
+}
+
 int pcg_init(stst_problem *h) {
   cudaStream_t st = h->stream;
   const long long N = h->N_dof;
@@ -258,8 +284,11 @@ int pcg_init(stst_problem *h) {
   const int prec = h->prec_mode;  // STST_PREC_* equals fd_apply's precision code
   double *P = h->partials;
   double *pA = P, *pB = P + STST_MAXPART, *pC = P + 2 * STST_MAXPART;
-  // r = f - A x, partials ||r||^2 ; ||f||^2
-  STST_TRY(run_plan(h->sys_plan, h->w_x, h->w_r, 0, 1, h->w_f, nullptr, nullptr, nullptr, st, nullptr, pB));
+  // r = f - A x, partials ||r||^2 ; ||f||^2. From x0 = 0 (the paper's start, Sec. 6) r = f needs no
+  // mat-vec: a device check of x0 makes the residual's passes skip themselves and a copy takes over.
+  k_x0_zero_check<<<g, 256, 0, st>>>((const double2 *)h->w_x, N, h->ctl);
+  STST_TRY(run_plan(h->sys_plan, h->w_x, h->w_r, 0, 1, h->w_f, nullptr, nullptr, &h->ctl->x0_zero, st, nullptr, pB));
+  k_resid_from_zero<<<g, 512, 0, st>>>(h->ctl, (const double2 *)h->w_f, (double2 *)h->w_r, N, pB);
   k_norm2<double2><<<g, 256, 0, st>>>((const double2 *)h->w_f, N, pC);
   // z = P^{-1} r with <r, z>
   STST_TRY(fd_apply(h, h->w_r, h->w_z, prec, h->w_r, pA, nullptr, h->w_t1, h->w_t2));
@@ -336,6 +365,7 @@ int pcg_run(stst_problem *h, const double *rhs, double *x, double tol, int maxit
   PcgCtl c0 = {};
   c0.tol2 = tol * tol;
   c0.maxit = maxit;
+  c0.x0_zero = 1;  // cleared on the device if x holds a nonzero entry
   c0.flexible = h->prec_mode != STST_PREC_FP64;
   *h->ctl_host = c0;
   STST_CUDA(cudaMemcpyAsync(h->ctl, h->ctl_host, sizeof(PcgCtl), cudaMemcpyHostToDevice, st));
