@@ -63,6 +63,21 @@ def test_rhs_lift_matches_oracle(n_el, p, T, nu):
     prob.close()
 
 
+def _smooth_3d(t, x1, x2, x3):
+    return np.exp(1j * (t + x1 - 2.0 * x3)) * (1.0 + x2 * x3) + 0.1 * t * x1
+
+
+def _forcing_3d(t, x1, x2, x3):
+    return (x1 + 1j * x2) * np.exp(-1j * t) + x3 ** 2
+
+
+def test_rhs_lift_3d_matches_oracle():
+    prob, b, xd, b_ref, xd_ref = _lift_case([3, 3, 4, 2], [2, 2, 3, 2], _smooth_3d, _forcing_3d, T=0.8, nu=1.1)
+    assert rel_err(xd, xd_ref) < 1e-12
+    assert rel_err(b, b_ref) < 1e-12
+    prob.close()
+
+
 def test_rhs_lift_with_potential_and_no_forcing():
     prob, b, xd, b_ref, xd_ref = _lift_case([5, 6, 4], [2, 2, 3], _smooth_2d, None, V=harmonic_potential(2))
     assert rel_err(xd, xd_ref) < 1e-12

@@ -52,7 +52,6 @@ def _brute_rhs(n_el, p, T, nu, u_fn, f_fn, V, XD):
         wts.append(w)
         B.append([_basis(p[l], n_el[l], L[l], x, k) for k in range(3)])
     # axes of the coefficient / grid tensors: (x_d, ..., x_1, t)
-    letters = "abc"[:d][::-1]  # x_d .. x_1
     def ev(C, ders):
         """sum_j C[j] prod_l d^{ders[l]} b_{j_l}(x_l) on the grid."""
         G = C
@@ -105,15 +104,24 @@ def _f2(t, x1, x2):
     return (x1 - 0.3) * np.exp(-1j * t) + 0.5 * x2 ** 2
 
 
+def _u3(t, x1, x2, x3):
+    return np.exp(1j * (t + x1 - 2.0 * x3)) * (1.0 + x2 * x3) + 0.1 * t * x1
+
+
+def _f3(t, x1, x2, x3):
+    return (x1 + 1j * x2) * np.exp(-1j * t) + x3 ** 2
+
+
 @pytest.mark.parametrize("n_el,p,T,nu,pot", [([3, 4], [2, 3], 1.0, 1.0, False), ([2, 3], [3, 2], 0.7, 1.3, True),
                                              ([2, 2, 3], [2, 2, 3], 1.2, 0.9, False),
-                                             ([2, 3, 2], [2, 3, 2], 1.0, 1.0, True)])
+                                             ([2, 3, 2], [2, 3, 2], 1.0, 1.0, True),
+                                             ([2, 1, 2, 1], [2, 2, 2, 2], 0.9, 1.2, True)])
 def test_full_lifting_rhs_is_load_of_f_minus_S_of_lifting(n_el, p, T, nu, pot):
     d = len(n_el) - 1
     V = None
     if pot:
         V = [[(lambda x: 1.0 + x ** 2)] * d, [(lambda x: np.cos(x))] * d]
-    u_fn, f_fn = (_u1, _f1) if d == 1 else (_u2, _f2)
+    u_fn, f_fn = {1: (_u1, _f1), 2: (_u2, _f2), 3: (_u3, _f3)}[d]
     disc = oracle_disc(n_el, p, T=T, nu=nu, potential=V)
     b, XD = orhs.full_lifting(disc, u_fn, f_fn)
     ref = _brute_rhs(n_el, p, T, nu, u_fn, f_fn, V, np.asarray(XD))
