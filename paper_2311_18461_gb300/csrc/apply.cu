@@ -1473,11 +1473,11 @@ static int tune_ts(stst_problem *h) {
 }
 
 // ---- choice between fused and separate 2D transforms (FP32 preconditioner, d = 2) -------------------
-// h->fd2d = number S of CTAs per time index of the fused kernel, 0 for the separate mode products.
+// h->fd2d = number S of CTAs per (t, x_3) slab of the fused kernel, 0 for the separate mode products.
 // Measured (autotune mode 1): a forward plus a backward transform of each variant timed on work
-// vectors, cached per (n_t, n_1, n_2). Otherwise S is the smallest split giving two CTAs per SM.
+// vectors, cached per shape. Otherwise S is the smallest split giving two CTAs per SM.
 int g_fd2d_mode = 0;  // 0 chosen per shape, 1 separate kernels, 2 fused where it fits, 10 + S fused with split S
-static std::map<std::tuple<int, int, int>, int> g_fd2d_cache;
+static std::map<std::tuple<int, int, int, int>, int> g_fd2d_cache;  // (n_t, n_1, n_2, n_3 or 0 for d = 2)
 
 static int fd2d_default_split(const stst_problem *h) {
   int S = 1;
@@ -1496,7 +1496,7 @@ static int tune_fd2d(stst_problem *h) {
     h->fd2d = fd2d_default_split(h);
     return STST_OK;
   }
-  const auto key = std::make_tuple(h->n_t(), h->dir[1].n, h->dir[2].n);
+  const auto key = std::make_tuple(h->n_t(), h->dir[1].n, h->dir[2].n, h->d == 3 ? h->dir[3].n : 0);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_fd2d_cache.find(key);

@@ -125,7 +125,7 @@ struct stst_problem {
   MpCfg mp_cfg[STST_MAXD + 1];     // mode-product tile per direction (autotuned or default)
   float mp_us[STST_MAXD + 1];      // its measured time per launch (0: not measured)
   int tuned;
-  int fd2d;                        // fused 2D spatial transforms in the FP32 preconditioner (d = 2)
+  int fd2d;                        // CTAs per slab of the fused transforms (FP32 preconditioner, d = 2 or 3), 0: separate
   int eig_src[STST_MAXD + 1];
   double *U[STST_MAXD + 1];
   float *U32[STST_MAXD + 1];
