@@ -117,6 +117,7 @@ static int add_branch(stst_batch_s *b, cudaGraph_t G, int i, const double *rhs, 
   STST_CUDA(cudaGraphAddNode(&n_loop, G, &n_pre, nullptr, 1, &cp));
   STST_TRY(capture_into(st, cp.conditional.phGraph_out[0]));
   s = pcg_body(h, cond, 1);
+  if (s == STST_OK) s = pcg_body(h, cond, 1);  // two iterations per body, as in the single-problem graph
   s2 = end_capture(st);
   if (s != STST_OK) return s;
   if (s2 != STST_OK) return s2;
