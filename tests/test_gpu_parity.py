@@ -164,6 +164,29 @@ def test_pcg_fp64_matches_oracle_iterates(n_el, p, kind):
     assert res < 1e-9
 
 
+@pytest.mark.parametrize("where", ["last", "first", "middle"])
+def test_pcg_nonzero_initial_guess_follows_the_oracle(where):
+    """From x0 = 0 the residual is f without a mat-vec (a device check of x0); any nonzero entry of x0,
+    wherever it sits in the vector, must send the solve through r = f - A x0: the iterates then follow
+    the oracle's PCG from the same x0 (FP64 path)."""
+    prob, disc = _problem([9, 11, 7], [2, 3, 2], "harmonic")
+    prob.build_fd()
+    b = random_complex(prob.n_dof, 27)
+    x0 = np.zeros(prob.n_dof, dtype=complex)
+    k = {"last": prob.n_dof - 1, "first": 0, "middle": prob.n_dof // 2 + 3}[where]
+    x0[k] = 0.7 - 0.2j
+    xd = to_dev(x0)
+    x, st, it, rr = prob.pcg(to_dev(b), xd, tol=1e-10, maxit=200)
+    F = ofd.FastDiagonalization(disc)
+    xo, ito, rro, _ = opcg.pcg(disc.apply, F.apply, b, x0=x0, tol=1e-10, maxit=200)
+    assert st == 0 and abs(it - ito) <= 1
+    assert rel_err(to_np(x), xo) < 1e-9
+    # the same solve from zero takes the zero-guess path and still matches the oracle from zero
+    x, st, it0, rr = prob.pcg(to_dev(b), None, tol=1e-10, maxit=200)
+    xo0, ito0, _, _ = opcg.pcg(disc.apply, F.apply, b, tol=1e-10, maxit=200)
+    assert st == 0 and abs(it0 - ito0) <= 1 and rel_err(to_np(x), xo0) < 1e-9
+
+
 @pytest.mark.parametrize("n_el,p,kind", [([9, 11, 7], [2, 3, 2], "harmonic"), ([5, 6, 5, 7], [2, 2, 3, 2], None)])
 def test_pcg_fp32_preconditioner_solution(n_el, p, kind):
     prob, disc = _problem(n_el, p, kind, prec=S.STST_PREC_FP32)
