@@ -151,12 +151,15 @@ def source_hash(span):
     return hashlib.sha256(text[i:j].encode()).hexdigest()[:16]
 
 
-def traffic_for(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if taken on the kernel's current source."""
+def traffic_for(kernel, shape):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the kernel's current source and
+    on this workload's shape (`shape`: the number of unknowns and the plan's band applications per one)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(path)).get("kernels", {}).get(kernel)
         if not rec or rec.get("source_hash") != source_hash(rec["span"]):
+            return None
+        if rec.get("shape") != shape:
             return None
         return rec.get("dram_bytes_per_launch")
     except Exception:
@@ -645,7 +648,7 @@ def run_ours(args):
         S.stst_profile(prob.h, 1)
         flush.fill_(1)
         torch.cuda.nvtx.range_push("profiled_solve")
-        solve(x)
+        _, it_prof, _ = solve(x)
         torch.cuda.nvtx.range_pop()
         prof_solve = S.stst_profile_read(prob.h)
         S.stst_profile(prob.h, 0)
@@ -653,6 +656,18 @@ def run_ours(args):
         for k, (cnt, tot) in prof_solve.items():
             per = prof_ops[k][1] / prof_ops[k][0] if k in prof_ops else tot / cnt
             prof[k] = (cnt, per * cnt)
+        # kernels launched in the timed steps: the profiled solve runs the loop as plain launches, the
+        # timed ones as graph bodies of several iterations (the last body may run past convergence)
+        plain = int(sum(v[0] for v in prof.values()))
+        if args.solver == "ir":
+            launches = plain * args.steps
+            launch_basis = "plain-launch count of one profiled solve x steps"
+        else:
+            kpb, ipb = S.stst_pcg_graph_info(prob.h)
+            setup = plain - it_prof * (kpb // ipb)
+            launches = sum(setup + -(-int(k) // ipb) * kpb for k in iters)
+            launch_basis = (f"setup and PCG start {setup} kernels + ceil(iterations / {ipb}) graph bodies of "
+                            f"{kpb} kernel nodes, per timed step")
 
     n_dof = prob.n_dof
     d = cfg["d"]
@@ -691,7 +706,7 @@ def run_ours(args):
                                % (N_SM, FP64_FMA_PER_CLK_SM if dom.endswith("f64") else FP32_FMA_PER_CLK_SM,
                                   SM_MAX_MHZ_NOMINAL)) if roof["bound"] == "alu" else f"hbm_gbs of {peak_src}"
         roof["launch_ms"] = per_launch_s * 1e3
-        roof["traffic"] = traffic_for(dom)
+        roof["traffic"] = traffic_for(dom, {"n_dof": n_dof, "band_apps_per_dof": band_apps})
         roof["share_of_solve"] = tot / sum(v[1] for v in prof.values())
     out = {
         "metric": METRIC,
@@ -726,7 +741,8 @@ def run_ours(args):
         "fused_2d_transforms": S.stst_fused_transforms_info(prob.h),
         "kernels_ms_per_solve": {k: round(v[1], 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
         "kernel_launches_per_solve": {k: v[0] for k, v in prof.items()},
-        "gpu_launches": int(sum(v[0] for v in prof.values())) * args.steps,
+        "gpu_launches": launches,
+        "gpu_launches_basis": launch_basis,
         "roofline": roof,
         "clocks": clocks,
         "e2e": {"value": e2e_ms / 1e3, "unit": "s", "h2d_bytes_per_step": 16 * n_dof, "d2h_bytes_per_step": 16 * n_dof},

@@ -303,8 +303,9 @@ int stst_tile_info(stst_handle h, int dir, int *cols_per_cta, int *rows_per_cta,
  * synchronizes on return; stst_pcg_solve then runs its loop as plain launches
  * with one host check per iteration instead of the CUDA graph.
  * stst_profile_read: record idx (0-based) -> kernel name (NUL-terminated, at
- * most name_len bytes), launch count and total device milliseconds. Returns
- * STST_ERR_ARG past the last record. Host outputs.
+ * most name_len bytes), kernel launch count and total device milliseconds (a
+ * record may time a short run of kernels as one: the count is of kernels, the
+ * time of the run). Returns STST_ERR_ARG past the last record. Host outputs.
  */
 int stst_profile(stst_handle h, int enable);
 
@@ -316,6 +317,16 @@ int stst_profile(stst_handle h, int enable);
  * flops_per_dof (host, may be NULL): the algorithmic flops of one apply_sys per unknown.
  */
 int stst_plan_info(stst_handle h, int *n_passes, int *band_apps, double *flops_per_dof);
+
+/*
+ * stst_pcg_graph_info: the CUDA graph that runs the PCG loop of stst_pcg_solve (Sec. 6 solves
+ * with P-hat, Algorithm 1, as the preconditioner): a device-side WHILE node whose body holds
+ * iterations_per_body iterations of the loop in kernels_per_body kernel nodes (host outputs, may be
+ * NULL). A solve that takes k iterations launches ceil(k / iterations_per_body) bodies; every
+ * kernel of a body launched after convergence returns at once. STST_ERR_STATE before the first
+ * unprofiled stst_pcg_solve on the handle (the graph is built then).
+ */
+int stst_pcg_graph_info(stst_handle h, int *kernels_per_body, int *iterations_per_body);
 int stst_profile_read(stst_handle h, int idx, char *name, int name_len, long long *count, double *total_ms);
 
 /* ======================================================================================

@@ -10,22 +10,24 @@ from ._lib import (StstError, lib, library_path, stst_create, stst_create2, STST
                    stst_destroy, stst_strerror, stst_sizes, stst_quadrature_points, stst_assemble_1d,
                    stst_set_potential, stst_build_fd, stst_apply_sys, stst_apply_prec, stst_rhs,
                    stst_rhs_noalloc, stst_rhs_lift, stst_pcg_solve, stst_ir_solve, stst_profile, stst_profile_read,
-                   stst_plan_info, stst_batch_create, stst_batch_solve, stst_batch_destroy, stst_set_autotune,
+                   stst_plan_info, stst_pcg_graph_info, stst_batch_create, stst_batch_solve, stst_batch_destroy,
+                   stst_set_autotune,
                    stst_set_time_solver, stst_set_fused_transforms, stst_fused_transforms_info,
                    stst_time_solver_info, stst_last_cuda_error, stst_tile_info, stst_ws_create,
                    stst_ws_destroy, stst_ws_num_params, stst_ws_get_params, stst_ws_set_params,
                    stst_ws_forward, stst_ws_set_output_scale, stst_ws_grad, stst_ws_train_step,
                    stst_pod_basis, stst_pod_project, stst_pod_expand, stst_pcg_solve_guarded, Problem,
-                   STST_PREC_FP64, STST_PREC_FP32, STST_PREC_BF16)
+                   STST_PREC_FP64, STST_PREC_FP32, STST_PREC_BF16, STST_OK, STST_NOT_CONVERGED, STST_BREAKDOWN,
+                   STST_NOT_HPD, STST_TIMEOUT)
 
 __all__ = ["StstError", "lib", "library_path", "stst_create", "stst_create2", "STST_FORM_LS", "STST_FORM_UW",
            "stst_destroy", "stst_strerror", "stst_sizes", "stst_quadrature_points", "stst_assemble_1d",
            "stst_set_potential", "stst_build_fd", "stst_apply_sys", "stst_apply_prec", "stst_rhs",
            "stst_rhs_noalloc", "stst_rhs_lift", "stst_pcg_solve", "stst_ir_solve", "stst_profile", "stst_profile_read",
-           "stst_plan_info", "stst_batch_create", "stst_batch_solve", "stst_batch_destroy",
+           "stst_plan_info", "stst_pcg_graph_info", "stst_batch_create", "stst_batch_solve", "stst_batch_destroy",
            "stst_set_autotune", "stst_set_time_solver", "stst_set_fused_transforms",
            "stst_fused_transforms_info", "stst_time_solver_info", "stst_last_cuda_error", "stst_tile_info",
            "stst_ws_create", "stst_ws_destroy", "stst_ws_num_params", "stst_ws_get_params",
            "stst_ws_set_params", "stst_ws_forward", "stst_ws_set_output_scale", "stst_ws_grad",
            "stst_ws_train_step", "stst_pod_basis", "stst_pod_project", "stst_pod_expand",
-           "stst_pcg_solve_guarded", "Problem", "STST_PREC_FP64", "STST_PREC_FP32", "STST_PREC_BF16"]
+           "stst_pcg_solve_guarded", "Problem", "STST_PREC_FP64", "STST_PREC_FP32", "STST_PREC_BF16", "STST_OK", "STST_NOT_CONVERGED", "STST_BREAKDOWN", "STST_NOT_HPD", "STST_TIMEOUT"]

@@ -12,6 +12,7 @@ library_path = os.path.join(HERE, "libstst.so")
 
 STST_PREC_FP64, STST_PREC_FP32, STST_PREC_BF16 = 0, 1, 2
 STST_FORM_LS, STST_FORM_UW = 0, 1
+STST_OK, STST_NOT_CONVERGED, STST_BREAKDOWN, STST_NOT_HPD, STST_TIMEOUT = 0, 1, 2, 3, 4
 STATUS = {0: "OK", 1: "NOT_CONVERGED", 2: "BREAKDOWN", 3: "NOT_HPD", 4: "TIMEOUT", -1: "ERR_ARG",
           -2: "ERR_HANDLE", -3: "ERR_OOM", -4: "ERR_CUDA", -5: "ERR_STATE"}
 
@@ -58,6 +59,7 @@ def lib():
             "stst_batch_solve": [P, D, I, IP, DP, IP],
             "stst_batch_destroy": [P],
             "stst_plan_info": [P, IP, IP, DP],
+            "stst_pcg_graph_info": [P, IP, IP],
             "stst_profile_read": [P, I, ctypes.c_char_p, I, ctypes.POINTER(LL), DP],
             "stst_set_autotune": [I],
             "stst_set_time_solver": [I],
@@ -250,6 +252,13 @@ def stst_plan_info(h):
     f = ctypes.c_double()
     _chk(lib().stst_plan_info(h, ctypes.byref(n), ctypes.byref(a), ctypes.byref(f)), "stst_plan_info")
     return n.value, a.value, f.value
+
+
+def stst_pcg_graph_info(h):
+    k = ctypes.c_int()
+    i = ctypes.c_int()
+    _chk(lib().stst_pcg_graph_info(h, ctypes.byref(k), ctypes.byref(i)), "stst_pcg_graph_info")
+    return k.value, i.value
 
 
 def stst_profile_read(h):

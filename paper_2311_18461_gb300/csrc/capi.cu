@@ -879,6 +879,14 @@ int stst_profile(stst_handle h, int enable) {
   return STST_OK;
 }
 
+int stst_pcg_graph_info(stst_handle h, int *kernels_per_body, int *iterations_per_body) {
+  STST_TRY(check(h));
+  if (!h->pcg_graph_valid) return STST_ERR_STATE;
+  if (kernels_per_body) *kernels_per_body = h->pcg_body_kernels;
+  if (iterations_per_body) *iterations_per_body = 2;
+  return STST_OK;
+}
+
 int stst_plan_info(stst_handle h, int *n_passes, int *band_apps, double *flops_per_dof) {
   STST_TRY(check(h));
   int apps = 0;

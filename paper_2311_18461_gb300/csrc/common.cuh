@@ -161,6 +161,7 @@ struct stst_problem {
   // PCG graph
   cudaGraphExec_t pcg_exec;
   int pcg_graph_valid;
+  int pcg_body_kernels;  // kernel nodes in the WHILE node's body (two iterations)
   int pcg_graph_flexible;
   cudaGraphExec_t ir_exec;
   int ir_graph_valid;

@@ -787,7 +787,7 @@ int fd_setup_launch(stst_problem *h) {
     // FP64 factors need full accuracy; the FP32 preconditioner needs FP32 accuracy only
     const int refine = (h->prec_mode == STST_PREC_FP64) ? 3 : 1;
     for (int it = 0; it < refine; ++it) {
-      STST_PROF("eig_refine_f64", st);
+      STST_PROF_N("eig_refine_f64", st, 4);
       k_oa_band<<<g, 64, 0, st>>>(M.d, L.d, X, n, p, PM, PL);
       k_oa_gram<<<g, 64, 0, st>>>(X, PM, PL, n, R, S);
       k_oa_E<<<g, 64, 0, st>>>(R, S, n, E, h->lam[l]);
@@ -804,7 +804,7 @@ int fd_setup_launch(stst_problem *h) {
       STST_CUDA(cudaMemcpyAsync(h->U[l], h->U[src], sizeof(double) * n * n, cudaMemcpyDeviceToDevice, st));
       STST_CUDA(cudaMemcpyAsync(h->lam[l], h->lam[src], sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     }
-    STST_TRY(launch_to_f32(h->U[l], h->U32[l], (long long)h->dir[l].n * h->dir[l].n, st));
+    { STST_PROF("to_f32", st); STST_TRY(launch_to_f32(h->U[l], h->U32[l], (long long)h->dir[l].n * h->dir[l].n, st)); }
     if (h->prec_mode == STST_PREC_BF16) STST_TRY(launch_u_to_bf16(h->U[l], h->dir[l].n, h->Ubf[l], st));
   }
   const BandMat &Lt = h->mats[0][0], &Mt = h->mats[0][1], &KAt = h->mats[0][2];

@@ -286,14 +286,20 @@ int pcg_init(stst_problem *h) {
   double *pA = P, *pB = P + STST_MAXPART, *pC = P + 2 * STST_MAXPART;
   // r = f - A x, partials ||r||^2 ; ||f||^2. From x0 = 0 (the paper's start, Sec. 6) r = f needs no
   // mat-vec: a device check of x0 makes the residual's passes skip themselves and a copy takes over.
-  k_x0_zero_check<<<g, 256, 0, st>>>((const double2 *)h->w_x, N, h->ctl);
+  { STST_PROF("pcg_init", st); k_x0_zero_check<<<g, 256, 0, st>>>((const double2 *)h->w_x, N, h->ctl); }
   STST_TRY(run_plan(h->sys_plan, h->w_x, h->w_r, 0, 1, h->w_f, nullptr, nullptr, &h->ctl->x0_zero, st, nullptr, pB));
-  k_resid_from_zero<<<g, 512, 0, st>>>(h->ctl, (const double2 *)h->w_f, (double2 *)h->w_r, N, pB);
-  k_norm2<double2><<<g, 256, 0, st>>>((const double2 *)h->w_f, N, pC);
+  {
+    STST_PROF_N("pcg_init", st, 2);
+    k_resid_from_zero<<<g, 512, 0, st>>>(h->ctl, (const double2 *)h->w_f, (double2 *)h->w_r, N, pB);
+    k_norm2<double2><<<g, 256, 0, st>>>((const double2 *)h->w_f, N, pC);
+  }
   // z = P^{-1} r with <r, z>
   STST_TRY(fd_apply(h, h->w_r, h->w_z, prec, h->w_r, pA, nullptr, h->w_t1, h->w_t2));
-  k_pcg_init<<<1, 1024, 0, st>>>(h->ctl, pC, g, pB, g, pA, fd_partials_count(h));
-  k_copy_vec<double2><<<g, 256, 0, st>>>((const double2 *)h->w_z, (double2 *)h->w_p, N, &h->ctl->done);
+  {
+    STST_PROF_N("pcg_init", st, 2);
+    k_pcg_init<<<1, 1024, 0, st>>>(h->ctl, pC, g, pB, g, pA, fd_partials_count(h));
+    k_copy_vec<double2><<<g, 256, 0, st>>>((const double2 *)h->w_z, (double2 *)h->w_p, N, &h->ctl->done);
+  }
   STST_CUDA(cudaGetLastError());
   return STST_OK;
 }
@@ -342,6 +348,22 @@ static int build_pcg_graph(stst_problem *h) {
     if (e != cudaSuccess) stst_last_cuda = e;
     return s != STST_OK ? s : STST_ERR_CUDA;
   }
+  size_t n_nodes = 0;
+  e = cudaGraphGetNodes(body, nullptr, &n_nodes);
+  std::vector<cudaGraphNode_t> nodes(n_nodes);
+  if (e == cudaSuccess && n_nodes) e = cudaGraphGetNodes(body, nodes.data(), &n_nodes);
+  int kernels = 0;
+  for (size_t i = 0; e == cudaSuccess && i < n_nodes; ++i) {
+    cudaGraphNodeType t;
+    e = cudaGraphNodeGetType(nodes[i], &t);
+    kernels += (e == cudaSuccess && t == cudaGraphNodeTypeKernel);
+  }
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    stst_last_cuda = e;
+    return STST_ERR_CUDA;
+  }
+  h->pcg_body_kernels = kernels;
   e = cudaGraphInstantiate(&h->pcg_exec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) {

@@ -13,10 +13,11 @@ static cudaEvent_t take_event(Profiler *p) {
   return p->pool[p->pool_used++];
 }
 
-void prof_begin(const char *name, cudaStream_t s) {
+void prof_begin(const char *name, cudaStream_t s, int kernels) {
   Profiler *p = g_prof;
   ProfRecord r;
   r.name = name;
+  r.kernels = kernels;
   r.a = take_event(p);
   r.b = take_event(p);
   cudaEventRecord(r.a, s);
@@ -45,7 +46,7 @@ void prof_flush(Profiler *p) {
       p->count.push_back(0);
     }
     p->total_ms[k] += ms;
-    p->count[k] += 1;
+    p->count[k] += r.kernels;
   }
   p->pending.clear();
   p->pool_used = 0;

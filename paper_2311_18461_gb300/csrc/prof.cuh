@@ -1,7 +1,8 @@
 // Per-kernel launch timing with CUDA events (the library's tracing hook). When a handle has
 // profiling enabled, each API call installs the handle's profiler as the current one; every launch
-// site brackets its kernel with prof_begin / prof_end, which record events on the launch stream.
-// Durations are collected by stst_profile_read. Graph-captured launches are never profiled.
+// site brackets its kernel (or a short run of kernels, counted as such) with prof_begin / prof_end,
+// which record events on the launch stream. Durations and kernel launch counts are collected by
+// stst_profile_read. Graph-captured launches are never profiled. Scopes do not nest.
 #pragma once
 #include <cuda_runtime.h>
 #include <string>
@@ -10,6 +11,7 @@
 struct ProfRecord {
   std::string name;
   cudaEvent_t a, b;
+  int kernels;  // kernel launches inside the bracket
 };
 
 struct Profiler {
@@ -24,17 +26,18 @@ struct Profiler {
 extern thread_local Profiler *g_prof;
 extern thread_local cudaStream_t g_prof_stream;
 
-void prof_begin(const char *name, cudaStream_t s);
+void prof_begin(const char *name, cudaStream_t s, int kernels);
 void prof_end(cudaStream_t s);
 void prof_flush(Profiler *p);
 
 struct ProfScope {
   bool on;
-  ProfScope(const char *name, cudaStream_t s) : on(g_prof != nullptr) {
-    if (on) prof_begin(name, s);
+  ProfScope(const char *name, cudaStream_t s, int kernels = 1) : on(g_prof != nullptr) {
+    if (on) prof_begin(name, s, kernels);
   }
   ~ProfScope() {
     if (on) prof_end(g_prof_stream);
   }
 };
 #define STST_PROF(name, stream) ProfScope prof_scope_##__LINE__(name, stream)
+#define STST_PROF_N(name, stream, kernels) ProfScope prof_scope_##__LINE__(name, stream, kernels)

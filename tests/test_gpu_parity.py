@@ -187,6 +187,34 @@ def test_pcg_nonzero_initial_guess_follows_the_oracle(where):
     assert st == 0 and abs(it0 - ito0) <= 1 and rel_err(to_np(x), xo0) < 1e-9
 
 
+def test_profile_counts_kernels_and_graph_body_holds_two_iterations():
+    """The tracing hook counts kernel launches (a record may time a short run of them), and the PCG
+    graph's WHILE body holds two iterations of the plain loop: two more plain iterations launch
+    exactly one body's kernel nodes."""
+    prob, disc = _problem([9, 11, 7], [2, 3, 2], "harmonic", prec=S.STST_PREC_FP32)
+    prob.build_fd()
+    b = to_dev(random_complex(prob.n_dof, 31))
+    x = prob.vec()
+    with pytest.raises(S.StstError):
+        S.stst_pcg_graph_info(prob.h)  # the graph is built by the first unprofiled solve
+    counts = []
+    for maxit in (1, 3):
+        x.zero_()
+        S.stst_profile(prob.h, 1)
+        st, it, rr = S.stst_pcg_solve(prob.h, b, x, 1e-14, maxit)
+        prof = S.stst_profile_read(prob.h)
+        S.stst_profile(prob.h, 0)
+        assert st == S.STST_NOT_CONVERGED and it == maxit
+        assert prof["pcg_update_xr"][0] == maxit and prof["pcg_init"][0] == 5
+        counts.append(sum(c for c, _ in prof.values()))
+    x.zero_()
+    st, it, rr = S.stst_pcg_solve(prob.h, b, x, 1e-10, 200)
+    assert st == 0
+    kpb, ipb = S.stst_pcg_graph_info(prob.h)
+    assert ipb == 2 and kpb == counts[1] - counts[0]
+    prob.close()
+
+
 @pytest.mark.parametrize("n_el,p,kind", [([9, 11, 7], [2, 3, 2], "harmonic"), ([5, 6, 5, 7], [2, 2, 3, 2], None)])
 def test_pcg_fp32_preconditioner_solution(n_el, p, kind):
     prob, disc = _problem(n_el, p, kind, prec=S.STST_PREC_FP32)
