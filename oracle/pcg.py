@@ -12,7 +12,9 @@ this equals ||r_k|| / ||r_0||).
 `flexible=True` replaces beta = <r_k+1, z_k+1>/<r_k, z_k> by the
 Polak-Ribiere form <r_k+1, z_k+1 - z_k>/<r_k, z_k>, the standard choice when
 the preconditioner is applied inexactly (not in the paper; parity unpinned
-beyond the exact-preconditioner case, where both forms coincide).
+beyond the exact-preconditioner case, where both forms coincide: the extra term
+<r_k+1, z_k> vanishes in exact arithmetic for a fixed Hermitian preconditioner
+or one rescaled at each step, so no closed form checks it).
 """
 import numpy as np
 
