@@ -332,7 +332,7 @@ int stst_profile_read(stst_handle h, int idx, char *name, int name_len, long lon
 /* ======================================================================================
  * Learned warm start. The paper has no learned component: these calls are an extension.
  * A network maps a problem's data parameters to coordinates c in a basis Q of the solution
- * space; x0 = Q^T c starts PCG (stst_pcg_solve_guarded), which stays the judge of the result.
+ * space; x0 = Q^T c starts PCG (stst_pcg_solve_guarded), which stays the arbiter of the result.
  * All arrays are device memory owned by the caller unless stated; calls are ordered on the
  * given stream (the network's own stream for stst_ws_*).
  * ====================================================================================== */

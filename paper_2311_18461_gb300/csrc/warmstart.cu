@@ -2,7 +2,7 @@
 //
 // A fully connected network maps a problem's data parameters (e.g. a wavepacket's centre, width and
 // momentum) to coordinates c in a real orthonormal basis of the solution space; x0 = Q^T c (optionally times
-// a per-problem complex phase) starts PCG, which stays the judge of the result.
+// a per-problem complex phase) starts PCG, which stays the arbiter of the result.
 //   * basis: randomized subspace iteration on the snapshot matrix Y whose rows are solutions the solver
 //     produced (Halko, Martinsson and Tropp 2011, Alg. 4.4); every orthonormalization is CholeskyQR2 with the
 //     Gram matrices accumulated in FP64;

@@ -7,7 +7,7 @@ an input basis; its output is the coordinates of x0 in an output basis of the so
 Stage s > 0 is trained on the remaining error of the stages before it, rescaled to unit RMS, so the
 BF16 rounding of the weights (2^-9 relative) limits the cascade to about its product over the stages.
 With a fixed potential the exact map c0 -> u is linear, so a linear network can learn it to the
-accuracy of the two bases; PCG from x0 stays the judge of the result.
+accuracy of the two bases; PCG from x0 stays the arbiter of the result.
 
 The pipeline orders library calls and owns device buffers; every numerical step on the device runs in
 the library's kernels; one-time scalings of the training data and the random draws are done on the host:

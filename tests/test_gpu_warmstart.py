@@ -270,7 +270,7 @@ def test_guarded_pcg_keeps_good_and_rejects_bad_guesses():
 
 
 def test_trained_warm_start_saves_iterations():
-    """Small version of the learned-warm-start workload: train on 400 solves, judge on 12 new ones."""
+    """Small version of the learned-warm-start workload: train on 400 solves, evaluate on 12 new ones."""
     from paper_2311_18461_gb300.warmstart import WarmStart
     torch = _torch()
     prob = _small_problem()
@@ -298,6 +298,6 @@ def test_trained_warm_start_saves_iterations():
         err.append((e0, (torch.linalg.vector_norm(xw - xc) / torch.linalg.vector_norm(xc)).item()))
     ws.close()
     prob.close()
-    # the judge: the same tolerance is met from the learned start in fewer iterations
+    # the arbiter: the same tolerance is met from the learned start in fewer iterations
     assert np.mean(warm) < np.mean(cold) - 1.0, (cold, warm, err)
     assert max(e[1] for e in err) < 1e-5
