@@ -241,6 +241,21 @@ def test_iterative_refinement_solution(n_el, p, kind):
     assert res < 1e-9
 
 
+def test_iterative_refinement_degenerate_starts():
+    """IR started at the solution stops after its first FP64 residual, with no inner solve and x untouched;
+    maxit = 0 only measures the residual of the start (x0 = 0: relative residual 1)."""
+    prob, disc = _problem([9, 11, 7], [2, 3, 2], "harmonic", prec=S.STST_PREC_FP32)
+    prob.build_fd()
+    b = random_complex(prob.n_dof, 24)
+    xo, _, _, _ = opcg.pcg(disc.apply, ofd.FastDiagonalization(disc).apply, b, tol=1e-13, maxit=300)
+    x, st, it, outer, rr = prob.ir(to_dev(b), to_dev(xo), tol=1e-10, maxit=10)
+    assert st == 0 and outer == 0 and it == 0 and rr <= 1e-10
+    assert np.array_equal(to_np(x), xo)
+    x, st, it, outer, rr = prob.ir(to_dev(b), None, tol=1e-10, maxit=0)
+    assert st == S.STST_NOT_CONVERGED and outer == 0 and it == 0
+    assert abs(rr - 1.0) < 1e-12 and not np.any(to_np(x))
+
+
 def test_c1_workload_end_to_end():
     """1D+t, p=2, 32x32, u = exp(i pi^2 t) sin(pi x): rhs by lifting, PCG to 1e-10, against the oracle."""
     from inputs import CONFIGS, initial_factors, product_fn
