@@ -660,6 +660,64 @@ int stst_assemble_1d(int p, int n_el, double length, int bc, const double *weigh
   return STST_OK;
 }
 
+// Additive potential V = sum_l v_l(x_l) (each factor differs from 1 in one direction only, one factor per
+// direction): the operator is i d_t + sum_l H_l with H_l = -nu d_ll + v_l, so the least-squares matrix is
+//   L_t (x) M..M + sum_l KA (x) G_l + sum_l M_t (x) A_l + 2 sum_{l<k} M_t (x) G_l (x) G_k
+// (each G_l / A_l at position l, M elsewhere), G_l = nu L_l + M_{v_l} (the Galerkin matrix of H_l) and
+// A_l = nu^2 J_l + M_{v_l^2} - nu (K2_{v_l} + K2_{v_l}^T). The cross terms 2 nu^2 L (x) L + 2 M_v (x) M_v
+// - nu M_v (x) K2S - nu K2S (x) M_v of the general expansion are 2 G_l (x) G_k because K2 + K2^T = -2 L
+// for spatial functions that vanish on the boundary (integration by parts). The same matrix in fewer
+// Kronecker terms: the mat-vec needs as many band applications as with V = 0.
+static int additive_terms(stst_problem *h, int rank, const int *dir_of, const int (*wm)[3], const int (*wk)[3],
+                          const int (*pm)[3][3], std::vector<Term> &T) {
+  const int d = h->d;
+  const double nu = h->nu;
+  int gm[STST_MAXD + 1], am[STST_MAXD + 1];
+  double gc[STST_MAXD + 1], ac[STST_MAXD + 1];
+  for (int l = 1; l <= d; ++l) {
+    int r = -1;
+    for (int q = 0; q < rank; ++q)
+      if (dir_of[q] == l) r = q;
+    if (r < 0) {
+      gm[l] = SM_L, gc[l] = nu;
+      am[l] = SM_J, ac[l] = nu * nu;
+      continue;
+    }
+    const int g = add_combo(h, l, SM_L, nu, wm[l][r], 1.0);
+    if (g < 0) return g;
+    const int a1 = add_combo(h, l, SM_J, nu * nu, pm[l][r][r], 1.0);
+    if (a1 < 0) return a1;
+    const int a = add_combo(h, l, a1, 1.0, wk[l][r], -nu);
+    if (a < 0) return a;
+    gm[l] = g, gc[l] = 1.0;
+    am[l] = a, ac[l] = 1.0;
+  }
+  auto mk = [&](double c, int tm) {
+    Term t;
+    t.coef = c;
+    t.m[0] = tm;
+    for (int l = 1; l <= STST_MAXD; ++l) t.m[l] = (l <= d) ? SM_M : 0;
+    return t;
+  };
+  T.clear();
+  T.push_back(mk(1.0, TM_L));
+  for (int l = 1; l <= d; ++l) {
+    Term w = mk(gc[l], TM_KA);
+    w.m[l] = gm[l];
+    T.push_back(w);
+    Term a = mk(ac[l], TM_M);
+    a.m[l] = am[l];
+    T.push_back(a);
+    for (int k = l + 1; k <= d; ++k) {
+      Term c = mk(2.0 * gc[l] * gc[k], TM_M);
+      c.m[l] = gm[l];
+      c.m[k] = gm[k];
+      T.push_back(c);
+    }
+  }
+  return STST_OK;
+}
+
 int stst_set_potential(stst_handle h, int rank, const double *v_qp) {
   STST_TRY(check(h));
   ApiScope scope(h);
@@ -695,6 +753,7 @@ int stst_set_potential(stst_handle h, int rank, const double *v_qp) {
     // factor id f in [0, rank): v_{f,l}; "one" if the samples are identically 1.
     int wm[STST_MAXD + 1][3], wk[STST_MAXD + 1][3];
     int pm[STST_MAXD + 1][3][3];
+    bool onef[STST_MAXD + 1][3];
     int off = 0;
     for (int l = 1; l <= d; ++l) {
       const int Ql = h->dir[l].Q();
@@ -711,6 +770,7 @@ int stst_set_potential(stst_handle h, int rank, const double *v_qp) {
           if (!memcmp(a, b, sizeof(double) * Ql)) { canon[r] = canon[s]; break; }
         }
       }
+      for (int r = 0; r < rank; ++r) onef[l][r] = one[r];
       for (int r = 0; r < rank; ++r) {
         if (one[r]) { wm[l][r] = SM_M; wk[l][r] = SM_K2S; continue; }
         if (canon[r] != r) { wm[l][r] = wm[l][canon[r]]; wk[l][r] = wk[l][canon[r]]; continue; }
@@ -732,6 +792,25 @@ int stst_set_potential(stst_handle h, int rank, const double *v_qp) {
           pm[l][r][s] = add_band(h, l, MK_M, wp);
         }
       off += Ql;
+    }
+    // which direction each factor lives in, if every factor is 1 in all directions but one
+    int dir_of[3] = {-1, -1, -1};
+    bool additive = true, taken[STST_MAXD + 1] = {};
+    for (int r = 0; r < rank && additive; ++r) {
+      for (int l = 1; l <= d; ++l)
+        if (!onef[l][r]) {
+          if (dir_of[r] >= 0) additive = false;
+          dir_of[r] = l;
+        }
+      if (dir_of[r] < 0 || taken[dir_of[r]]) additive = false;
+      else taken[dir_of[r]] = true;
+    }
+    if (additive) {
+      STST_TRY(additive_terms(h, rank, dir_of, wm, wk, pm, terms));
+      h->pot_rank = rank;
+      STST_TRY(replan(h, terms));
+      STST_CUDA(cudaStreamSynchronize(st));
+      return STST_OK;
     }
     for (int r = 0; r < rank; ++r) {
       for (int s = 0; s < rank; ++s) {

@@ -118,6 +118,55 @@ def _potential(kind, d):
             [(lambda x: 1 + 0 * x), (lambda x: np.exp(-(x - 0.4) ** 2 / 0.1))]]
 
 
+def _additive_A(disc, V):
+    """A for V = sum_l v_l(x_l) in the grouped form the mat-vec planner uses:
+    L_t (x) M..M + sum_l W (x) G_l + sum_l M_t (x) A_l + 2 sum_{l<k} M_t (x) G_l (x) G_k, with
+    G_l = nu L + M_{v_l} and A_l = nu^2 J + M_{v_l^2} - nu (K2_{v_l} + K2_{v_l}^T)."""
+    d, nu = disc.d, disc.nu
+    M = [None] + [disc.sp[l]["M"] for l in range(1, d + 1)]
+    G, Al = [None], [None]
+    for l in range(1, d + 1):
+        (v,) = [t[l - 1] for t in V if np.any(t[l - 1](np.linspace(0, 1, 7)) != 1.0)]
+        W = disc.weighted_space(l, v)
+        W2 = disc.weighted_space(l, lambda x, v=v: v(x) * v(x))
+        G.append(nu * disc.sp[l]["L"] + W["M"])
+        Al.append(nu ** 2 * disc.sp[l]["J"] + W2["M"] - nu * (W["K2"] + W["K2"].T))
+
+    def kron(f):
+        K = f[0]
+        for l in range(1, d + 1):
+            K = np.kron(f[l], K)
+        return K
+    A = kron([disc.Lt] + M[1:])
+    for l in range(1, d + 1):
+        f = [disc.Wsym] + M[1:]
+        f[l] = G[l]
+        A = A + kron(f)
+        f = [disc.Mt] + M[1:]
+        f[l] = Al[l]
+        A = A + kron(f)
+        for k in range(l + 1, d + 1):
+            f = [disc.Mt] + M[1:]
+            f[l], f[k] = G[l], G[k]
+            A = A + 2 * kron(f)
+    return A
+
+
+@pytest.mark.parametrize("n_el,p", [([3, 4, 3], [2, 3]), ([2, 3, 2, 3], [2, 2]), ([4, 5], [3, 2])])
+def test_additive_potential_grouping_equals_bruteforce_quadrature(n_el, p):
+    """For an additive potential the cross terms of the expansion collapse to 2 G_l (x) G_k, because
+    K2 + K2^T = -2 L for spatial functions vanishing on the boundary: the grouped form is A itself."""
+    d = len(n_el) - 1
+    V = [[(lambda x, s=1.5 + r: s * (x - .45) ** 2) if l == r else (lambda x: 1 + 0 * x) for l in range(d)]
+         for r in range(d)]
+    disc = Discretization(n_el, p, T=0.7, nu=1.3, potential=V)
+    Ad = direct.dense_A(disc, _pot_fn(V))
+    assert np.abs(_additive_A(disc, V) - Ad).max() <= 1e-12 * np.abs(Ad).max()
+    for l in range(1, d + 1):
+        K2, L = disc.sp[l]["K2"], disc.sp[l]["L"]
+        assert np.abs(K2 + K2.T + 2 * L).max() <= 1e-13 * np.abs(L).max()
+
+
 @pytest.mark.parametrize("n_el,p,pot", CASES)
 def test_kronecker_A_equals_bruteforce_quadrature(n_el, p, pot):
     d = len(n_el) - 1
