@@ -127,6 +127,10 @@ int stst_assemble_1d(int p, int n_el, double length, int bc, const double *weigh
  * of v_{r,l} at the quadrature points of direction l (stst_quadrature_points).
  * rank = 0 removes the potential. The preconditioner stays the V-free P-hat
  * (Eq. prec_definition). Re-plans the mat-vec; may allocate. rank <= 3.
+ * A factor identically 1 at every quadrature point counts as absent. When each
+ * term r has exactly one factor different from 1 and no two terms share a
+ * direction (V = sum_l v_l(x_l), e.g. a harmonic potential), the mat-vec groups
+ * the operator as i d_t + sum_l H_l and costs as many band applications as V = 0.
  */
 int stst_set_potential(stst_handle h, int rank, const double *v_qp);
 
