@@ -113,3 +113,32 @@ def test_ultraweak_initial_term_with_flipped_sign_is_caught():
     planted = orhs.rhs_ultraweak(disc, f, None) - (orhs.rhs_ultraweak(disc, None, u0))
     assert np.abs(good - ref).max() <= 1e-11 * np.abs(ref).max()
     assert np.abs(planted - ref).max() > 1e-2 * np.abs(ref).max()
+
+
+def _grouped_mismatch(cross=2.0, g_sign=1.0):
+    """The grouped additive-potential form (the mat-vec's Kronecker terms) against brute-force quadrature,
+    with an optional planted mistake: the cross-term factor or the sign of M_v inside G_l."""
+    from tests.test_oracle_pins import _pot_fn
+    d, nu = 2, 1.3
+    V = [[(lambda x: 1.5 * (x - .45) ** 2), (lambda x: 1 + 0 * x)],
+         [(lambda x: 1 + 0 * x), (lambda x: 2.5 * (x - .45) ** 2)]]
+    disc = Discretization([3, 4, 3], [2, 3], T=0.7, nu=nu, potential=V)
+    M = [None] + [disc.sp[l]["M"] for l in (1, 2)]
+    G, Al = [None], [None]
+    for l in (1, 2):
+        v = V[l - 1][l - 1]
+        W = disc.weighted_space(l, v)
+        W2 = disc.weighted_space(l, lambda x, v=v: v(x) * v(x))
+        G.append(nu * disc.sp[l]["L"] + g_sign * W["M"])
+        Al.append(nu ** 2 * disc.sp[l]["J"] + W2["M"] - nu * (W["K2"] + W["K2"].T))
+    k = lambda a, b, c: np.kron(c, np.kron(b, a))
+    A = k(disc.Lt, M[1], M[2]) + k(disc.Wsym, G[1], M[2]) + k(disc.Wsym, M[1], G[2])
+    A = A + k(disc.Mt, Al[1], M[2]) + k(disc.Mt, M[1], Al[2]) + cross * k(disc.Mt, G[1], G[2])
+    Ad = direct.dense_A(disc, _pot_fn(V))
+    return np.abs(A - Ad).max() / np.abs(Ad).max()
+
+
+def test_grouped_potential_form_mistakes_are_caught():
+    assert _grouped_mismatch() < 1e-12
+    assert _grouped_mismatch(cross=1.0) > 1e-3
+    assert _grouped_mismatch(g_sign=-1.0) > 1e-3
