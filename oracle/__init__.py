@@ -15,7 +15,9 @@ Modules, each citing the passage of the paper it restates:
   system    -- Kronecker form of the least-squares matrix A (Eq. syst_mat),
                its separable-potential extension, mode products (Eq. kron_vec_multi)
   direct    -- independent (d+1)-dimensional quadrature of (S B_j, S B_i) (Sec. 4.3)
-  fd        -- the preconditioner P-hat (Eq. prec_definition) and Algorithm 1
+  fd        -- the preconditioner P-hat (Eq. prec_definition) and Algorithm 1; its potential-aware
+               variant P_V for potentials that are sums of one-direction factors (an extension: the
+               construction of Eq. prec_definition applied to i d_t + sum_l (-nu d_ll + v_l))
   pcg       -- preconditioned conjugate gradients (Sec. 5.3, Sec. 6)
   rhs       -- load vector F(S B_i) and liftings of initial / boundary data (Sec. 2.2, Sec. 4.3)
   norms     -- L2 and V-norm errors (Sec. 2.1, Theorem 2)
@@ -28,6 +30,8 @@ the separable-potential terms, whose Kronecker expansion is pinned only by
 brute-force quadrature of the same sesquilinear form (the paper has no
 potential), and the inexact-preconditioner (flexible) CG variant, which the
 paper does not define: parity unpinned beyond the exact-preconditioner case.
+P_V is pinned by its spatial operators against brute-force Galerkin matrices and by Algorithm 1
+against the dense inverse of P_V assembled from its definition; it has no CUDA counterpart yet.
 The warm-start module has no counterpart in the paper; its functions are pinned against finite
 differences, closed forms and the SVD, but whether a trained warm start helps is judged only by PCG
 iterations and final error against the cold start.

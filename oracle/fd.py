@@ -75,3 +75,75 @@ class FastDiagonalization:
     def kappa_U(self, l):
         """kappa_2(U_l) = ||U_l||_2 ||U_l^{-1}||_2 (Table cond_number_space)."""
         return np.linalg.cond(self.U[l], 2)
+
+
+# ------------------------------------------------------------------------------------------------
+# Potential-aware variant (an extension: the paper treats V = 0). For V = sum_l v_l(x_l) the
+# operator is S_V = i d_t + sum_l H_l with H_l = -nu d_ll + v_l; the construction of Eq.
+# prec_definition applied to it replaces the spatial stiffness nu L_s by the Kronecker sum of the
+# Galerkin matrices G_l = nu L_l + M_{v_l} of the H_l:
+#   P_V = M_s (x) L_t + H_s^T M_s^{-1} H_s (x) M_t + H_s (x) (W_t + W_t^*),  H_s = sum_l G_l (Kronecker sum).
+# Algorithm 1 is unchanged with the generalized eigenpairs of (G_l, M_l) and
+# H_i = L_t + lambda_i^2 M_t + lambda_i (W_t + W_t^*) (nu is inside G_l). With V = 0 this is P-hat.
+
+def additive_factors(disc):
+    """v_l for each spatial direction (None where V has no factor there), if the potential is a sum of
+    one-direction factors with at most one per direction; raises ValueError otherwise. A factor counts as
+    absent where it equals 1 at every quadrature point of its direction."""
+    d = disc.d
+    out = [None] * (d + 1)
+    for term in (disc.potential or []):
+        live = [l for l in range(1, d + 1) if not np.all(term[l - 1](disc.quad(l)[0]) == 1.0)]
+        if len(live) != 1 or out[live[0]] is not None:
+            raise ValueError("potential is not a sum of one-direction factors")
+        out[live[0]] = term[live[0] - 1]
+    return out
+
+
+def spatial_operators(disc):
+    """G_l = nu L_l + M_{v_l} (restricted spatial bases), l = 1..d."""
+    v = additive_factors(disc)
+    G = [None]
+    for l in range(1, disc.d + 1):
+        g = disc.nu * disc.sp[l]["L"]
+        if v[l] is not None:
+            g = g + disc.weighted_space(l, v[l])["M"]
+        G.append(g)
+    return G
+
+
+def dense_P_potential(disc):
+    """Assembled P_V (dense; tiny meshes only), straight from its definition above."""
+    G = spatial_operators(disc)
+    Ms = np.ones((1, 1))
+    Hs = np.zeros((1, 1))
+    for l in range(1, disc.d + 1):
+        M = disc.sp[l]["M"]
+        Hs = np.kron(M, Hs) + np.kron(G[l], Ms)
+        Ms = np.kron(M, Ms)
+    HMH = Hs.T @ np.linalg.solve(Ms, Hs)
+    return np.kron(Ms, disc.Lt) + np.kron(HMH, disc.Mt) + np.kron(Hs, disc.Wsym)
+
+
+class PotentialFastDiagonalization(FastDiagonalization):
+    """Algorithm 1 for P_V: eigenpairs of (G_l, M_l) in step 1, H_i without the factor nu in step 3."""
+
+    def __init__(self, disc):
+        self.disc = disc
+        self.U, self.lam = [None], [None]
+        G = spatial_operators(disc)
+        for l in range(1, disc.d + 1):
+            lam, U = scipy.linalg.eigh(G[l], disc.sp[l]["M"])
+            self.U.append(U)
+            self.lam.append(lam)
+        lam_s = np.zeros(disc.shape[:-1])
+        for l in range(1, disc.d + 1):
+            shp = [1] * disc.d
+            shp[disc.d - l] = disc.n[l]
+            lam_s = lam_s + self.lam[l].reshape(shp)
+        self.lam_s = lam_s.ravel()
+
+    def H(self, lam_i):
+        """H_i = L_t + lambda_i^2 M_t + lambda_i (W_t + W_t^*)."""
+        disc = self.disc
+        return disc.Lt + lam_i ** 2 * disc.Mt + lam_i * disc.Wsym
