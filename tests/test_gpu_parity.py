@@ -25,6 +25,9 @@ CASES = [
     ([5, 6, 5, 7], [2, 2, 3, 2], None),
     ([5, 6, 5, 4], [3, 2, 2, 2], "bump"),
     ([3, 1], [1, 2], None),
+    # harmonic potentials in 1D+t and 3D+t: the mat-vec's grouped form for sums of one-direction factors
+    ([6, 9], [2, 3], "harmonic"),
+    ([5, 6, 5, 4], [2, 2, 3, 2], "harmonic"),
 ]
 
 
