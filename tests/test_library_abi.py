@@ -39,3 +39,45 @@ def test_binding_names_match_header():
     import paper_2311_18461_gb300 as P
     for n in _declared():
         assert hasattr(P, n), n
+
+
+@pytest.mark.skipif(shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"),
+                    reason="CUDA toolkit absent")
+def test_host_side_argument_checks_need_no_gpu():
+    """The calls that reject arguments before any CUDA call return the documented status codes; the
+    process-wide tuning switches are restored to their defaults (autotune 1, time solver 0, fused 0)."""
+    from paper_2311_18461_gb300 import build
+    L = ctypes.CDLL(build.build())
+    ERR_ARG, ERR_HANDLE = -1, -2
+    try:
+        for mode in (0, 1, 132, 12, 14, 22, 44):
+            assert L.stst_set_autotune(mode) == 0, mode
+        for mode in (-1, 2, 15, 52, 99, 131):
+            assert L.stst_set_autotune(mode) == ERR_ARG, mode
+        for mode in (0, 1, 2, 11, 14):
+            assert L.stst_set_fused_transforms(mode) == 0, mode
+        for mode in (-1, 3, 10, 15):
+            assert L.stst_set_fused_transforms(mode) == ERR_ARG, mode
+        for mode in (0, 1, 2):
+            assert L.stst_set_time_solver(mode) == 0, mode
+        for mode in (-1, 3):
+            assert L.stst_set_time_solver(mode) == ERR_ARG, mode
+    finally:
+        L.stst_set_autotune(1)
+        L.stst_set_time_solver(0)
+        L.stst_set_fused_transforms(0)
+    n = ctypes.c_longlong()
+    assert L.stst_sizes(None, ctypes.byref(n), None) == ERR_HANDLE
+    assert L.stst_pcg_graph_info(None, None, None) == ERR_HANDLE
+    assert L.stst_build_fd(None) == ERR_HANDLE
+    assert L.stst_set_potential(None, 0, None) == ERR_HANDLE
+    out = ctypes.c_int()
+    bad = [(0, 4, 1.0, 2), (9, 4, 1.0, 2), (2, 0, 1.0, 2), (2, 4, 0.0, 2), (2, 4, -1.0, 1), (2, 4, 1.0, 3),
+           (1, 1, 1.0, 2)]  # the last leaves no function after dropping both ends
+    for p, n_el, length, bc in bad:
+        assert L.stst_assemble_1d(p, n_el, ctypes.c_double(length), bc, None, None, None, None, None, None,
+                                  ctypes.byref(out), None) == ERR_ARG, (p, n_el, length, bc)
+    L.stst_strerror.restype = ctypes.c_char_p
+    texts = {s: L.stst_strerror(s).decode() for s in (0, 1, 2, 3, 4, -1, -2, -3, -4, -5)}
+    assert len(set(texts.values())) == len(texts) and "unknown" not in " ".join(texts.values())
+    assert L.stst_strerror(77).decode() == "unknown status"
