@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--config", default="c2")
     ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "bf16"])
     ap.add_argument("--solver", default="pcg", choices=["pcg", "ir"])
+    ap.add_argument("--prec-op", default="phat", choices=["phat", "potential"],
+                    help="preconditioner operator: the paper's P-hat, or P_V built from the potential's "
+                         "one-direction operators (sums of one-direction factors only)")
     ap.add_argument("--autotune", type=int, default=1,
                     help="mode-product tiles: 1 measured per shape, 0 default, 10 rpt + cpt forced (stst_set_autotune)")
     ap.add_argument("--tw-p", type=int, default=3, help="degree of the travelling-wave workload (--config tw)")
@@ -205,7 +208,7 @@ def sample_1d(prob, fn, l):
     return np.asarray(fn(x)) * np.ones_like(x)
 
 
-def build_problem(cfg, V, u0, prec, stream, formulation="ls"):
+def build_problem(cfg, V, u0, prec, stream, formulation="ls", prec_op="phat"):
     import numpy as np
     import torch
     import paper_2311_18461_gb300 as S
@@ -216,6 +219,8 @@ def build_problem(cfg, V, u0, prec, stream, formulation="ls"):
     if V:
         cols = [sample_1d(prob, term[l - 1], l) for term in V for l in range(1, d + 1)]
         prob.set_potential(torch.tensor(np.concatenate(cols), dtype=torch.float64, device="cuda"), len(V))
+    if prec_op == "potential":
+        S.stst_set_prec_operator(prob.h, 1)
     if u0 is None:  # the travelling wave
         return prob, tw_rhs(prob)
     grids = [prob.quad_points(l).cpu().numpy() for l in range(1, d + 1)]
@@ -538,7 +543,7 @@ def run_ours(args):
     cfg, V, u0 = workload(args.config)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        prob, b = build_problem(cfg, V, u0, args.prec, stream, args.formulation)
+        prob, b = build_problem(cfg, V, u0, args.prec, stream, args.formulation, args.prec_op)
     tol = cfg.get("tol", 1e-8)
     x = prob.vec()
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > 129 MB L2
@@ -724,7 +729,8 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": workload_name(args.config, cfg, tol) + (", ultraweak formulation (Sec. 4.4)"
                                                                        if args.formulation == "uw" else ""),
-                   "n_dof": n_dof, "preconditioner": args.prec, "solver": args.solver,
+                   "n_dof": n_dof, "preconditioner": args.prec + (" P_V (potential-aware)" if args.prec_op == "potential"
+                                                                  else " P-hat"), "solver": args.solver,
                    "pcg_iterations": statistics.median(iters),
                    "step": "build_fd (setup) + pcg_solve from x0 = 0", "l2": "flushed (512 MB write) before each step",
                    "parallelism": f"replicas x{world}"},

@@ -135,6 +135,20 @@ int stst_assemble_1d(int p, int n_el, double length, int bc, const double *weigh
 int stst_set_potential(stst_handle h, int rank, const double *v_qp);
 
 /*
+ * stst_set_prec_operator: the spatial operator the preconditioner is built from (an extension).
+ *   0  the paper's P-hat (Eq. prec_definition): the potential-free stiffness nu L_l (default);
+ *   1  P_V: for a potential that is a sum of one-direction factors (see stst_set_potential), the
+ *      Galerkin matrices G_l = nu L_l + M_{v_l} of H_l = -nu d_ll + v_l in place of nu L_l. Algorithm 1
+ *      is unchanged with the eigenpairs of (G_l, M_l) and H_i = L_t + lambda_i^2 M_t + lambda_i (W_t + W_t^*).
+ *      With V = 0 it is P-hat.
+ * ERR_ARG for another op, or for 1 while the potential is not such a sum. A change takes effect at the
+ * next stst_build_fd (apply_prec and the solves return ERR_STATE until then). With 1 selected,
+ * stst_set_potential invalidates the preconditioner as well (P_V depends on V), and stst_build_fd
+ * returns ERR_STATE if the potential it installed is not such a sum.
+ */
+int stst_set_prec_operator(stst_handle h, int op);
+
+/*
  * stst_build_fd: preconditioner setup, step 1 of Algorithm 1 plus the
  * per-eigenvalue time operators H_i = L_t + nu^2 lambda_i^2 M_t + nu lambda_i (W_t + W_t^*)
  * (Sec. 5.2). Generalized eigenpairs of (L_l, M_l) with U_l^T M_l U_l = I

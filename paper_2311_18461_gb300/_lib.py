@@ -60,6 +60,7 @@ def lib():
             "stst_batch_destroy": [P],
             "stst_plan_info": [P, IP, IP, DP],
             "stst_pcg_graph_info": [P, IP, IP],
+            "stst_set_prec_operator": [P, I],
             "stst_profile_read": [P, I, ctypes.c_char_p, I, ctypes.POINTER(LL), DP],
             "stst_set_autotune": [I],
             "stst_set_time_solver": [I],
@@ -252,6 +253,10 @@ def stst_plan_info(h):
     f = ctypes.c_double()
     _chk(lib().stst_plan_info(h, ctypes.byref(n), ctypes.byref(a), ctypes.byref(f)), "stst_plan_info")
     return n.value, a.value, f.value
+
+
+def stst_set_prec_operator(h, op):
+    return _chk(lib().stst_set_prec_operator(h, int(op)), "stst_set_prec_operator")
 
 
 def stst_pcg_graph_info(h):

@@ -681,6 +681,9 @@ static int additive_terms(stst_problem *h, int rank, const int *dir_of, const in
     if (r < 0) {
       gm[l] = SM_L, gc[l] = nu;
       am[l] = SM_J, ac[l] = nu * nu;
+      const int g = add_combo(h, l, SM_L, nu, SM_M, 0.0);  // nu L_l as a matrix of its own for the FD setup
+      if (g < 0) return g;
+      h->g_mat[l] = g;
       continue;
     }
     const int g = add_combo(h, l, SM_L, nu, wm[l][r], 1.0);
@@ -691,7 +694,9 @@ static int additive_terms(stst_problem *h, int rank, const int *dir_of, const in
     if (a < 0) return a;
     gm[l] = g, gc[l] = 1.0;
     am[l] = a, ac[l] = 1.0;
+    h->g_mat[l] = g;
   }
+  h->g_valid = 1;
   auto mk = [&](double c, int tm) {
     Term t;
     t.coef = c;
@@ -736,6 +741,8 @@ int stst_set_potential(stst_handle h, int rank, const double *v_qp) {
   for (double *p : h->pot_bufs) cudaFree(p);
   h->pot_bufs.clear();
   h->pot_rank = 0;
+  h->g_valid = 0;
+  if (h->prec_op == 1) h->fd_ready = 0;  // the potential-aware factors depend on V
   std::vector<Term> terms = base_terms(h);
   if (rank > 0) {
     int stride = 0;
@@ -844,6 +851,7 @@ int stst_set_potential(stst_handle h, int rank, const double *v_qp) {
 int stst_build_fd(stst_handle h) {
   STST_TRY(check(h));
   ApiScope scope(h);
+  if (h->prec_op == 1 && h->pot_rank > 0 && !h->g_valid) return STST_ERR_STATE;  // P_V needs a sum of one-direction factors
   STST_TRY(fd_setup(h));
   return tune_modeprod(h);
 }
@@ -955,6 +963,15 @@ int stst_profile(stst_handle h, int enable) {
     h->prof->count.clear();
   }
   h->prof_on = enable ? 1 : 0;
+  return STST_OK;
+}
+
+int stst_set_prec_operator(stst_handle h, int op) {
+  STST_TRY(check(h));
+  if (op != 0 && op != 1) return STST_ERR_ARG;
+  if (op == 1 && h->pot_rank > 0 && !h->g_valid) return STST_ERR_ARG;
+  if (op != h->prec_op) h->fd_ready = 0;
+  h->prec_op = op;
   return STST_OK;
 }
 

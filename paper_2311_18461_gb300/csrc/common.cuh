@@ -118,6 +118,11 @@ struct stst_problem {
 
   // potential
   int pot_rank;
+  // potential-aware preconditioner: G_l = nu L_l + M_{v_l} (band ids in mats[l]), recorded by
+  // stst_set_potential for sums of one-direction factors; prec_op 1 builds the FD from them
+  int g_valid;
+  int g_mat[STST_MAXD + 1];
+  int prec_op;
   std::vector<double *> pot_bufs;  // device buffers of weights (owned)
 
   // FD

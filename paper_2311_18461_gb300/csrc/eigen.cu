@@ -757,14 +757,16 @@ int fd_setup_launch(stst_problem *h) {
   cudaStream_t st = h->stream;
   const int d = h->d;
   STST_CUDA(cudaMemsetAsync(h->flags, 0, sizeof(int) * 4, st));
+  // potential-aware operator: eigenpairs of (G_l, M_l), G_l = nu L_l + M_{v_l}; nu is inside G_l
+  const bool pv = h->prec_op == 1 && h->pot_rank > 0 && h->g_valid;
   for (int l = 1; l <= d; ++l) {
-    int src = l;  // directions with the same degree and mesh share one eigendecomposition
-    for (int k = 1; k < l; ++k)
+    int src = l;  // directions with the same degree and mesh share one eigendecomposition (P-hat only)
+    for (int k = 1; k < l && !pv; ++k)
       if (h->dir[k].p == h->dir[l].p && h->dir[k].n_el == h->dir[l].n_el) { src = k; break; }
     h->eig_src[l] = src;
     if (src != l) continue;
     const int n = h->dir[l].n, p = h->dir[l].p;
-    const BandMat &M = h->mats[l][0], &L = h->mats[l][1];
+    const BandMat &M = h->mats[l][0], &L = pv ? h->mats[l][h->g_mat[l]] : h->mats[l][1];
     const size_t sm = (2 * (size_t)n * (n + 1) + (size_t)n * (p + 1) + 5 * (size_t)n + 2 * (size_t)n * (2 * p + 1)) *
                       sizeof(float);
     float *scratch = (float *)h->oa_work;  // the refinement's 6 n_max^2 doubles hold EigScratch
@@ -813,6 +815,7 @@ int fd_setup_launch(stst_problem *h) {
   const double *l1 = h->lam[1], *l2 = d >= 2 ? h->lam[2] : nullptr, *l3 = d >= 3 ? h->lam[3] : nullptr;
   int grid = grid_for(h->N_s, 64);
   const bool f64 = h->prec_mode == STST_PREC_FP64;
+  const double nu_h = pv ? 1.0 : h->nu;
   size_t hsm = 3 * (size_t)h->n_t() * (2 * h->dir[0].p + 1) * (f64 ? sizeof(double) : sizeof(float));
   const int stage = hsm <= 48 * 1024;  // otherwise the bands are read from global memory
   if (!stage) hsm = 0;
@@ -822,11 +825,11 @@ int fd_setup_launch(stst_problem *h) {
 #define CASE(PP)                                                                                                 \
   case PP:                                                                                                       \
     if (f64)                                                                                                     \
-      k_hfactor<double, PP><<<grid, 64, hsm, st>>>(Lt.d, Mt.d, KAt.d, h->n_t(), h->nu, d, l1, l2, l3, n1, n2,     \
+      k_hfactor<double, PP><<<grid, 64, hsm, st>>>(Lt.d, Mt.d, KAt.d, h->n_t(), nu_h, d, l1, l2, l3, n1, n2,     \
                                                  h->N_s, (double2 *)h->Hg, h->Hd, (float2 *)h->Hg32, h->Hd32,    \
                                                  h->flags, stage);                                                      \
     else                                                                                                         \
-      k_hfactor<float, PP><<<grid, 64, hsm, st>>>(Lt32, Mt32, KAt32, h->n_t(), h->nu, d, l1, l2, l3, n1, n2,      \
+      k_hfactor<float, PP><<<grid, 64, hsm, st>>>(Lt32, Mt32, KAt32, h->n_t(), nu_h, d, l1, l2, l3, n1, n2,      \
                                                 h->N_s, nullptr, nullptr, (float2 *)h->Hg32, h->Hd32, h->flags,  \
                                                 stage);                                                         \
     break;
