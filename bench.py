@@ -761,7 +761,7 @@ def run_ours(args):
                            "seconds": 4.7142, "iterations": 8}),
     }
     if rank == 0 and world == 1 and args.cpu_baseline == "on":
-        cb = cpu_baseline(args.config, iters_full=None, formulation=args.formulation)
+        cb = cpu_baseline(args.config, iters_full=None, formulation=args.formulation, prec_op=args.prec_op)
         x_ref = cb.pop("_x_ref", None)
         out["cpu_baseline"] = cb
         if x_ref is not None:
@@ -808,20 +808,22 @@ def oracle_problem(cfg_name, formulation="ls"):
     return cfg, disc, b
 
 
-def cpu_baseline(cfg_name, iters_full=None, sample_iters=2, formulation="ls"):
-    """The oracle timed on this host: setup + `sample_iters` PCG iterations, extrapolated to the full count."""
+def cpu_baseline(cfg_name, iters_full=None, sample_iters=2, formulation="ls", prec_op="phat"):
+    """The oracle timed on this host: setup + `sample_iters` PCG iterations, extrapolated to the full count.
+    prec_op "potential": the oracle's potential-aware preconditioner P_V in place of P-hat."""
     from oracle import fd, pcg
     cfg, disc, b = oracle_problem(cfg_name, formulation)
+    FD = fd.PotentialFastDiagonalization if prec_op == "potential" else fd.FastDiagonalization
     terms = disc.terms()
     x_ref = None
     if iters_full is None:
         # one untimed full solve, to 1e-12: its residual history gives the iteration count at 1e-8,
         # its solution is the FP64 reference the GPU result is compared with
-        F = fd.FastDiagonalization(disc)
+        F = FD(disc)
         x_ref, _, _, hist = pcg.pcg(disc.apply, F.apply, b, tol=1e-12, maxit=400)
         iters_full = next(i for i, h in enumerate(hist) if h <= cfg.get("tol", 1e-8))
     t0 = time.perf_counter()
-    F = fd.FastDiagonalization(disc)
+    F = FD(disc)
     t1 = time.perf_counter()
     pcg.pcg(disc.apply, F.apply, b, tol=0.0, maxit=sample_iters)
     t2 = time.perf_counter()
@@ -848,11 +850,11 @@ def run_reference(args):
                           "(c1, c2, c3*, c5, tw); c4's 128 problems have no bounded oracle sample"}), flush=True)
         return
     cfg, disc, b = oracle_problem(args.config, formulation)
-    F = fd.FastDiagonalization(disc)
+    F = (fd.PotentialFastDiagonalization if args.prec_op == "potential" else fd.FastDiagonalization)(disc)
     _, iters_full, _, _ = pcg.pcg(disc.apply, F.apply, b, tol=cfg.get("tol", 1e-8), maxit=200)
     vals = []
     for k in range(args.warmup + args.steps):
-        r = cpu_baseline(args.config, iters_full=iters_full, formulation=formulation)
+        r = cpu_baseline(args.config, iters_full=iters_full, formulation=formulation, prec_op=args.prec_op)
         if k >= args.warmup:
             vals.append(r["value"])
     v = statistics.mean(vals)
@@ -861,7 +863,10 @@ def run_reference(args):
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": workload_name(args.config, cfg, cfg.get("tol", 1e-8))
                                   + (", ultraweak formulation (Sec. 4.4)" if formulation == "uw" else ""),
-                      "n_dof": disc.N_dof, "preconditioner": "fp64 (oracle)", "solver": "pcg",
+                      "n_dof": disc.N_dof, "preconditioner": "fp64 (oracle) " + ("P_V (potential-aware)"
+                                                                                if args.prec_op == "potential"
+                                                                                else "P-hat"),
+                      "solver": "pcg",
                       "pcg_iterations": iters_full, "step": "build_fd (setup) + pcg_solve from x0 = 0",
                       "parallelism": "oracle on the host cores, rank 0"},
            "cpu_baseline": {"value": v, "unit": "s", "cores": r["cores"], "kind": "oracle", "sample": r["sample"]},
