@@ -814,6 +814,28 @@ int stst_set_potential(stst_handle h, int rank, const double *v_qp) {
     }
     if (additive) {
       STST_TRY(additive_terms(h, rank, dir_of, wm, wk, pm, terms));
+      // directions whose G_l are equal (same degree and mesh, no factor in either or bitwise equal factor
+      // samples) share one eigendecomposition in the potential-aware setup
+      int offs[STST_MAXD + 2] = {0};
+      for (int l = 1; l <= d; ++l) offs[l + 1] = offs[l] + h->dir[l].Q();
+      for (int l = 1; l <= d; ++l) {
+        h->g_share[l] = l;
+        int rl = -1;
+        for (int q = 0; q < rank; ++q)
+          if (dir_of[q] == l) rl = q;
+        for (int k = 1; k < l && h->g_share[l] == l; ++k) {
+          if (h->dir[k].p != h->dir[l].p || h->dir[k].n_el != h->dir[l].n_el) continue;
+          int rk = -1;
+          for (int q = 0; q < rank; ++q)
+            if (dir_of[q] == k) rk = q;
+          if ((rk < 0) != (rl < 0)) continue;
+          const size_t Q = (size_t)h->dir[l].Q();
+          if (rl >= 0 && memcmp(host.data() + (size_t)rk * stride + offs[k], host.data() + (size_t)rl * stride + offs[l],
+                                sizeof(double) * Q) != 0)
+            continue;
+          h->g_share[l] = h->g_share[k];
+        }
+      }
       h->pot_rank = rank;
       STST_TRY(replan(h, terms));
       STST_CUDA(cudaStreamSynchronize(st));

@@ -122,6 +122,7 @@ struct stst_problem {
   // stst_set_potential for sums of one-direction factors; prec_op 1 builds the FD from them
   int g_valid;
   int g_mat[STST_MAXD + 1];
+  int g_share[STST_MAXD + 1];  // direction whose eigendecomposition of (G_l, M_l) this one reuses (itself if none)
   int prec_op;
   std::vector<double *> pot_bufs;  // device buffers of weights (owned)
 

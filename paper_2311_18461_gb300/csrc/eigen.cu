@@ -760,7 +760,8 @@ int fd_setup_launch(stst_problem *h) {
   // potential-aware operator: eigenpairs of (G_l, M_l), G_l = nu L_l + M_{v_l}; nu is inside G_l
   const bool pv = h->prec_op == 1 && h->pot_rank > 0 && h->g_valid;
   for (int l = 1; l <= d; ++l) {
-    int src = l;  // directions with the same degree and mesh share one eigendecomposition (P-hat only)
+    // directions with the same degree and mesh share one eigendecomposition (P_V: and the same G_l)
+    int src = pv ? h->g_share[l] : l;
     for (int k = 1; k < l && !pv; ++k)
       if (h->dir[k].p == h->dir[l].p && h->dir[k].n_el == h->dir[l].n_el) { src = k; break; }
     h->eig_src[l] = src;
