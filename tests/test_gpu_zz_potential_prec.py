@@ -40,6 +40,21 @@ def test_apply_prec_potential_fp64(n_el, p):
     prob.close()
 
 
+@pytest.mark.parametrize("same", [True, False])
+def test_apply_prec_potential_equal_meshes(same):
+    """Equal meshes in both directions: with the same factor the two G_l are equal and share one
+    eigendecomposition; with different factors they must not."""
+    f1 = lambda x: 6.0 * (x - 0.5) ** 2
+    f2 = f1 if same else (lambda x: 3.0 + 4.0 * x)
+    one = lambda x: 1.0 + 0.0 * x
+    prob, disc = _problem([8, 10, 10], [2, 3, 3], V=[[f1, one], [one, f2]])
+    assert prob.build_fd() == 0
+    r = random_complex(prob.n_dof, 34)
+    s = to_np(prob.apply_prec(to_dev(r)))
+    assert rel_err(s, ofd.PotentialFastDiagonalization(disc).apply(r)) < 1e-10
+    prob.close()
+
+
 def test_apply_prec_potential_fp32():
     prob, disc = _problem([9, 11, 7], [2, 3, 2], prec=S.STST_PREC_FP32)
     assert prob.build_fd() == 0
