@@ -661,7 +661,8 @@ int stst_assemble_1d(int p, int n_el, double length, int bc, const double *weigh
 }
 
 // Additive potential V = sum_l v_l(x_l) (each factor differs from 1 in one direction only, one factor per
-// direction): the operator is i d_t + sum_l H_l with H_l = -nu d_ll + v_l, so the least-squares matrix is
+// direction): the operator is i d_t + sum_l H_l with H_l = -nu d_ll + v_l, so the least-squares matrix
+// (Sec. 4.3, Eq. syst_mat with the potential's terms) is
 //   L_t (x) M..M + sum_l KA (x) G_l + sum_l M_t (x) A_l + 2 sum_{l<k} M_t (x) G_l (x) G_k
 // (each G_l / A_l at position l, M elsewhere), G_l = nu L_l + M_{v_l} (the Galerkin matrix of H_l) and
 // A_l = nu^2 J_l + M_{v_l^2} - nu (K2_{v_l} + K2_{v_l}^T). The cross terms 2 nu^2 L (x) L + 2 M_v (x) M_v
