@@ -31,7 +31,8 @@ brute-force quadrature of the same sesquilinear form (the paper has no
 potential), and the inexact-preconditioner (flexible) CG variant, which the
 paper does not define: parity unpinned beyond the exact-preconditioner case.
 P_V is pinned by its spatial operators against brute-force Galerkin matrices and by Algorithm 1
-against the dense inverse of P_V assembled from its definition; it has no CUDA counterpart yet.
+against the dense inverse of P_V assembled from its definition; its ANOVA approximation for products of
+factors by closed-form means and by its equality with P_V for additive potentials.
 The warm-start module has no counterpart in the paper; its functions are pinned against finite
 differences, closed forms and the SVD, but whether a trained warm start helps is judged only by PCG
 iterations and final error against the cold start.

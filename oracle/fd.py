@@ -100,8 +100,35 @@ def additive_factors(disc):
     return out
 
 
-def spatial_operators(disc):
-    """G_l = nu L_l + M_{v_l} (restricted spatial bases), l = 1..d."""
+def anova_factors(disc):
+    """First-order ANOVA terms of a separable V = sum_r prod_l f_{r,l}(x_l) on the unit cube:
+    g_l(x_l) = E[V | x_l] - ((d-1)/d) E[V] = sum_r f_{r,l}(x_l) prod_{k != l} mu_{r,k} - ((d-1)/d) sum_r prod_k mu_{r,k},
+    mu_{r,k} the mean of f_{r,k} over (0,1) (direction k's Gauss rule). sum_l g_l is the L2-best additive
+    approximation of V; for an additive V it is V itself."""
+    d = disc.d
+    V = disc.potential or []
+    mu = []
+    for term in V:
+        row = []
+        for k in range(1, d + 1):
+            x, w = disc.quad(k)
+            row.append(float(np.sum(w * term[k - 1](x))))
+        mu.append(row)
+    V0 = sum(np.prod(row) for row in mu)
+    out = [None]
+    for l in range(1, d + 1):
+        coefs = [np.prod([mu[r][k - 1] for k in range(1, d + 1) if k != l]) for r in range(len(V))]
+        out.append(lambda x, l=l, coefs=coefs: sum(c * V[r][l - 1](x) for r, c in enumerate(coefs))
+                   - (d - 1) / d * V0 + 0.0 * np.asarray(x))
+    return out
+
+
+def spatial_operators(disc, approximate=False):
+    """G_l = nu L_l + M_{v_l} (restricted spatial bases), l = 1..d. approximate=True takes the ANOVA terms
+    g_l in place of the v_l, for any separable potential."""
+    if approximate:
+        g = anova_factors(disc)
+        return [None] + [disc.nu * disc.sp[l]["L"] + disc.weighted_space(l, g[l])["M"] for l in range(1, disc.d + 1)]
     v = additive_factors(disc)
     G = [None]
     for l in range(1, disc.d + 1):
@@ -112,9 +139,9 @@ def spatial_operators(disc):
     return G
 
 
-def dense_P_potential(disc):
+def dense_P_potential(disc, approximate=False):
     """Assembled P_V (dense; tiny meshes only), straight from its definition above."""
-    G = spatial_operators(disc)
+    G = spatial_operators(disc, approximate)
     Ms = np.ones((1, 1))
     Hs = np.zeros((1, 1))
     for l in range(1, disc.d + 1):
@@ -128,10 +155,10 @@ def dense_P_potential(disc):
 class PotentialFastDiagonalization(FastDiagonalization):
     """Algorithm 1 for P_V: eigenpairs of (G_l, M_l) in step 1, H_i without the factor nu in step 3."""
 
-    def __init__(self, disc):
+    def __init__(self, disc, approximate=False):
         self.disc = disc
         self.U, self.lam = [None], [None]
-        G = spatial_operators(disc)
+        G = spatial_operators(disc, approximate)
         for l in range(1, disc.d + 1):
             lam, U = scipy.linalg.eigh(G[l], disc.sp[l]["M"])
             self.U.append(U)

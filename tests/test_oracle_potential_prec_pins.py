@@ -103,3 +103,52 @@ def test_fewer_iterations_than_p_hat_on_the_harmonic_workload_family():
     x1, it1, _, _ = pcg.pcg(disc.apply, fd.PotentialFastDiagonalization(disc).apply, b, tol=1e-8, maxit=200)
     assert (it0, it1) == (11, 8)
     assert np.linalg.norm(x1 - x0) <= 1e-6 * np.linalg.norm(x0)
+
+
+# ---- the ANOVA approximation for products of factors (approximate=True) ------------------------------
+
+def test_anova_form_equals_the_exact_one_for_an_additive_potential():
+    """The ANOVA terms of V = sum_l v_l are v_l plus constants summing to zero: the Kronecker sum H_s, hence P_V,
+    is unchanged."""
+    disc = Discretization([3, 4, 3, 2], [2, 2], T=0.8, nu=1.2, potential=_additive(3))
+    P = fd.dense_P_potential(disc)
+    assert np.abs(fd.dense_P_potential(disc, approximate=True) - P).max() <= 1e-12 * np.abs(P).max()
+
+
+def test_anova_terms_of_a_polynomial_product_match_closed_form_means():
+    """V = (1 + x1)(2 - x2^2): means 3/2 and 5/3, E[V] = 5/2, g_1 = (5/3)(1 + x) - 5/4, g_2 = (3/2)(2 - x^2) - 5/4."""
+    V = [[(lambda x: 1.0 + x), (lambda x: 2.0 - x ** 2)]]
+    disc = Discretization([3, 4, 5], [2, 3], nu=0.9, potential=V)
+    G = fd.spatial_operators(disc, approximate=True)
+    g = [None, lambda x: 5.0 / 3.0 * (1.0 + x) - 1.25, lambda x: 1.5 * (2.0 - x ** 2) - 1.25]
+    for l in (1, 2):
+        ref = 0.9 * disc.sp[l]["L"] + disc.weighted_space(l, g[l])["M"]
+        assert np.abs(G[l] - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("n_el,p", [([4, 5, 4], [2, 3]), ([2, 3, 2, 3], [2, 2])])
+def test_anova_fd_equals_dense_inverse_for_a_product_potential(n_el, p):
+    d = len(n_el) - 1
+    bump = [[(lambda x: 2.0 * np.exp(-(x - .5) ** 2 / .05)) for _ in range(d)]]
+    disc = Discretization(n_el, p, T=0.9, nu=1.1, potential=bump)
+    P = fd.dense_P_potential(disc, approximate=True)
+    assert np.linalg.eigvalsh(P).min() > 0
+    r = np.random.default_rng(5).standard_normal(disc.N_dof) * (1 + 0.3j)
+    ref = np.linalg.solve(P, r)
+    got = fd.PotentialFastDiagonalization(disc, approximate=True).apply(r)
+    assert np.abs(got - ref).max() <= 1e-11 * np.abs(ref).max()
+
+
+def test_anova_preconditioner_on_the_bump_workload_family():
+    """3D+t p = 2, Gaussian bump, wavepacket datum at 16 x 8^3 elements: PCG to 1e-8 with the ANOVA P_V takes
+    8 iterations where P-hat takes 9 (16 x 16^3: 11 against 14; 48 x 24^3: 11 against 16)."""
+    from inputs import CONFIGS, potential, initial_factors, product_fn
+    from oracle import pcg, rhs
+    cfg = dict(CONFIGS["c3p2_bump"])
+    cfg["n_el"] = [16, 8, 8, 8]
+    disc = Discretization(cfg["n_el"], [cfg["p"]] * 4, T=cfg["T"], nu=cfg["nu"], potential=potential(cfg))
+    b, _ = rhs.rhs_initial(disc, None, product_fn(initial_factors(cfg)))
+    _, it0, _, _ = pcg.pcg(disc.apply, fd.FastDiagonalization(disc).apply, b, tol=1e-8, maxit=200)
+    _, it1, _, _ = pcg.pcg(disc.apply, fd.PotentialFastDiagonalization(disc, approximate=True).apply, b, tol=1e-8,
+                           maxit=200)
+    assert (it0, it1) == (9, 8)
