@@ -431,6 +431,10 @@ class Problem:
     def set_potential(self, v_qp, rank):
         return stst_set_potential(self.h, rank, v_qp)
 
+    def set_prec_operator(self, op):
+        """0: the paper's P-hat; 1: the potential-aware P_V (rebuild with build_fd)."""
+        return stst_set_prec_operator(self.h, op)
+
     def build_fd(self):
         return stst_build_fd(self.h)
 
