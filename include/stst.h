@@ -127,6 +127,12 @@ int stst_assemble_1d(int p, int n_el, double length, int bc, const double *weigh
  * of v_{r,l} at the quadrature points of direction l (stst_quadrature_points).
  * rank = 0 removes the potential. The preconditioner stays the V-free P-hat
  * (Eq. prec_definition). Re-plans the mat-vec; may allocate. rank <= 3.
+ * Errors: STST_ERR_ARG (bad rank, NULL samples, or a sample that is not finite:
+ * the handle keeps its previous potential); STST_ERR_OOM / STST_ERR_CUDA part-way:
+ * the potential is removed (V = 0), and if even that operator cannot be planned,
+ * every call that applies the matrix returns STST_ERR_STATE until a later
+ * stst_set_potential succeeds. Batches (stst_batch_create) captured the previous
+ * operator: destroy and re-create them after changing the potential.
  * A factor identically 1 at every quadrature point counts as absent. When each
  * term r has exactly one factor different from 1 and no two terms share a
  * direction (V = sum_l v_l(x_l), e.g. a harmonic potential), the mat-vec groups
@@ -214,9 +220,13 @@ int stst_rhs_lift(stst_handle h, const double *f_qp, const double *u_qp, double 
  * (2^20 complex128 values) built into the library: every GPU that loads the
  * library holds it until the process exits. The first call on a device looks
  * up the array's device address (with that device current); make that first
- * call before any stream capture. The forcing path needs 4 n_t prod_l Q_l
- * complex values of it (5 with a potential, Q_l = n_el[l]*(p[l]+2)); larger
- * problems return STST_ERR_ARG and do nothing. The initial-datum path uses the
+ * call before any stream capture. The lookup is repeated when the device's
+ * context has changed (after cudaDeviceReset the module is loaded again): the
+ * first call in a new context is again a set-up call. The forcing path needs
+ * 3 n_t prod_l Q_l complex values of it for the ultraweak load, 4 for the
+ * least-squares load and 5 for the least-squares load with a potential
+ * (Q_l = n_el[l]*(p[l]+2)); larger problems return STST_ERR_ARG and do nothing.
+ * The initial-datum path uses the
  * handle's own workspaces. All calls share the array: calls whose work may
  * overlap on the GPU (other streams, other host threads, other handles on the
  * same device) race on it and must be serialized by the caller. Nothing in it

@@ -13,6 +13,7 @@ library_path = os.path.join(HERE, "libstst.so")
 STST_PREC_FP64, STST_PREC_FP32, STST_PREC_BF16 = 0, 1, 2
 STST_FORM_LS, STST_FORM_UW = 0, 1
 STST_OK, STST_NOT_CONVERGED, STST_BREAKDOWN, STST_NOT_HPD, STST_TIMEOUT = 0, 1, 2, 3, 4
+STST_ERR_ARG, STST_ERR_HANDLE, STST_ERR_OOM, STST_ERR_CUDA, STST_ERR_STATE = -1, -2, -3, -4, -5
 STATUS = {0: "OK", 1: "NOT_CONVERGED", 2: "BREAKDOWN", 3: "NOT_HPD", 4: "TIMEOUT", -1: "ERR_ARG",
           -2: "ERR_HANDLE", -3: "ERR_OOM", -4: "ERR_CUDA", -5: "ERR_STATE"}
 

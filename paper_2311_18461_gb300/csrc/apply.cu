@@ -157,6 +157,7 @@ int run_plan(const Plan &plan, const void *x, void *y, int precision, int epi, c
              double *dot_partials, const int *done, cudaStream_t s, const void *dot2vec, double *dot2_partials) {
   (void)dot2vec;
   const int np = (int)plan.passes.size();
+  if (np == 0) return STST_ERR_STATE;  // dropped by a failed re-plan (see stst_set_potential)
   for (int ip = 0; ip < np; ++ip) {
     const PassParams &pp = plan.passes[ip];
     PassK k;

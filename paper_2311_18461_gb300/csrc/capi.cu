@@ -50,10 +50,15 @@ int add_band(stst_problem *h, int l, int kind, const double *weight) {
   B.n = D.n;
   B.p = D.p;
   STST_TRY(alloc((void **)&B.d, sizeof(double) * B.n * (2 * B.p + 1)));
-  STST_TRY(launch_assemble_band(kind, D.p, D.n_el, D.len, D.nq, D.off, D.n, D.n, weight, B.d, h->stream));
-  float *f32;
-  STST_TRY(alloc((void **)&f32, sizeof(float) * B.n * (2 * B.p + 1)));
-  STST_TRY(launch_to_f32(B.d, f32, (long long)B.n * (2 * B.p + 1), h->stream));
+  float *f32 = nullptr;
+  int s = launch_assemble_band(kind, D.p, D.n_el, D.len, D.nq, D.off, D.n, D.n, weight, B.d, h->stream);
+  if (s == STST_OK) s = alloc((void **)&f32, sizeof(float) * B.n * (2 * B.p + 1));
+  if (s == STST_OK) s = launch_to_f32(B.d, f32, (long long)B.n * (2 * B.p + 1), h->stream);
+  if (s != STST_OK) {
+    cudaFree(B.d);
+    cudaFree(f32);
+    return s;
+  }
   h->mats[l].push_back(B);
   h->mats32[l].push_back(f32);
   return (int)h->mats[l].size() - 1;
@@ -258,9 +263,14 @@ int add_combo(stst_problem *h, int l, int i1, double c1, int i2, double c2) {
   B.p = D.p;
   const int nb = B.n * (2 * B.p + 1);
   STST_TRY(alloc((void **)&B.d, sizeof(double) * nb));
-  float *f32;
-  STST_TRY(alloc((void **)&f32, sizeof(float) * nb));
-  STST_TRY(launch_band_axpby(h->mats[l][i1].d, c1, h->mats[l][i2].d, c2, B.d, f32, nb, h->stream));
+  float *f32 = nullptr;
+  int s = alloc((void **)&f32, sizeof(float) * nb);
+  if (s == STST_OK) s = launch_band_axpby(h->mats[l][i1].d, c1, h->mats[l][i2].d, c2, B.d, f32, nb, h->stream);
+  if (s != STST_OK) {
+    cudaFree(B.d);
+    cudaFree(f32);
+    return s;
+  }
   h->mats[l].push_back(B);
   h->mats32[l].push_back(f32);
   return (int)h->mats[l].size() - 1;
@@ -318,7 +328,34 @@ int free_pool(stst_problem *h) {
   return STST_OK;
 }
 
+// The plans and the solver graphs captured from them hold pointers into the band matrices and the
+// intermediate pool. They are dropped whenever those change: run_plan refuses an empty plan
+// (STST_ERR_STATE) and the graphs are rebuilt by the next solve.
+void invalidate_plans(stst_problem *h) {
+  h->sys_plan.passes.clear();
+  h->lift_plan.passes.clear();
+  h->pcg_graph_valid = 0;
+  if (h->pcg_exec) {
+    cudaGraphExecDestroy(h->pcg_exec);
+    h->pcg_exec = nullptr;
+  }
+  h->ir_graph_valid = 0;
+  if (h->ir_exec) {
+    cudaGraphExecDestroy(h->ir_exec);
+    h->ir_exec = nullptr;
+  }
+}
+
+int replan_impl(stst_problem *h, const std::vector<Term> &terms);
+
 int replan(stst_problem *h, const std::vector<Term> &terms) {
+  invalidate_plans(h);
+  const int s = replan_impl(h, terms);
+  if (s != STST_OK) invalidate_plans(h);
+  return s;
+}
+
+int replan_impl(stst_problem *h, const std::vector<Term> &terms) {
   int need1 = 0, need2 = 0;
   STST_TRY(make_plan(h, terms, false, h->sys_plan, &need1));
   // lifting: time matrices are the full ones; same term list (time ids index tfull)
@@ -370,11 +407,6 @@ int replan(stst_problem *h, const std::vector<Term> &terms) {
       if (lev > 0)
         for (int a = 0; a < pp.n_in; ++a) pp.in[a] = src[a];
     }
-  }
-  h->pcg_graph_valid = 0;
-  if (h->pcg_exec) {
-    cudaGraphExecDestroy(h->pcg_exec);
-    h->pcg_exec = nullptr;
   }
   return STST_OK;
 }
@@ -724,14 +756,11 @@ static int additive_terms(stst_problem *h, int rank, const int *dir_of, const in
   return STST_OK;
 }
 
-int stst_set_potential(stst_handle h, int rank, const double *v_qp) {
-  STST_TRY(check(h));
-  ApiScope scope(h);
-  if (rank < 0 || rank > 3 || (rank > 0 && !v_qp)) return STST_ERR_ARG;
-  cudaStream_t st = h->stream;
-  const int d = h->d;
-  // drop previous weighted matrices (ids >= SM_K2S+1) and weight buffers
-  for (int l = 1; l <= d; ++l) {
+// Removes the potential: its band matrices (ids beyond SM_K2S, including the combined ones) and weight
+// buffers are freed, so the plans that point at them are dropped as well until the next replan.
+static void drop_potential(stst_problem *h) {
+  invalidate_plans(h);
+  for (int l = 1; l <= h->d; ++l) {
     while ((int)h->mats[l].size() > SM_K2S + 1) {
       cudaFree(h->mats[l].back().d);
       cudaFree(h->mats32[l].back());
@@ -744,6 +773,41 @@ int stst_set_potential(stst_handle h, int rank, const double *v_qp) {
   h->pot_rank = 0;
   h->g_valid = 0;
   if (h->prec_op == 1) h->fd_ready = 0;  // the potential-aware factors depend on V
+}
+
+static int set_potential_impl(stst_problem *h, int rank, const double *v_qp, const std::vector<double> &host);
+
+int stst_set_potential(stst_handle h, int rank, const double *v_qp) {
+  STST_TRY(check(h));
+  ApiScope scope(h);
+  if (rank < 0 || rank > 3 || (rank > 0 && !v_qp)) return STST_ERR_ARG;
+  // the samples are read and checked before anything of the handle changes: a rejected potential
+  // leaves the previous operator in place
+  std::vector<double> host;
+  if (rank > 0) {
+    int stride = 0;
+    for (int l = 1; l <= h->d; ++l) stride += h->dir[l].Q();
+    host.resize((size_t)stride * rank);
+    STST_CUDA(cudaStreamSynchronize(h->stream));
+    STST_CUDA(cudaMemcpy(host.data(), v_qp, sizeof(double) * host.size(), cudaMemcpyDeviceToHost));
+    for (double v : host)
+      if (!std::isfinite(v)) return STST_ERR_ARG;
+  }
+  const int s = set_potential_impl(h, rank, v_qp, host);
+  if (s != STST_OK) {
+    // a failure part-way (allocation, launch) leaves the V = 0 operator; if even that cannot be planned,
+    // every call that needs the mat-vec returns STST_ERR_STATE
+    drop_potential(h);
+    replan(h, combine_terms(h, merge_terms(base_terms(h))));
+    cudaStreamSynchronize(h->stream);
+  }
+  return s;
+}
+
+static int set_potential_impl(stst_problem *h, int rank, const double *v_qp, const std::vector<double> &host) {
+  cudaStream_t st = h->stream;
+  const int d = h->d;
+  drop_potential(h);
   std::vector<Term> terms = base_terms(h);
   if (rank > 0) {
     int stride = 0;
@@ -752,11 +816,6 @@ int stst_set_potential(stst_handle h, int rank, const double *v_qp) {
     STST_TRY(alloc((void **)&vcopy, sizeof(double) * stride * rank));
     h->pot_bufs.push_back(vcopy);
     STST_CUDA(cudaMemcpyAsync(vcopy, v_qp, sizeof(double) * stride * rank, cudaMemcpyDeviceToDevice, st));
-    std::vector<double> host((size_t)stride * rank);
-    STST_CUDA(cudaMemcpyAsync(host.data(), v_qp, sizeof(double) * stride * rank, cudaMemcpyDeviceToHost, st));
-    STST_CUDA(cudaStreamSynchronize(st));
-    for (double v : host)
-      if (!std::isfinite(v)) return STST_ERR_ARG;
     // weight registry per direction: key = list of factor ids (sorted) -> (M id, K2S id)
     // factor id f in [0, rank): v_{f,l}; "one" if the samples are identically 1.
     int wm[STST_MAXD + 1][3], wk[STST_MAXD + 1][3];
@@ -784,7 +843,9 @@ int stst_set_potential(stst_handle h, int rank, const double *v_qp) {
         if (canon[r] != r) { wm[l][r] = wm[l][canon[r]]; wk[l][r] = wk[l][canon[r]]; continue; }
         const double *w = vcopy + (size_t)r * stride + off;
         wm[l][r] = add_band(h, l, MK_M, w);
+        if (wm[l][r] < 0) return wm[l][r];
         wk[l][r] = add_band(h, l, MK_K2S, w);
+        if (wk[l][r] < 0) return wk[l][r];
       }
       for (int r = 0; r < rank; ++r)
         for (int s = 0; s < rank; ++s) {
@@ -798,6 +859,7 @@ int stst_set_potential(stst_handle h, int rank, const double *v_qp) {
           STST_TRY(launch_weight_product(vcopy + (size_t)r * stride + off, vcopy + (size_t)s * stride + off, wp, Ql,
                                          st));
           pm[l][r][s] = add_band(h, l, MK_M, wp);
+          if (pm[l][r][s] < 0) return pm[l][r][s];
         }
       off += Ql;
     }

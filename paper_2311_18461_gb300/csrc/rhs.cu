@@ -462,16 +462,39 @@ int rhs_lift_compute(stst_problem *h, const double *f_qp, const double *u_qp, do
 #define STST_RHS_SCRATCH_ELEMS (1 << 20)  // complex128 elements: 16 MiB
 static __device__ __align__(256) double2 g_rhs_scratch[STST_RHS_SCRATCH_ELEMS];
 
-// Device address of g_rhs_scratch, looked up once per device with that device current.
+// Device address of g_rhs_scratch, looked up once per device with that device current. The lookup is
+// keyed on the device's current context as well: a device reset (cudaDeviceReset) ends the context and
+// the module is loaded again in the next one, possibly at another address, so a new context id makes
+// the lookup run again.
+typedef int (*CtxGetIdFn)(void *ctx, unsigned long long *id);
+
+static unsigned long long current_context_id() {
+  static CtxGetIdFn fn = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (CtxGetIdFn)f;
+    looked = true;
+  }
+  unsigned long long id = 0;
+  if (!fn || fn(nullptr, &id) != 0) return 0;  // 0: unknown (no entry point, or no current context yet)
+  return id;
+}
+
 static int rhs_scratch_address(double2 **out) {
   static std::mutex mu;
   static double2 *addr[256];
+  static unsigned long long ctx[256];
   static bool ready[256];
   int dev = 0;
   STST_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 256) return STST_ERR_ARG;
   std::lock_guard<std::mutex> lock(mu);
-  if (!ready[dev]) {
+  const unsigned long long id = current_context_id();
+  if (!ready[dev] || id == 0 || id != ctx[dev]) {
     void *p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_rhs_scratch);
     if (e != cudaSuccess || p == nullptr) {
@@ -479,6 +502,7 @@ static int rhs_scratch_address(double2 **out) {
       return STST_ERR_CUDA;
     }
     addr[dev] = (double2 *)p;
+    ctx[dev] = id ? id : current_context_id();  // the lookup above has made the primary context current
     ready[dev] = true;
   }
   *out = addr[dev];
@@ -538,15 +562,18 @@ extern "C" int stst_rhs_noalloc(stst_handle h, const double *f_qp, const double 
   STST_TRY(rhs_scratch_address(&scratch));
   long long sz = n[0];
   for (int l = 1; l <= d; ++l) sz *= Q[l];
-  const long long need = (h->pot_rank > 0 ? 5 : 4) * sz;
+  // slices of the scratch in the order they are needed: T0, W1, W2 for every load; T1 for the
+  // least-squares load; T0V for the least-squares load with a potential (the ultraweak load has no V term)
+  const bool uw = h->formulation == STST_FORM_UW;  // ultraweak: plain load int f conj(B_i)
+  const long long need = (uw ? 3 : (h->pot_rank > 0 ? 5 : 4)) * sz;
   if (f_qp && need > STST_RHS_SCRATCH_ELEMS) return STST_ERR_ARG;  // forcing grid too large for the static scratch
   STST_CUDA(cudaMemsetAsync(rhs, 0, sizeof(double2) * h->N_dof, st));
   if (f_qp) {
-    double2 *T1 = scratch, *T0 = scratch + sz, *W1 = scratch + 2 * sz, *W2 = scratch + 3 * sz;
-    double2 *T0V = h->pot_rank > 0 ? scratch + 4 * sz : nullptr;
+    double2 *T0 = scratch, *W1 = scratch + sz, *W2 = scratch + 2 * sz;
+    double2 *T1 = uw ? nullptr : scratch + 3 * sz;
+    double2 *T0V = (h->pot_rank > 0 && !uw) ? scratch + 4 * sz : nullptr;
     long long Qs = 1;
     for (int l = 1; l <= d; ++l) Qs *= Q[l];
-    const bool uw = h->formulation == STST_FORM_UW;  // ultraweak: plain load int f conj(B_i)
     if (!uw) STST_TRY(contract(h, 0, (const double2 *)f_qp, T1, 1, Qs, 1, 0.0, -1.0, 0));
     STST_TRY(contract(h, 0, (const double2 *)f_qp, T0, 1, Qs, 0, 1.0, 0.0, 0));
     struct Term { double2 *src; int der[STST_MAXD + 1]; double s; };
@@ -563,7 +590,7 @@ extern "C" int stst_rhs_noalloc(stst_handle h, const double *f_qp, const double 
         terms.push_back(t);
       }
     }
-    if (T0V && !uw) {
+    if (T0V) {
       const DirInfo &D = h->dir[0];
       long long tot = Qs * D.n;
       k_contract_time_pot<<<grid_for(tot, 128), 128, 0, st>>>((const double2 *)f_qp, T0V, h->tab[0], h->qwts[0], D.p,

@@ -329,6 +329,38 @@ def test_status_codes():
     assert st == 0 and it == 0
 
 
+def test_rejected_potential_keeps_the_previous_operator():
+    """A potential with a non-finite sample is rejected (STST_ERR_ARG) before anything of the handle
+    changes: the mat-vec, the captured PCG graph and the iterative-refinement graph keep applying the
+    potential installed before, and a later valid potential replaces it in all of them."""
+    prob, disc = _problem([6, 7, 5], [2, 3, 2], "harmonic", prec=S.STST_PREC_FP32)
+    prob.build_fd()
+    b = random_complex(prob.n_dof, 61)
+    x1, st, _, _ = prob.pcg(to_dev(b), tol=1e-10, maxit=200)      # builds the PCG graph
+    y1, st1, _, _, _ = prob.ir(to_dev(b), tol=1e-10, maxit=40)     # builds the IR graph
+    assert st == 0 and st1 == 0
+    bad = sample_potential(prob, harmonic_potential(2))
+    bad[3] = float("nan")
+    with pytest.raises(S.StstError) as e:
+        prob.set_potential(bad, 2)
+    assert e.value.status == S.STST_ERR_ARG
+    v = random_complex(prob.n_dof, 62)
+    assert rel_err(to_np(prob.apply_sys(to_dev(v))), disc.apply(v)) < 1e-12
+    x2, st, _, _ = prob.pcg(to_dev(b), tol=1e-10, maxit=200)
+    assert st == 0 and rel_err(to_np(x2), to_np(x1)) < 1e-12
+    # a different valid potential reaches the mat-vec and both solver graphs
+    V = bump_potential(2)
+    prob.set_potential(sample_potential(prob, V), len(V))
+    disc_b = oracle_disc([6, 7, 5], [2, 3, 2], potential=V)
+    assert rel_err(to_np(prob.apply_sys(to_dev(v))), disc_b.apply(v)) < 1e-12
+    xo, _, _, _ = opcg.pcg(disc_b.apply, ofd.FastDiagonalization(disc_b).apply, b, tol=1e-13, maxit=300)
+    x3, st, _, rr = prob.pcg(to_dev(b), tol=1e-12, maxit=300)
+    assert st == 0 and rel_err(to_np(x3), xo) < 1e-8
+    y3, st, _, _, _ = prob.ir(to_dev(b), tol=1e-10, maxit=80, inner_maxit=100)
+    assert st == 0 and rel_err(to_np(y3), xo) < 1e-8
+    prob.close()
+
+
 @pytest.mark.parametrize("p", [2, 3, 4])
 def test_apply_prec_size_sweep(p):
     """Every spatial size from 1 to 100 unknowns: the eigen setup must handle the nearly degenerate

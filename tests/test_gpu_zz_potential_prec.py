@@ -55,6 +55,25 @@ def test_apply_prec_potential_equal_meshes(same):
     prob.close()
 
 
+@pytest.mark.parametrize("n_el,p,V", [
+    ([6, 9], [2, 3], [[lambda x: -100.0 * x * (1 - x)]]),
+    ([8, 10, 9], [2, 3, 2], [[lambda x: -100.0 * x * (1 - x), lambda x: 1.0 + 0.0 * x],
+                             [lambda x: 1.0 + 0.0 * x, lambda x: 3.0 + 4.0 * x]]),
+])
+def test_apply_prec_potential_with_negative_eigenvalues(n_el, p, V):
+    """A negative factor makes G_l = nu L_l + M_{v_l} indefinite: some eigenvalues of (G_l, M_l) are
+    negative (the Sturm-count bracket of the eigensolver and the lambda < 0 sign of the advection term
+    in H_i). H_i stays Hermitian positive definite for every real lambda."""
+    prob, disc = _problem(n_el, p, V=V)
+    F = ofd.PotentialFastDiagonalization(disc)
+    assert F.lam[1].min() < 0 < F.lam[1].max()
+    assert prob.build_fd() == 0
+    r = random_complex(prob.n_dof, 35)
+    s = to_np(prob.apply_prec(to_dev(r)))
+    assert rel_err(s, F.apply(r)) < 1e-10
+    prob.close()
+
+
 def test_apply_prec_potential_fp32():
     prob, disc = _problem([9, 11, 7], [2, 3, 2], prec=S.STST_PREC_FP32)
     assert prob.build_fd() == 0

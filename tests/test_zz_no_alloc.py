@@ -23,10 +23,15 @@ def _forcing(t, *xs):
     return np.exp(1j * (2 * t + xs[0])) * (1 + 0.5 * sum(x ** 2 for x in xs))
 
 
-@pytest.mark.parametrize("n_el,p,with_potential", [([6, 7, 5], [2, 2, 3], True), ([9, 8], [3, 2], False)])
-def test_noalloc_matches_allocating_rhs_on_consecutive_calls(n_el, p, with_potential):
+@pytest.mark.parametrize("n_el,p,with_potential,form", [
+    ([6, 7, 5], [2, 2, 3], True, S.STST_FORM_LS),
+    ([9, 8], [3, 2], False, S.STST_FORM_LS),
+    ([6, 7, 5], [2, 2, 3], True, S.STST_FORM_UW),     # the ultraweak load: T0 only, initial term added
+    ([4, 5, 4, 3], [2, 2, 3, 2], True, S.STST_FORM_LS),  # 3D+t: the chain of contractions through W1, W2
+])
+def test_noalloc_matches_allocating_rhs_on_consecutive_calls(n_el, p, with_potential, form):
     d = len(n_el) - 1
-    prob = S.Problem(d, n_el, p, T=0.8, nu=1.2)
+    prob = S.Problem(d, n_el, p, T=0.8, nu=1.2, formulation=form)
     if with_potential:
         V = harmonic_potential(d)
         prob.set_potential(sample_potential(prob, V), len(V))
@@ -72,3 +77,24 @@ def test_noalloc_takes_no_device_memory_and_rejects_oversized_grids():
         S.stst_rhs_noalloc(big.h, f_big, None, big.vec(), None)
     assert e.value.status == -1
     big.close()
+
+
+def test_noalloc_ultraweak_load_needs_three_slices():
+    """The ultraweak load uses three grid-sized slices of the static array (no least-squares time
+    derivative, no potential term): a grid that needs 3 but not 4 or 5 slices is accepted, with a
+    potential installed, and matches stst_rhs."""
+    n_el, p = [30, 25, 25], [2, 2, 2]
+    prob = S.Problem(2, n_el, p, formulation=S.STST_FORM_UW)
+    sz = prob.n[0] * (25 * 4) ** 2
+    assert 3 * sz <= 2 ** 20 < 4 * sz
+    V = harmonic_potential(2)
+    prob.set_potential(sample_potential(prob, V), len(V))
+    f_qp = sample_forcing(prob, _forcing)
+    ref = prob.vec()
+    S.stst_rhs(prob.h, f_qp, None, ref, None)
+    for _ in range(2):
+        out = torch.full_like(ref, complex(5.0, 1.0))
+        S.stst_rhs_noalloc(prob.h, f_qp, None, out, None)
+        torch.cuda.synchronize()
+        assert rel_err(to_np(out), to_np(ref)) < 1e-12
+    prob.close()
