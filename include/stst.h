@@ -238,8 +238,13 @@ int stst_rhs_noalloc(stst_handle h, const double *f_qp, const double *u0_qp, dou
  * stst_pcg_solve: P-hat-preconditioned conjugate gradients (Sec. 5.3, Sec. 6)
  * from the initial guess in x (x is overwritten by the solution). Stops when
  * ||rhs - A x_k||_2 <= tol ||rhs||_2 (recursive residual) or after maxit
- * iterations. With a low-precision preconditioner the Polak-Ribiere
- * (flexible) beta is used. iters, relres: host outputs (may be NULL).
+ * iterations. With the FP64 preconditioner this is the paper's PCG. With a
+ * low-precision one (STST_PREC_FP32 / BF16, a slightly different operator at
+ * every application) it is the flexible CG of Notay (2000) with one kept
+ * direction: complex alpha = <r, p> / <p, A p> (exact line search) and
+ * complex beta = -<z, A p> / <p, A p> (each direction A-orthogonal to the
+ * previous one); for a fixed Hermitian preconditioner both give the same
+ * iterates. iters, relres: host outputs (may be NULL).
  * Needs build_fd. Returns OK, NOT_CONVERGED or BREAKDOWN, or TIMEOUT when a
  * bounded device-side wait expired since the last solve (the BF16 tensor-core
  * mode products wait on their MMAs' completion barrier; the flag is then
@@ -250,7 +255,7 @@ int stst_pcg_solve(stst_handle h, const double *rhs, double *x, double tol, int 
 
 /*
  * stst_ir_solve: mixed-precision iterative refinement (an extension): FP64
- * residual rhs - A x and FP64 update x += d around an inner FP32 PCG on
+ * residual rhs - A x and FP64 update x += d around an inner FP32 flexible CG on
  * A d = r (FP32 mat-vec, FP32/BF16 preconditioner, inner tolerance inner_tol).
  * Stops when the FP64 relative residual <= tol or after maxit outer steps.
  * iters receives the total inner iterations, outer the outer steps. Returns

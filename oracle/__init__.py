@@ -18,18 +18,21 @@ Modules, each citing the passage of the paper it restates:
   fd        -- the preconditioner P-hat (Eq. prec_definition) and Algorithm 1; its potential-aware
                variant P_V for potentials that are sums of one-direction factors (an extension: the
                construction of Eq. prec_definition applied to i d_t + sum_l (-nu d_ll + v_l))
-  pcg       -- preconditioned conjugate gradients (Sec. 5.3, Sec. 6)
+  pcg       -- preconditioned conjugate gradients (Sec. 5.3, Sec. 6); flexible CG for preconditioners
+               applied inexactly (Notay 2000; not in the paper)
   rhs       -- load vector F(S B_i) and liftings of initial / boundary data (Sec. 2.2, Sec. 4.3)
   norms     -- L2 and V-norm errors (Sec. 2.1, Theorem 2)
   warmstart -- network, loss, gradient, Adam and randomized snapshot basis of the learned warm start
                (not in the paper: its PCG starts from zero, Sec. 6)
 
 Parity status: every function here is pinned by a `-m "not gpu"` test against
-closed forms, the paper's printed numbers, invariants or brute force, except
-the separable-potential terms, whose Kronecker expansion is pinned only by
-brute-force quadrature of the same sesquilinear form (the paper has no
-potential), and the inexact-preconditioner (flexible) CG variant, which the
-paper does not define: parity unpinned beyond the exact-preconditioner case.
+closed forms, the paper's printed numbers, invariants or brute force. The
+separable-potential terms (the paper has no potential) are pinned by
+brute-force quadrature of the same sesquilinear form. The flexible CG used
+with low-precision preconditioners (Notay's method, not in the paper) is
+pinned by the invariants it fixes under a preconditioner that changes at every
+iteration: A-orthogonal consecutive directions, exact line searches, a
+non-increasing A-norm error, and plain PCG's iterates for a fixed one.
 P_V is pinned by its spatial operators against brute-force Galerkin matrices and by Algorithm 1
 against the dense inverse of P_V assembled from its definition; its ANOVA approximation for products of
 factors by closed-form means and by its equality with P_V for additive potentials.

@@ -252,8 +252,7 @@ int run_plan(const Plan &plan, const void *x, void *y, int precision, int epi, c
 template <typename R, typename TI, typename TO, int RPT, int CPT>
 __global__ void __launch_bounds__(256) k_modeprod(const TI *__restrict__ X, TO *__restrict__ Y, const R *__restrict__ U,
                                                   int n, long long inner, long long ncols, int backward,
-                                                  const TO *__restrict__ dotvec, double *dot_partials,
-                                                  const int *done) {
+                                                  const EpiDot ed, const int *done) {
   using T = typename C2<R>::T;
   constexpr int CW = 8 * CPT, RB = 32 * RPT, RBP = RB + 1;  // U rows padded: the transposed staging
                                                             // (backward) writes stride RBP, no bank conflicts
@@ -321,7 +320,7 @@ __global__ void __launch_bounds__(256) k_modeprod(const TI *__restrict__ X, TO *
     cp_async_wait_all();
   }
   __syncthreads();
-  double dacc = 0.0;
+  double dacc[4] = {0.0, 0.0, 0.0, 0.0};
   if constexpr (CPT == 32) {
     // wide tile (n <= ~100, FP32): 32 rows x 256 columns per CTA. Warp w owns rows 8 rg .. 8 rg + 7
     // (rg = w / 2) and column group cgp = 32 (w % 2) + lane; a thread accumulates those 8 rows x the
@@ -363,10 +362,7 @@ __global__ void __launch_bounds__(256) k_modeprod(const TI *__restrict__ X, TO *
           res.x = ax[r][q];
           res.y = ay[r][q];
           Y[idx] = res;
-          if (dotvec) {
-            TO dv = dotvec[idx];
-            dacc += (double)dv.x * (double)res.x + (double)dv.y * (double)res.y;
-          }
+          if (ed.part) epi_dot_acc<TO>(dacc, ed, idx, (double)res.x, (double)res.y);
         }
       }
     }
@@ -414,18 +410,12 @@ __global__ void __launch_bounds__(256) k_modeprod(const TI *__restrict__ X, TO *
           res.x = ax[r][c];
           res.y = ay[r][c];
           Y[idx] = res;
-          if (dotvec) {
-            TO dv = dotvec[idx];
-            dacc += (double)dv.x * (double)res.x + (double)dv.y * (double)res.y;
-          }
+          if (ed.part) epi_dot_acc<TO>(dacc, ed, idx, (double)res.x, (double)res.y);
         }
       }
     }
   }
-  if (dot_partials) {
-    double s = block_sum(dacc, sh);
-    if (threadIdx.x == 0) dot_partials[blockIdx.y * gridDim.x + blockIdx.x] = s;
-  }
+  if (ed.part) epi_dot_store(dacc, ed, (long long)blockIdx.y * gridDim.x + blockIdx.x, sh);
 }
 
 static size_t modeprod_smem(int n, MpCfg c, size_t rsize) {
@@ -438,16 +428,16 @@ static dim3 modeprod_grid(int n, long long ncols, MpCfg c) {
 
 template <typename R, typename TI, typename TO>
 static int launch_modeprod(const TI *X, TO *Y, const R *U, int n, long long inner, long long outer, int backward,
-                           const TO *dotvec, double *dot_partials, const int *done, cudaStream_t s, MpCfg cfg) {
+                           const EpiDot &ed, const int *done, cudaStream_t s, MpCfg cfg) {
   const long long ncols = inner * outer;
   const dim3 grid = modeprod_grid(n, ncols, cfg);
-  if (dot_partials && (long long)grid.x * grid.y > STST_MAXPART) return STST_ERR_ARG;
+  if (ed.part && (long long)grid.x * grid.y > STST_MAXPART) return STST_ERR_ARG;
   if (grid.x > 0x7fffffffu || grid.y > 65535u) return STST_ERR_ARG;
   STST_PROF(sizeof(R) == 8 ? "modeprod_f64" : "modeprod_f32", s);
   const size_t sm = modeprod_smem(n, cfg, sizeof(R));
   auto go = [&](auto kern) -> int {
     STST_TRY(ensure_dyn_smem((const void *)kern, sm));
-    kern<<<grid, 256, sm, s>>>(X, Y, U, n, inner, ncols, backward, dotvec, dot_partials, done);
+    kern<<<grid, 256, sm, s>>>(X, Y, U, n, inner, ncols, backward, ed, done);
     return STST_OK;
   };
   int st = STST_ERR_ARG;
@@ -521,11 +511,11 @@ static int tune_one(stst_problem *h, int l, long long inner, long long outer, Mp
     {
       if (modeprod_smem(n, c, sizeof(R)) > (size_t)optin) continue;
       for (int w = 0; w < 2 && status == STST_OK; ++w)
-        status = launch_modeprod<R, T, T>(X, Y, U, n, inner, outer, 0, nullptr, nullptr, nullptr, st, c);
+        status = launch_modeprod<R, T, T>(X, Y, U, n, inner, outer, 0, EpiDot(), nullptr, st, c);
       if (status != STST_OK) break;
       cudaEventRecord(e0, st);
       for (int w = 0; w < 5 && status == STST_OK; ++w)
-        status = launch_modeprod<R, T, T>(X, Y, U, n, inner, outer, 0, nullptr, nullptr, nullptr, st, c);
+        status = launch_modeprod<R, T, T>(X, Y, U, n, inner, outer, 0, EpiDot(), nullptr, st, c);
       cudaEventRecord(e1, st);
       const cudaError_t es = cudaEventSynchronize(e1);
       if (es != cudaSuccess) {
@@ -1084,7 +1074,7 @@ __device__ __forceinline__ void fd2d_contract(const float *__restrict__ sR, int 
 template <typename TI, typename TO>
 __global__ void __launch_bounds__(512) k_fd2d(const TI *__restrict__ X, TO *__restrict__ Y, const float *__restrict__ U1,
                                               const float *__restrict__ U2, int n1, int n2, int nt, int backward,
-                                              const TO *__restrict__ dotvec, double *dot_partials, const int *done) {
+                                              const EpiDot ed, const int *done) {
   constexpr int NR = FD2D_NR, NC = FD2D_NC;
   if (done && *done) return;
   extern __shared__ __align__(16) unsigned char fd_smem[];
@@ -1158,7 +1148,7 @@ __global__ void __launch_bounds__(512) k_fd2d(const TI *__restrict__ X, TO *__re
       }
   }
   __syncthreads();
-  double dacc = 0.0;
+  double dacc[4] = {0.0, 0.0, 0.0, 0.0};
   if (tid < Ra2 * ((m + NC - 1) / NC)) {
     const int a0 = tid % Ra2, g = tid / Ra2;
     if (!backward)  // Y[j][k] = sum_c U2[c][k] Z[j][c]
@@ -1177,17 +1167,11 @@ __global__ void __launch_bounds__(512) k_fd2d(const TI *__restrict__ X, TO *__re
           res.x = ax[k][q];
           res.y = ay[k][q];
           Y[idx] = res;
-          if (dotvec) {
-            const TO dv = dotvec[idx];
-            dacc += (double)dv.x * (double)res.x + (double)dv.y * (double)res.y;
-          }
+          if (ed.part) epi_dot_acc<TO>(dacc, ed, idx, (double)res.x, (double)res.y);
         }
       }
   }
-  if (dot_partials) {
-    const double s2 = block_sum(dacc, sh);
-    if (tid == 0) dot_partials[(long long)blockIdx.x * S + part] = s2;
-  }
+  if (ed.part) epi_dot_store(dacc, ed, (long long)blockIdx.x * S + part, sh);
 }
 
 // items of the larger of the two contractions, at least 256 threads for the staging
@@ -1222,8 +1206,8 @@ bool fd2d_fits(const stst_problem *h) {
 }
 
 template <typename TI, typename TO>
-static int launch_fd2d(const TI *X, TO *Y, const stst_problem *h, int backward, const TO *dotvec, double *partials,
-                       const int *done, cudaStream_t s, int S) {
+static int launch_fd2d(const TI *X, TO *Y, const stst_problem *h, int backward, const EpiDot &ed, const int *done,
+                       cudaStream_t s, int S) {
   const int n1 = h->dir[1].n, n2 = h->dir[2].n, nt = h->n_t();
   if (S < 1 || S > FD2D_MAXS || !fd2d_split_ok(n1, n2, S)) return STST_ERR_ARG;
   const int m = backward ? (n2 + S - 1) / S : (n1 + S - 1) / S;
@@ -1232,7 +1216,7 @@ static int launch_fd2d(const TI *X, TO *Y, const stst_problem *h, int backward, 
   STST_PROF("modeprod2d_f32", s);
   STST_TRY(ensure_dyn_smem((const void *)k_fd2d<TI, TO>, sm));
   k_fd2d<TI, TO><<<dim3((unsigned)fd2d_slabs(h), S), nth, sm, s>>>(X, Y, h->U32[1], h->U32[2], n1, n2, nt, backward,
-                                                                   dotvec, partials, done);
+                                                                   ed, done);
   STST_CUDA(cudaGetLastError());
   return STST_OK;
 }
@@ -1249,15 +1233,15 @@ static int time_solve(stst_problem *h, void *Y, const int *done, cudaStream_t st
   return launch_timesolve<R>(Y, G, D, h->n_t(), h->N_s, h->dir[0].p, done, st);
 }
 
-int fd_apply(stst_problem *h, const double *r, double *s, int precision, const void *dotvec, double *dot_partials,
-             const int *done, void *bufA, void *bufB, float *out32, const float *in32) {
-  const int d = h->d, nt = h->n_t();
-  const long long Ns = h->N_s;
+int fd_apply(stst_problem *h, const double *r, double *s, int precision, const EpiDot &ed, const int *done,
+             void *bufA, void *bufB, float *out32, const float *in32) {
+  const int d = h->d;
   cudaStream_t st = h->stream;
+  const EpiDot none;
   // tensor geometry of mode l (1..d) in the time-fastest layout: inner = nt * prod_{k<l} n_k
   long long inner[STST_MAXD + 1], outer[STST_MAXD + 1];
   {
-    long long acc = nt;
+    long long acc = h->n_t();
     for (int l = 1; l <= d; ++l) {
       inner[l] = acc;
       acc *= h->dir[l].n;
@@ -1272,8 +1256,8 @@ int fd_apply(stst_problem *h, const double *r, double *s, int precision, const v
     int cur = 0;
     for (int l = 1; l <= d; ++l) {
       double2 *dst = bufs[cur];
-      STST_TRY((launch_modeprod<double, double2, double2>(src, dst, h->U[l], h->dir[l].n, inner[l], outer[l], 0,
-                                                           nullptr, nullptr, done, st, h->mp_cfg[l])));
+      STST_TRY((launch_modeprod<double, double2, double2>(src, dst, h->U[l], h->dir[l].n, inner[l], outer[l], 0, none,
+                                                           done, st, h->mp_cfg[l])));
       src = dst;
       cur ^= 1;
     }
@@ -1281,8 +1265,7 @@ int fd_apply(stst_problem *h, const double *r, double *s, int precision, const v
     for (int l = d; l >= 1; --l) {
       double2 *dst = (l == 1) ? (double2 *)s : bufs[cur];
       STST_TRY((launch_modeprod<double, double2, double2>(src, dst, h->U[l], h->dir[l].n, inner[l], outer[l], 1,
-                                                           l == 1 ? (const double2 *)dotvec : nullptr,
-                                                           l == 1 ? dot_partials : nullptr, done, st, h->mp_cfg[l])));
+                                                           l == 1 ? ed : none, done, st, h->mp_cfg[l])));
       src = dst;
       cur ^= 1;
     }
@@ -1304,12 +1287,12 @@ int fd_apply(stst_problem *h, const double *r, double *s, int precision, const v
     for (int l = 1; l <= d; ++l) {
       float2 *dst = bufs[cur];
       if (l == 1 && !in32) {
-        STST_TRY((launch_modeprod_tc<double2, float2>((const double2 *)r, dst, Bk(l, 0), lo(l), split, h->dir[l].n, inner[l],
-                                                      outer[l], nullptr, nullptr, done, ef, st)));
+        STST_TRY((launch_modeprod_tc<double2, float2>((const double2 *)r, dst, Bk(l, 0), lo(l), split, h->dir[l].n,
+                                                      inner[l], outer[l], none, done, ef, st)));
       } else {
         const float2 *in = (l == 1) ? (const float2 *)in32 : src32;
-        STST_TRY((launch_modeprod_tc<float2, float2>(in, dst, Bk(l, 0), lo(l), split, h->dir[l].n, inner[l], outer[l], nullptr,
-                                                     nullptr, done, ef, st)));
+        STST_TRY((launch_modeprod_tc<float2, float2>(in, dst, Bk(l, 0), lo(l), split, h->dir[l].n, inner[l], outer[l],
+                                                     none, done, ef, st)));
       }
       src32 = dst;
       cur ^= 1;
@@ -1318,17 +1301,16 @@ int fd_apply(stst_problem *h, const double *r, double *s, int precision, const v
     for (int l = d; l >= 1; --l) {
       if (l == 1) {
         if (out32) {
-          STST_TRY((launch_modeprod_tc<float2, float2>(src32, (float2 *)out32, Bk(l, 1), lo(l), split, h->dir[l].n, inner[l],
-                                                       outer[l], (const float2 *)dotvec, dot_partials, done, ef, st)));
+          STST_TRY((launch_modeprod_tc<float2, float2>(src32, (float2 *)out32, Bk(l, 1), lo(l), split, h->dir[l].n,
+                                                       inner[l], outer[l], ed, done, ef, st)));
         } else {
-          STST_TRY((launch_modeprod_tc<float2, double2>(src32, (double2 *)s, Bk(l, 1), lo(l), split, h->dir[l].n, inner[l],
-                                                        outer[l], (const double2 *)dotvec, dot_partials, done, ef,
-                                                        st)));
+          STST_TRY((launch_modeprod_tc<float2, double2>(src32, (double2 *)s, Bk(l, 1), lo(l), split, h->dir[l].n,
+                                                        inner[l], outer[l], ed, done, ef, st)));
         }
       } else {
         float2 *dst = bufs[cur];
-        STST_TRY((launch_modeprod_tc<float2, float2>(src32, dst, Bk(l, 1), lo(l), split, h->dir[l].n, inner[l], outer[l], nullptr,
-                                                     nullptr, done, ef, st)));
+        STST_TRY((launch_modeprod_tc<float2, float2>(src32, dst, Bk(l, 1), lo(l), split, h->dir[l].n, inner[l],
+                                                     outer[l], none, done, ef, st)));
         src32 = dst;
         cur ^= 1;
       }
@@ -1339,22 +1321,20 @@ int fd_apply(stst_problem *h, const double *r, double *s, int precision, const v
   if (h->fd2d) {  // modes 1 and 2 of each transform in one kernel per (t, i3) slab; mode 3 (d = 3) separate
     float2 *y32 = (float2 *)bufA;
     const int S = h->fd2d;
-    if (in32) STST_TRY((launch_fd2d<float2, float2>((const float2 *)in32, y32, h, 0, nullptr, nullptr, done, st, S)));
-    else STST_TRY((launch_fd2d<double2, float2>((const double2 *)r, y32, h, 0, nullptr, nullptr, done, st, S)));
+    if (in32) STST_TRY((launch_fd2d<float2, float2>((const float2 *)in32, y32, h, 0, none, done, st, S)));
+    else STST_TRY((launch_fd2d<double2, float2>((const double2 *)r, y32, h, 0, none, done, st, S)));
     if (d == 3) {
       float2 *z32 = (float2 *)bufB;
-      STST_TRY((launch_modeprod<float, float2, float2>(y32, z32, h->U32[3], h->dir[3].n, inner[3], outer[3], 0,
-                                                       nullptr, nullptr, done, st, h->mp_cfg[3])));
+      STST_TRY((launch_modeprod<float, float2, float2>(y32, z32, h->U32[3], h->dir[3].n, inner[3], outer[3], 0, none,
+                                                       done, st, h->mp_cfg[3])));
       STST_TRY(time_solve<float>(h, (void *)z32, done, st));
-      STST_TRY((launch_modeprod<float, float2, float2>(z32, y32, h->U32[3], h->dir[3].n, inner[3], outer[3], 1,
-                                                       nullptr, nullptr, done, st, h->mp_cfg[3])));
+      STST_TRY((launch_modeprod<float, float2, float2>(z32, y32, h->U32[3], h->dir[3].n, inner[3], outer[3], 1, none,
+                                                       done, st, h->mp_cfg[3])));
     } else {
       STST_TRY(time_solve<float>(h, (void *)y32, done, st));
     }
-    if (out32)
-      return launch_fd2d<float2, float2>(y32, (float2 *)out32, h, 1, (const float2 *)dotvec, dot_partials, done, st,
-                                         S);
-    return launch_fd2d<float2, double2>(y32, (double2 *)s, h, 1, (const double2 *)dotvec, dot_partials, done, st, S);
+    if (out32) return launch_fd2d<float2, float2>(y32, (float2 *)out32, h, 1, ed, done, st, S);
+    return launch_fd2d<float2, double2>(y32, (double2 *)s, h, 1, ed, done, st, S);
   }
   float2 *bufs[2] = {(float2 *)bufA, (float2 *)bufB};
   int cur = 0;
@@ -1364,14 +1344,14 @@ int fd_apply(stst_problem *h, const double *r, double *s, int precision, const v
     if (l == 1) {
       if (in32) {
         STST_TRY((launch_modeprod<float, float2, float2>((const float2 *)in32, dst, h->U32[l], h->dir[l].n, inner[l],
-                                                         outer[l], 0, nullptr, nullptr, done, st, h->mp_cfg[l])));
+                                                         outer[l], 0, none, done, st, h->mp_cfg[l])));
       } else {
         STST_TRY((launch_modeprod<float, double2, float2>((const double2 *)r, dst, h->U32[l], h->dir[l].n, inner[l],
-                                                          outer[l], 0, nullptr, nullptr, done, st, h->mp_cfg[l])));
+                                                          outer[l], 0, none, done, st, h->mp_cfg[l])));
       }
     } else {
-      STST_TRY((launch_modeprod<float, float2, float2>(src32, dst, h->U32[l], h->dir[l].n, inner[l], outer[l], 0,
-                                                       nullptr, nullptr, done, st, h->mp_cfg[l])));
+      STST_TRY((launch_modeprod<float, float2, float2>(src32, dst, h->U32[l], h->dir[l].n, inner[l], outer[l], 0, none,
+                                                       done, st, h->mp_cfg[l])));
     }
     src32 = dst;
     cur ^= 1;
@@ -1381,17 +1361,15 @@ int fd_apply(stst_problem *h, const double *r, double *s, int precision, const v
     if (l == 1) {
       if (out32) {
         STST_TRY((launch_modeprod<float, float2, float2>(src32, (float2 *)out32, h->U32[l], h->dir[l].n, inner[l],
-                                                         outer[l], 1, (const float2 *)dotvec, dot_partials, done, st,
-                                                         h->mp_cfg[l])));
+                                                         outer[l], 1, ed, done, st, h->mp_cfg[l])));
       } else {
         STST_TRY((launch_modeprod<float, float2, double2>(src32, (double2 *)s, h->U32[l], h->dir[l].n, inner[l],
-                                                          outer[l], 1, (const double2 *)dotvec, dot_partials, done,
-                                                          st, h->mp_cfg[l])));
+                                                          outer[l], 1, ed, done, st, h->mp_cfg[l])));
       }
     } else {
       float2 *dst = bufs[cur];
-      STST_TRY((launch_modeprod<float, float2, float2>(src32, dst, h->U32[l], h->dir[l].n, inner[l], outer[l], 1,
-                                                       nullptr, nullptr, done, st, h->mp_cfg[l])));
+      STST_TRY((launch_modeprod<float, float2, float2>(src32, dst, h->U32[l], h->dir[l].n, inner[l], outer[l], 1, none,
+                                                       done, st, h->mp_cfg[l])));
       src32 = dst;
       cur ^= 1;
     }
@@ -1524,17 +1502,13 @@ static int tune_fd2d(stst_problem *h) {
     if (S > 0 && !fd2d_split_ok(h->dir[1].n, h->dir[2].n, S)) continue;
     auto run = [&]() -> int {
       if (S > 0) {
-        STST_TRY((launch_fd2d<float2, float2>(X, Y, h, 0, nullptr, nullptr, nullptr, st, S)));
-        return launch_fd2d<float2, float2>(Y, X, h, 1, nullptr, nullptr, nullptr, st, S);
+        STST_TRY((launch_fd2d<float2, float2>(X, Y, h, 0, EpiDot(), nullptr, st, S)));
+        return launch_fd2d<float2, float2>(Y, X, h, 1, EpiDot(), nullptr, st, S);
       }
-      STST_TRY((launch_modeprod<float, float2, float2>(X, Z, h->U32[1], h->dir[1].n, inner[1], outer[1], 0, nullptr,
-                                                       nullptr, nullptr, st, h->mp_cfg[1])));
-      STST_TRY((launch_modeprod<float, float2, float2>(Z, Y, h->U32[2], h->dir[2].n, inner[2], outer[2], 0, nullptr,
-                                                       nullptr, nullptr, st, h->mp_cfg[2])));
-      STST_TRY((launch_modeprod<float, float2, float2>(Y, Z, h->U32[2], h->dir[2].n, inner[2], outer[2], 1, nullptr,
-                                                       nullptr, nullptr, st, h->mp_cfg[2])));
-      return launch_modeprod<float, float2, float2>(Z, X, h->U32[1], h->dir[1].n, inner[1], outer[1], 1, nullptr,
-                                                    nullptr, nullptr, st, h->mp_cfg[1]);
+      STST_TRY((launch_modeprod<float, float2, float2>(X, Z, h->U32[1], h->dir[1].n, inner[1], outer[1], 0, EpiDot(), nullptr, st, h->mp_cfg[1])));
+      STST_TRY((launch_modeprod<float, float2, float2>(Z, Y, h->U32[2], h->dir[2].n, inner[2], outer[2], 0, EpiDot(), nullptr, st, h->mp_cfg[2])));
+      STST_TRY((launch_modeprod<float, float2, float2>(Y, Z, h->U32[2], h->dir[2].n, inner[2], outer[2], 1, EpiDot(), nullptr, st, h->mp_cfg[2])));
+      return launch_modeprod<float, float2, float2>(Z, X, h->U32[1], h->dir[1].n, inner[1], outer[1], 1, EpiDot(), nullptr, st, h->mp_cfg[1]);
     };
     for (int w = 0; w < 2 && status == STST_OK; ++w) status = run();
     cudaEventRecord(e0, st);

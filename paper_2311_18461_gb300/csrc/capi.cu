@@ -553,7 +553,7 @@ int create_impl(stst_problem *h, int d, const int *n_el, const int *p, double T,
   const size_t vb = sizeof(double2) * (size_t)h->N_dof;
   double **ws[] = {&h->w_x, &h->w_r, &h->w_z, &h->w_zold, &h->w_p, &h->w_q, &h->w_f, &h->w_t1, &h->w_t2};
   for (double **w : ws) STST_TRY(alloc((void **)w, vb));
-  STST_TRY(alloc((void **)&h->partials, sizeof(double) * 4 * STST_MAXPART));
+  STST_TRY(alloc((void **)&h->partials, sizeof(double) * PS_COUNT * STST_MAXPART));
   STST_TRY(alloc((void **)&h->ctl, sizeof(PcgCtl)));
   STST_TRY(alloc((void **)&h->ctl2, sizeof(PcgCtl)));
   float **vs[] = {&h->v_d, &h->v_r, &h->v_z, &h->v_p, &h->v_q};
@@ -1004,7 +1004,7 @@ int stst_apply_prec(stst_handle h, const double *r, double *s) {
   if (!r || !s) return STST_ERR_ARG;
   if (!h->fd_ready) return STST_ERR_STATE;
   int prec = h->prec_mode;  // STST_PREC_* equals fd_apply's precision code
-  return fd_apply(h, r, s, prec, nullptr, nullptr, nullptr, h->w_t1, h->w_t2);
+  return fd_apply(h, r, s, prec, EpiDot(), nullptr, h->w_t1, h->w_t2);
 }
 
 int stst_rhs(stst_handle h, const double *f_qp, const double *u0_qp, double *rhs, double *c0) {

@@ -10,6 +10,7 @@
 #define STST_MAXD 3
 #define STST_MAXP 8
 #define STST_MAXN_SPACE 128
+#define STST_MAXPART 65536  // per-CTA partial sums per component (the grids of the reducing kernels stay below)
 
 // ---- error handling -------------------------------------------------------------------------
 #define STST_CUDA(call)                                   \
@@ -78,18 +79,81 @@ struct Plan {
   int n_levels = 0;
 };
 
+// ---- inner products in the epilogue of a preconditioner application -------------------------------
+// The last kernel of s = P^{-1} r sums, per output element v = s[idx] (complex), the products the CG
+// update needs next, so no kernel reads s again for them:
+//   component 0: Re sum conj(a) v                (a = r: <r, s> of the plain CG, real for Hermitian P)
+//   component 1: Im sum conj(a) v                (cplx: the complex <s, r>)
+//   components 2, 3: Re, Im sum conj(b) v        (cplx with b: <s, b>, b = A p for the flexible CG)
+// a and b have the output's type (double2 or float2). A CTA writes component c of its sums to
+// part[c * STST_MAXPART + slot]; the slot is the CTA's index in its grid.
+struct EpiDot {
+  const void *a = nullptr, *b = nullptr;
+  double *part = nullptr;
+  int cplx = 0;
+  __host__ __device__ int ncomp() const { return !part ? 0 : (!cplx ? 1 : (b ? 4 : 2)); }
+};
+
+template <typename TO>
+__device__ __forceinline__ void epi_dot_acc(double (&acc)[4], const EpiDot &ed, long long idx, double vx, double vy) {
+  const TO av = ((const TO *)ed.a)[idx];
+  acc[0] += (double)av.x * vx + (double)av.y * vy;
+  if (ed.cplx) {
+    acc[1] += (double)av.x * vy - (double)av.y * vx;
+    if (ed.b) {
+      const TO bv = ((const TO *)ed.b)[idx];
+      acc[2] += (double)bv.x * vx + (double)bv.y * vy;
+      acc[3] += (double)bv.x * vy - (double)bv.y * vx;
+    }
+  }
+}
+
+// Deterministic sum over the CTA (blockDim.x a multiple of 32, <= 1024); valid in thread 0.
+__device__ __forceinline__ double epi_block_sum(double v, double *sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = (l < (int)(blockDim.x >> 5)) ? sh[l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  return t;
+}
+
+// Every thread of the CTA calls this (it synchronizes); sh holds 32 doubles.
+__device__ __forceinline__ void epi_dot_store(const double (&acc)[4], const EpiDot &ed, long long slot, double *sh) {
+  const int nc = ed.ncomp();
+  for (int c = 0; c < nc; ++c) {
+    const double t = epi_block_sum(acc[c], sh);
+    if (threadIdx.x == 0) ed.part[(long long)c * STST_MAXPART + slot] = t;
+  }
+}
+
 // ---- PCG control block (device) ---------------------------------------------------------------
 // Tile of the SIMT mode product: cpt columns per thread (8 cpt per CTA), rpt groups of 32 output rows.
 struct MpCfg {
   int cpt, rpt;
 };
 
+// Plain CG (FP64 preconditioner): rho = <r, z> real, alpha = rho / pq, beta = rho_new / rho.
+// Flexible CG (low-precision preconditioners, flexible = 1): complex alpha = sigma / pq with
+// sigma = <r, p>, complex beta = -<z, A p> / pq (directions A-orthogonalized), sigma_new = <r, z> +
+// conj(beta) <r, p_old>.
 struct PcgCtl {
-  double ff, rr, rho, pq, alpha, beta, rz_old, tol2;
+  double ff, rr, rho, pq, alpha, beta, tol2;
+  double sig_re, sig_im, alpha_im, beta_im;
   int it, maxit, done, status;
   int flexible;
   int x0_zero;  // 1 until a nonzero entry of the initial guess is seen (the host and the batch set it to 1)
 };
+
+// Slots of the handle's partial-sum buffer (units of STST_MAXPART doubles): the preconditioner's epilogue
+// components (EpiDot, up to 4), ||r||^2, <r_new, p> (flexible CG: real and imaginary part, two halves
+// used by alternate iterations; ||f||^2 at the start), <p, A p>.
+enum { PS_Z = 0, PS_RR = 4, PS_RP = 5, PS_PQ = 9, PS_COUNT = 10 };
 
 // ---- handle -------------------------------------------------------------------------------------
 struct stst_problem {
@@ -189,7 +253,6 @@ struct ApiScope {
 };
 
 #define STST_MAGIC 0x57575354
-#define STST_MAXPART 65536
 
 // ---- kernels / launchers (defined in the .cu files) ------------------------------------------
 int launch_assemble_band(int kind, int p, int n_el, double len, int nq, int off, int n_rows, int n_cols,
@@ -210,10 +273,10 @@ int fd_setup_launch(stst_problem *h);
 int pcg_init(stst_problem *h);
 int pcg_body(stst_problem *h, cudaGraphConditionalHandle cond, int use_cond);
 int reduction_grid(long long total);
-// dotvec: FP64 vector (double2) when the output is FP64, FP32 (float2) when out32 is given.
-int fd_apply(stst_problem *h, const double *r, double *s, int precision, const void *dotvec, double *dot_partials,
-             const int *done, void *f32_scratch_a, void *f32_scratch_b, float *out32 = nullptr,
-             const float *in32 = nullptr);
+// ed: inner products of the output taken by the last kernel (EpiDot); its vectors are FP64 (double2)
+// when the output is FP64, FP32 (float2) when out32 is given.
+int fd_apply(stst_problem *h, const double *r, double *s, int precision, const EpiDot &ed, const int *done,
+             void *f32_scratch_a, void *f32_scratch_b, float *out32 = nullptr, const float *in32 = nullptr);
 int rhs_compute(stst_problem *h, const double *f_qp, const double *u0_qp, double *rhs, double *c0);
 int rhs_lift_compute(stst_problem *h, const double *f_qp, const double *u_qp, double *rhs, double *xd);
 
@@ -241,7 +304,7 @@ bool fd2d_fits(const stst_problem *h);
 int launch_u_to_bf16(const double *U, int n, __nv_bfloat16 *out, cudaStream_t s);
 template <typename TI, typename TO>
 int launch_modeprod_tc(const TI *X, TO *Y, const __nv_bfloat16 *Bk, long long lo_stride, int split, int n,
-                       long long inner, long long outer, const TO *dotvec, double *dot_partials, const int *done,
-                       int *errflag, cudaStream_t s);
+                       long long inner, long long outer, const EpiDot &ed, const int *done, int *errflag,
+                       cudaStream_t s);
 int tc_partials_count(long long ncols);
 inline int pad16(int n) { return (n + 15) / 16 * 16; }

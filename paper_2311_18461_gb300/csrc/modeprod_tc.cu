@@ -62,7 +62,7 @@ template <typename TI, typename TO, int SPLIT>
 __global__ void __launch_bounds__(128) k_modeprod_tc(const TI *__restrict__ X, TO *__restrict__ Y,
                                                      const __nv_bfloat16 *__restrict__ Bk, long long lo_stride, int n,
                                                      int np, int kp, long long inner, long long ncols,
-                                                     const TO *__restrict__ dotvec, double *dot_partials,
+                                                     const EpiDot ed,
                                                      const int *done, int *errflag) {
   if (done && *done) return;
   extern __shared__ __align__(1024) unsigned char tc_smem[];
@@ -193,7 +193,9 @@ __global__ void __launch_bounds__(128) k_modeprod_tc(const TI *__restrict__ X, T
   ok = __syncthreads_and(ok);  // one decision for the whole CTA (tcgen05.ld needs whole warps)
   if (!ok && tid == 0) atomicOr(errflag, 4);
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-  double dacc = 0.0;
+  // this thread holds part (0 real, 1 imaginary) of each output v; conj(a) v = (a.x v.x + a.y v.y) +
+  // i (a.x v.y - a.y v.x), so the real part takes a[part] v and the imaginary part (-1)^(1-part) a[1-part] v
+  double dacc[4] = {0.0, 0.0, 0.0, 0.0};
   if (ok) {
     const int m = tid;  // TMEM lane = GEMM row; warp w owns lanes 32w..32w+31
     const int cc = m >> 1, part = m & 1;
@@ -216,12 +218,21 @@ __global__ void __launch_bounds__(128) k_modeprod_tc(const TI *__restrict__ X, T
           if (j < n) {
             const long long idx = (o * n + j) * inner + c;
             const float v = __uint_as_float(r[q]);
-            if constexpr (sizeof(TO) == 16) {
-              ((double *)Y)[2 * idx + part] = (double)v;
-              if (dotvec) dacc += ((const double *)dotvec)[2 * idx + part] * (double)v;
-            } else {
-              ((float *)Y)[2 * idx + part] = v;
-              if (dotvec) dacc += (double)((const float *)dotvec)[2 * idx + part] * (double)v;
+            if constexpr (sizeof(TO) == 16) ((double *)Y)[2 * idx + part] = (double)v;
+            else ((float *)Y)[2 * idx + part] = v;
+            if (ed.part) {
+              using R = decltype(TO().x);
+              const R *a = (const R *)ed.a + 2 * idx;
+              const double sgn = part ? 1.0 : -1.0;
+              dacc[0] += (double)a[part] * (double)v;
+              if (ed.cplx) {
+                dacc[1] += sgn * (double)a[1 - part] * (double)v;
+                if (ed.b) {
+                  const R *b = (const R *)ed.b + 2 * idx;
+                  dacc[2] += (double)b[part] * (double)v;
+                  dacc[3] += sgn * (double)b[1 - part] * (double)v;
+                }
+              }
             }
           }
         }
@@ -234,43 +245,37 @@ __global__ void __launch_bounds__(128) k_modeprod_tc(const TI *__restrict__ X, T
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;\n" ::"r"(tmem));
   }
-  if (dot_partials) {
-    // block reduction (4 warps)
-    for (int off = 16; off > 0; off >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, off);
-    if ((tid & 31) == 0) sh[tid >> 5] = dacc;
-    __syncthreads();
-    if (tid == 0) dot_partials[blockIdx.x] = sh[0] + sh[1] + sh[2] + sh[3];
-  }
+  if (ed.part) epi_dot_store(dacc, ed, blockIdx.x, sh);
 }
 
 int tc_partials_count(long long ncols) { return grid_for(ncols, 64); }
 
 template <typename TI, typename TO>
 int launch_modeprod_tc(const TI *X, TO *Y, const __nv_bfloat16 *Bk, long long lo_stride, int split, int n,
-                       long long inner, long long outer, const TO *dotvec, double *dot_partials, const int *done,
-                       int *errflag, cudaStream_t s) {
+                       long long inner, long long outer, const EpiDot &ed, const int *done, int *errflag,
+                       cudaStream_t s) {
   const long long ncols = inner * outer;
   const int np = (n + 15) / 16 * 16, kp = np;
   const int grid = grid_for(ncols, 64);
-  if (dot_partials && grid > STST_MAXPART) return STST_ERR_ARG;
+  if (ed.part && grid > STST_MAXPART) return STST_ERR_ARG;
   // BF16 operands (high, and low for the split) + the FP32 staging tile of 64 complex columns
   const size_t sm = (size_t)(split == 3 ? 2 : 1) * (128 + np) * kp * sizeof(__nv_bfloat16) +
                     (size_t)n * 64 * sizeof(float2);
   STST_PROF(split == 3 ? "modeprod_bf16x3_tc" : "modeprod_bf16_tc", s);
   if (split == 3) {
     STST_TRY(ensure_dyn_smem((const void *)k_modeprod_tc<TI, TO, 3>, sm));
-    k_modeprod_tc<TI, TO, 3><<<grid, 128, sm, s>>>(X, Y, Bk, lo_stride, n, np, kp, inner, ncols, dotvec,
-                                                   dot_partials, done, errflag);
+    k_modeprod_tc<TI, TO, 3><<<grid, 128, sm, s>>>(X, Y, Bk, lo_stride, n, np, kp, inner, ncols, ed, done,
+                                                   errflag);
   } else {
     STST_TRY(ensure_dyn_smem((const void *)k_modeprod_tc<TI, TO, 1>, sm));
-    k_modeprod_tc<TI, TO, 1><<<grid, 128, sm, s>>>(X, Y, Bk, lo_stride, n, np, kp, inner, ncols, dotvec,
-                                                   dot_partials, done, errflag);
+    k_modeprod_tc<TI, TO, 1><<<grid, 128, sm, s>>>(X, Y, Bk, lo_stride, n, np, kp, inner, ncols, ed, done,
+                                                   errflag);
   }
   STST_CUDA(cudaGetLastError());
   return STST_OK;
 }
 
-template int launch_modeprod_tc<double2, float2>(const double2 *, float2 *, const __nv_bfloat16 *, long long, int, int, long long, long long, const float2 *, double *, const int *, int *, cudaStream_t);
-template int launch_modeprod_tc<float2, float2>(const float2 *, float2 *, const __nv_bfloat16 *, long long, int, int, long long, long long, const float2 *, double *, const int *, int *, cudaStream_t);
-template int launch_modeprod_tc<float2, double2>(const float2 *, double2 *, const __nv_bfloat16 *, long long, int, int, long long, long long, const double2 *, double *, const int *, int *, cudaStream_t);
-template int launch_modeprod_tc<double2, double2>(const double2 *, double2 *, const __nv_bfloat16 *, long long, int, int, long long, long long, const double2 *, double *, const int *, int *, cudaStream_t);
+template int launch_modeprod_tc<double2, float2>(const double2 *, float2 *, const __nv_bfloat16 *, long long, int, int, long long, long long, const EpiDot &, const int *, int *, cudaStream_t);
+template int launch_modeprod_tc<float2, float2>(const float2 *, float2 *, const __nv_bfloat16 *, long long, int, int, long long, long long, const EpiDot &, const int *, int *, cudaStream_t);
+template int launch_modeprod_tc<float2, double2>(const float2 *, double2 *, const __nv_bfloat16 *, long long, int, int, long long, long long, const EpiDot &, const int *, int *, cudaStream_t);
+template int launch_modeprod_tc<double2, double2>(const double2 *, double2 *, const __nv_bfloat16 *, long long, int, int, long long, long long, const EpiDot &, const int *, int *, cudaStream_t);

@@ -10,8 +10,6 @@
 
 int fd_partials_count(stst_problem *h);
 
-enum { PART_A = 0, PART_B = 1, PART_C = 2, PART_D = 3 };
-
 __device__ __forceinline__ double block_sum_d(double v, double *sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -40,6 +38,60 @@ __device__ double reduce_partials(const double *part, int nparts, double *sh) {
   return r;
 }
 
+// Reductions for the FP64-poor GB300 (2 FP64 FMA per clock per SM): a butterfly shuffle tree makes all
+// 32 lanes of every warp do every addition, so sums that every CTA of a 304-CTA kernel repeats cost as
+// much FP64 issue as the vector arithmetic itself. Here warp c alone sums component c (NC <= number of
+// warps); the other warps only load and store. The order of the additions is fixed: deterministic.
+
+// NC sums over the CTA of one value per thread, valid in every thread on return. sh: at least
+// NC * blockDim.x + NC doubles (checked against 256 threads at compile time; the callers run 256).
+template <int NC, int SZ>
+__device__ __forceinline__ void block_sum_all(double (&v)[NC], double (&sh)[SZ]) {
+  static_assert(SZ >= NC * 256 + NC, "block_sum_all: shared buffer too small for 256 threads");
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nt = blockDim.x;
+  __syncthreads();  // sh may still be read by an earlier reduction
+#pragma unroll
+  for (int c = 0; c < NC; ++c) sh[c * nt + threadIdx.x] = v[c];
+  __syncthreads();
+  if (w < NC) {
+    double t = 0.0;
+    for (int i = l; i < nt; i += 32) t += sh[w * nt + i];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (l == 0) sh[NC * nt + w] = t;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < NC; ++c) v[c] = sh[NC * nt + c];
+}
+
+// The sums of NC sets of per-CTA partials (set c: part[c][0 .. n[c])), warp c summing set c; valid in
+// every thread on return. sh: at least 33 doubles.
+template <int NC, int SZ>
+__device__ __forceinline__ void reduce_partials_all(const double *const (&part)[NC], const int (&n)[NC],
+                                                    double (&out)[NC], double (&sh)[SZ]) {
+  static_assert(SZ >= 33 && NC <= 8, "reduce_partials_all: shared buffer too small or too many sets");
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();  // sh may still be read by an earlier reduction
+  if (w < NC) {
+    const double *pc = part[0];
+    int nc = n[0];
+#pragma unroll
+    for (int c = 1; c < NC; ++c)
+      if (w == c) {
+        pc = part[c];
+        nc = n[c];
+      }
+    double t = 0.0;
+#pragma unroll 4
+    for (int i = l; i < nc; i += 32) t += pc[i];
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (l == 0) sh[w] = t;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < NC; ++c) out[c] = sh[c];
+}
+
 template <typename T>
 __global__ void k_norm2(const T *__restrict__ v, long long n, double *part) {
   __shared__ double sh[32];
@@ -52,20 +104,25 @@ __global__ void k_norm2(const T *__restrict__ v, long long n, double *part) {
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
-// init: ff, rr, rho from partials; done if converged already
-__global__ void k_pcg_init(PcgCtl *ctl, const double *pf, int nf, const double *pr, int nr, const double *prz, int nrz) {
+// init: ff, rr and rho (plain) or sigma = <r, p> = <r, z> (flexible) from partials; done if converged.
+// The preconditioner's epilogue summed conj(r) z, i.e. conj(<r, z>) (component 1: its imaginary part).
+__global__ void k_pcg_init(PcgCtl *ctl, const double *pf, int nf, const double *pr, int nr, const double *pz, int nz) {
   __shared__ double sh[32];
-  double ff = reduce_partials(pf, nf, sh);
-  double rr = reduce_partials(pr, nr, sh);
-  double rz = reduce_partials(prz, nrz, sh);
+  const int flexible = ctl->flexible;
+  const double ff = reduce_partials(pf, nf, sh);
+  const double rr = reduce_partials(pr, nr, sh);
+  const double rz = reduce_partials(pz, nz, sh);
+  const double rz_im = flexible ? -reduce_partials(pz + STST_MAXPART, nz, sh) : 0.0;
   if (threadIdx.x == 0) {
     ctl->ff = ff;
     ctl->rr = rr;
     ctl->rho = rz;
+    ctl->sig_re = rz;
+    ctl->sig_im = rz_im;
     ctl->it = 0;
     ctl->status = STST_OK;
     ctl->done = (ff == 0.0 || rr <= ctl->tol2 * ff) ? 1 : 0;
-    if (!ctl->done && !(rz > 0.0 && isfinite(rz))) { ctl->done = 1; ctl->status = STST_BREAKDOWN; }
+    if (!ctl->done && !(rz > 0.0 && isfinite(rz) && isfinite(rz_im))) { ctl->done = 1; ctl->status = STST_BREAKDOWN; }
   }
 }
 
@@ -88,20 +145,25 @@ int update_grid(long long n) {
   return g < 1 ? 1 : (int)g;
 }
 
-// alpha = rho / <p, q> (every CTA reduces the same partials in the same order; CTA 0 records it),
-// then x += alpha p; r -= alpha q; partials of ||r||^2 and (flexible) Re<r, z_old>
-// rho = <r, z> is reduced from the partials of the latest preconditioner application (prz_in), so no
-// CTA of this kernel reads a scalar that another CTA of it writes.
-template <typename T>
+// pq = <p, q> with q = A p (every CTA reduces the same partials in the same order; CTA 0 records it).
+// Plain (FLEX false): alpha = rho / pq, rho = <r, z> reduced from the latest preconditioner application
+// (pz, component 0). Flexible: alpha = sigma / pq, complex, sigma = <r, p>; at the first iteration the
+// start kernel recorded it, afterwards sigma = <r, z> + conj(beta) <r, p_old> from the preconditioner's
+// epilogue (pz components 0, 1: conj(<r, z>)), this kernel's previous partials of <r, p_old> (prp) and
+// the beta recorded by k_update_p. Then x += alpha p, r -= alpha q, partials of ||r||^2 (prr) and,
+// flexible, of conj(p) r_new = <r_new, p>. No CTA of this kernel reads a scalar or partial that another
+// CTA of it writes: the <r, p_old> partials are double-buffered by iteration parity (iteration k writes
+// half k & 1 of prp and reads the other half, written by iteration k - 1).
+template <typename T, bool FLEX>
 __global__ void __launch_bounds__(256) k_update_xr(T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p,
-                                                   const T *__restrict__ q, const T *__restrict__ zold, PcgCtl *ctl,
-                                                   long long n, double *prr, double *prz, const double *ppq, int npq,
-                                                   const double *prz_in, int nrz_in) {
+                                                   const T *__restrict__ q, PcgCtl *ctl, long long n, double *prr,
+                                                   double *prp, int nrp, const double *ppq, int npq,
+                                                   const double *pz, int nz) {
   if (ctl->done) return;
-  __shared__ double sh[32];
+  __shared__ double sh[3 * 256 + 3];
   const long long stride = (long long)gridDim.x * 256 * UPT;
   long long i0 = (long long)blockIdx.x * 256 * UPT + threadIdx.x;
-  T pv[UPT], qv[UPT], xv[UPT], rv[UPT], zv[UPT];
+  T pv[UPT], qv[UPT], xv[UPT], rv[UPT];
   auto load = [&](long long base) {
 #pragma unroll
     for (int u = 0; u < UPT; ++u) {
@@ -111,59 +173,101 @@ __global__ void __launch_bounds__(256) k_update_xr(T *__restrict__ x, T *__restr
         qv[u] = q[i];
         xv[u] = x[i];
         rv[u] = r[i];
-        if (zold) zv[u] = zold[i];
       }
     }
   };
   if (i0 < n) load(i0);
-  const double pq = reduce_partials(ppq, npq, sh);
-  const double rho = reduce_partials(prz_in, nrz_in, sh);
-  const bool bad = !(pq > 0.0) || !isfinite(pq);
-  const double alpha = bad ? 0.0 : rho / pq;
+  double pq, num_re, num_im = 0.0;
+  double *prp_out = prp;
+  if constexpr (FLEX) {
+    const int it = ctl->it;
+    const double *prp_in = prp + ((it + 1) & 1) * 2 * STST_MAXPART;
+    prp_out = prp + (it & 1) * 2 * STST_MAXPART;
+    const double *sp[5] = {ppq, pz, pz + STST_MAXPART, prp_in, prp_in + STST_MAXPART};
+    const int sn[5] = {npq, it ? nz : 0, it ? nz : 0, it ? nrp : 0, it ? nrp : 0};
+    double v[5];
+    reduce_partials_all(sp, sn, v, sh);
+    pq = v[0];
+    if (it == 0) {
+      num_re = ctl->sig_re;
+      num_im = ctl->sig_im;
+    } else {
+      // <r, z> = conj(e), e = (v[1], v[2]); conj(beta) tau = (b_re - i b_im)(t_re + i t_im)
+      const double b_re = ctl->beta, b_im = ctl->beta_im;
+      num_re = v[1] + (b_re * v[3] + b_im * v[4]);
+      num_im = -v[2] + (b_re * v[4] - b_im * v[3]);
+    }
+  } else {
+    const double *sp[2] = {ppq, pz};
+    const int sn[2] = {npq, nz};
+    double v[2];
+    reduce_partials_all(sp, sn, v, sh);
+    pq = v[0];
+    num_re = v[1];
+  }
+  const bool bad = !(pq > 0.0) || !isfinite(pq) || !isfinite(num_re) || !isfinite(num_im);
+  const double a_re = bad ? 0.0 : num_re / pq, a_im = bad ? 0.0 : num_im / pq;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ctl->pq = pq;
-    ctl->rho = rho;
-    ctl->alpha = alpha;
+    ctl->rho = num_re;
+    ctl->sig_re = num_re;
+    ctl->sig_im = num_im;
+    ctl->alpha = a_re;
+    ctl->alpha_im = a_im;
     if (bad) ctl->status = STST_BREAKDOWN;  // the check kernel ends the loop
   }
-  double arr = 0.0, arz = 0.0;
+  double arr = 0.0, arp_re = 0.0, arp_im = 0.0;
   for (; i0 < n; i0 += stride) {
 #pragma unroll
     for (int u = 0; u < UPT; ++u) {
       const long long i = i0 + 256 * u;
       if (i < n) {
-        xv[u].x += alpha * pv[u].x;
-        xv[u].y += alpha * pv[u].y;
-        rv[u].x -= alpha * qv[u].x;
-        rv[u].y -= alpha * qv[u].y;
+        if constexpr (FLEX) {
+          xv[u].x += a_re * pv[u].x - a_im * pv[u].y;
+          xv[u].y += a_re * pv[u].y + a_im * pv[u].x;
+          rv[u].x -= a_re * qv[u].x - a_im * qv[u].y;
+          rv[u].y -= a_re * qv[u].y + a_im * qv[u].x;
+        } else {
+          xv[u].x += a_re * pv[u].x;
+          xv[u].y += a_re * pv[u].y;
+          rv[u].x -= a_re * qv[u].x;
+          rv[u].y -= a_re * qv[u].y;
+        }
         x[i] = xv[u];
         r[i] = rv[u];
         arr += (double)rv[u].x * rv[u].x + (double)rv[u].y * rv[u].y;
-        if (zold) arz += (double)zv[u].x * rv[u].x + (double)zv[u].y * rv[u].y;
+        if constexpr (FLEX) {
+          arp_re += (double)pv[u].x * rv[u].x + (double)pv[u].y * rv[u].y;
+          arp_im += (double)pv[u].x * rv[u].y - (double)pv[u].y * rv[u].x;
+        }
       }
     }
     if (i0 + stride < n) load(i0 + stride);
   }
-  double s = block_sum_d(arr, sh);
-  if (threadIdx.x == 0) prr[blockIdx.x] = s;
-  if (zold) {
-    double t = block_sum_d(arz, sh);
-    if (threadIdx.x == 0) prz[blockIdx.x] = t;
+  if constexpr (FLEX) {
+    double v[3] = {arr, arp_re, arp_im};
+    block_sum_all(v, sh);
+    if (threadIdx.x == 0) {
+      prr[blockIdx.x] = v[0];
+      prp_out[blockIdx.x] = v[1];
+      prp_out[STST_MAXPART + blockIdx.x] = v[2];
+    }
+  } else {
+    double v[1] = {arr};
+    block_sum_all(v, sh);
+    if (threadIdx.x == 0) prr[blockIdx.x] = v[0];
   }
 }
 
 // control: count the iteration, test ||r|| <= tol ||f||, maxit; set the WHILE condition.
-__global__ void k_pcg_check(PcgCtl *ctl, const double *prr, int nrr, const double *prz, int nrz,
-                            cudaGraphConditionalHandle cond, int use_cond) {
+__global__ void k_pcg_check(PcgCtl *ctl, const double *prr, int nrr, cudaGraphConditionalHandle cond, int use_cond) {
   __shared__ double sh[32];
   int was_done = ctl->done;
   double rr = reduce_partials(prr, nrr, sh);
-  double rz = (prz && nrz > 0) ? reduce_partials(prz, nrz, sh) : 0.0;
   if (threadIdx.x == 0) {
     if (!was_done) {
       ctl->it += 1;
       ctl->rr = rr;
-      ctl->rz_old = rz;
       if (ctl->status == STST_BREAKDOWN) {
         ctl->done = 1;
       } else if (!isfinite(rr)) {
@@ -182,14 +286,16 @@ __global__ void k_pcg_check(PcgCtl *ctl, const double *prr, int nrr, const doubl
   }
 }
 
-// beta from the new <r, z> partials (Fletcher-Reeves, or Polak-Ribiere when flexible), p = z + beta p.
-// rho_old (written by k_update_xr) and rz_old (written by the check kernel) come from earlier
-// kernels; this kernel writes no scalar that its own CTAs read.
-template <typename T>
+// p = z + beta p; CTA 0 records beta.
+// Plain: beta = rho_new / rho (Fletcher-Reeves with the preconditioner), rho_new = <r, z> from the
+// epilogue of the preconditioner application (component 0); rho was recorded by k_update_xr.
+// Flexible: beta = -<z, q> / pq with q = A p_old (epilogue components 2, 3 hold sum conj(q) z = <z, q>),
+// which makes the new direction A-orthogonal to the old one whatever the preconditioner did.
+template <typename T, bool FLEX>
 __global__ void __launch_bounds__(256) k_update_p(T *__restrict__ p, const T *__restrict__ z, PcgCtl *ctl, long long n,
-                                                  const double *prz, int nrz) {
+                                                  const double *pz, int nz) {
   if (ctl->done) return;
-  __shared__ double sh[32];
+  __shared__ double sh[33];
   const long long stride = (long long)gridDim.x * 256 * UPT;
   long long i0 = (long long)blockIdx.x * 256 * UPT + threadIdx.x;
   T pv[UPT], zv[UPT];
@@ -204,51 +310,94 @@ __global__ void __launch_bounds__(256) k_update_p(T *__restrict__ p, const T *__
     }
   };
   if (i0 < n) load(i0);
-  const double rho_old = ctl->rho, rz_old = ctl->rz_old;
-  const int flexible = ctl->flexible;
-  const double rho_new = reduce_partials(prz, nrz, sh);
-  const bool bad = !(rho_new > 0.0) || !isfinite(rho_new);
-  const double beta = bad ? 0.0 : (flexible ? (rho_new - rz_old) / rho_old : rho_new / rho_old);
+  double b_re, b_im = 0.0;
+  bool bad;
+  if constexpr (FLEX) {
+    const double pq = ctl->pq;
+    const double *gp[2] = {pz + 2 * STST_MAXPART, pz + 3 * STST_MAXPART};
+    const int gn[2] = {nz, nz};
+    double g[2];
+    reduce_partials_all(gp, gn, g, sh);
+    b_re = -g[0] / pq;
+    b_im = -g[1] / pq;
+    bad = !isfinite(b_re) || !isfinite(b_im);
+  } else {
+    const double rho_old = ctl->rho;
+    const double *rp[1] = {pz};
+    const int rn[1] = {nz};
+    double rv[1];
+    reduce_partials_all(rp, rn, rv, sh);
+    const double rho_new = rv[0];
+    bad = !(rho_new > 0.0) || !isfinite(rho_new);
+    b_re = rho_new / rho_old;
+  }
+  if (bad) b_re = b_im = 0.0;
   if (bad && blockIdx.x == 0 && threadIdx.x == 0) ctl->status = STST_BREAKDOWN;
   for (; i0 < n; i0 += stride) {
 #pragma unroll
     for (int u = 0; u < UPT; ++u) {
       const long long i = i0 + 256 * u;
       if (i < n) {
-        pv[u].x = zv[u].x + beta * pv[u].x;
-        pv[u].y = zv[u].y + beta * pv[u].y;
+        const double px = pv[u].x, py = pv[u].y;
+        pv[u].x = zv[u].x + (b_re * px - b_im * py);
+        pv[u].y = zv[u].y + (b_re * py + b_im * px);
         p[i] = pv[u];
       }
     }
     if (i0 + stride < n) load(i0 + stride);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctl->beta = b_re;
+    ctl->beta_im = b_im;
   }
 }
 
 // ------------------------------------------------------------------------------------------------
 // FP64 PCG
 // ------------------------------------------------------------------------------------------------
-int pcg_body(stst_problem *h, cudaGraphConditionalHandle cond, int use_cond) {
+// The vectors of one PCG iteration: FP64 work vectors of the handle, or the FP32 ones of the inner solver.
+template <typename T>
+static int pcg_iteration(stst_problem *h, PcgCtl *ctl, T *x, T *r, T *z, T *p, T *q, int flexible, int fd_prec,
+                         cudaGraphConditionalHandle cond, int use_cond) {
   cudaStream_t st = h->stream;
   const long long N = h->N_dof;
   const int g = reduction_grid(N), gu = update_grid(N);
-  const int prec = h->prec_mode;  // STST_PREC_* equals fd_apply's precision code
   double *P = h->partials;
-  double *pA = P, *pB = P + STST_MAXPART, *pC = P + 2 * STST_MAXPART, *pD = P + 3 * STST_MAXPART;
-  const int *done = &h->ctl->done;
-  const int flexible = prec != 0;
-  const int nrz = fd_partials_count(h);
+  double *pZ = P + PS_Z * STST_MAXPART, *pRR = P + PS_RR * STST_MAXPART, *pRP = P + PS_RP * STST_MAXPART,
+         *pPQ = P + PS_PQ * STST_MAXPART;
+  const int *done = &ctl->done;
+  const int nz = fd_partials_count(h);
+  const bool f32 = sizeof(T) == sizeof(float2);
   // q = A p, partials <p, q>
-  STST_TRY(run_plan(h->sys_plan, h->w_p, h->w_q, 0, 0, nullptr, h->w_p, pD, done, st));
-  // alpha; x, r update (+ Re<r_new, z_old> for the flexible beta)
-  { STST_PROF("pcg_update_xr", st); k_update_xr<double2><<<gu, 256, 0, st>>>((double2 *)h->w_x, (double2 *)h->w_r, (const double2 *)h->w_p,
-                                          (const double2 *)h->w_q, flexible ? (const double2 *)h->w_z : nullptr,
-                                          h->ctl, N, pB, pC, pD, g, pA, nrz); }
-  { STST_PROF("pcg_scalar", st); k_pcg_check<<<1, 1024, 0, st>>>(h->ctl, pB, gu, flexible ? pC : nullptr, flexible ? gu : 0, cond, use_cond); }
-  // z = P^{-1} r, partials <r, z>
-  STST_TRY(fd_apply(h, h->w_r, h->w_z, prec, h->w_r, pA, done, h->w_t1, h->w_t2));
-  { STST_PROF("pcg_update_p", st); k_update_p<double2><<<gu, 256, 0, st>>>((double2 *)h->w_p, (const double2 *)h->w_z, h->ctl, N, pA, nrz); }
+  STST_TRY(run_plan(h->sys_plan, p, q, f32 ? 1 : 0, 0, nullptr, p, pPQ, done, st));
+  // alpha; x, r update (+ <r_new, p> for the flexible sigma)
+  {
+    STST_PROF("pcg_update_xr", st);
+    if (flexible) k_update_xr<T, true><<<gu, 256, 0, st>>>(x, r, p, q, ctl, N, pRR, pRP, gu, pPQ, g, pZ, nz);
+    else k_update_xr<T, false><<<gu, 256, 0, st>>>(x, r, p, q, ctl, N, pRR, pRP, gu, pPQ, g, pZ, nz);
+  }
+  { STST_PROF("pcg_scalar", st); k_pcg_check<<<1, 1024, 0, st>>>(ctl, pRR, gu, cond, use_cond); }
+  // z = P^{-1} r with the epilogue's inner products: <r, z> (plain: real part; flexible: complex, and <z, q>)
+  EpiDot ed;
+  ed.a = r;
+  ed.b = flexible ? q : nullptr;
+  ed.part = pZ;
+  ed.cplx = flexible;
+  if (f32) STST_TRY(fd_apply(h, nullptr, nullptr, fd_prec, ed, done, h->w_t1, h->w_t2, (float *)z, (const float *)r));
+  else STST_TRY(fd_apply(h, (const double *)r, (double *)z, fd_prec, ed, done, h->w_t1, h->w_t2));
+  {
+    STST_PROF("pcg_update_p", st);
+    if (flexible) k_update_p<T, true><<<gu, 256, 0, st>>>(p, z, ctl, N, pZ, nz);
+    else k_update_p<T, false><<<gu, 256, 0, st>>>(p, z, ctl, N, pZ, nz);
+  }
   STST_CUDA(cudaGetLastError());
   return STST_OK;
+}
+
+int pcg_body(stst_problem *h, cudaGraphConditionalHandle cond, int use_cond) {
+  // STST_PREC_* equals fd_apply's precision code; the low-precision preconditioners run the flexible CG
+  return pcg_iteration<double2>(h, h->ctl, (double2 *)h->w_x, (double2 *)h->w_r, (double2 *)h->w_z, (double2 *)h->w_p,
+                                (double2 *)h->w_q, h->prec_mode != STST_PREC_FP64, h->prec_mode, cond, use_cond);
 }
 
 // Clears ctl->x0_zero if any entry of the initial guess is nonzero (benign race: every writer stores 0).
@@ -283,21 +432,25 @@ int pcg_init(stst_problem *h) {
   const int g = reduction_grid(N);
   const int prec = h->prec_mode;  // STST_PREC_* equals fd_apply's precision code
   double *P = h->partials;
-  double *pA = P, *pB = P + STST_MAXPART, *pC = P + 2 * STST_MAXPART;
+  double *pZ = P + PS_Z * STST_MAXPART, *pRR = P + PS_RR * STST_MAXPART, *pF = P + PS_RP * STST_MAXPART;
   // r = f - A x, partials ||r||^2 ; ||f||^2. From x0 = 0 (the paper's start, Sec. 6) r = f needs no
   // mat-vec: a device check of x0 makes the residual's passes skip themselves and a copy takes over.
   { STST_PROF("pcg_init", st); k_x0_zero_check<<<g, 256, 0, st>>>((const double2 *)h->w_x, N, h->ctl); }
-  STST_TRY(run_plan(h->sys_plan, h->w_x, h->w_r, 0, 1, h->w_f, nullptr, nullptr, &h->ctl->x0_zero, st, nullptr, pB));
+  STST_TRY(run_plan(h->sys_plan, h->w_x, h->w_r, 0, 1, h->w_f, nullptr, nullptr, &h->ctl->x0_zero, st, nullptr, pRR));
   {
     STST_PROF_N("pcg_init", st, 2);
-    k_resid_from_zero<<<g, 512, 0, st>>>(h->ctl, (const double2 *)h->w_f, (double2 *)h->w_r, N, pB);
-    k_norm2<double2><<<g, 256, 0, st>>>((const double2 *)h->w_f, N, pC);
+    k_resid_from_zero<<<g, 512, 0, st>>>(h->ctl, (const double2 *)h->w_f, (double2 *)h->w_r, N, pRR);
+    k_norm2<double2><<<g, 256, 0, st>>>((const double2 *)h->w_f, N, pF);
   }
-  // z = P^{-1} r with <r, z>
-  STST_TRY(fd_apply(h, h->w_r, h->w_z, prec, h->w_r, pA, nullptr, h->w_t1, h->w_t2));
+  // z = P^{-1} r with <r, z> (complex for the flexible CG)
+  EpiDot ed;
+  ed.a = h->w_r;
+  ed.part = pZ;
+  ed.cplx = prec != STST_PREC_FP64;
+  STST_TRY(fd_apply(h, h->w_r, h->w_z, prec, ed, nullptr, h->w_t1, h->w_t2));
   {
     STST_PROF_N("pcg_init", st, 2);
-    k_pcg_init<<<1, 1024, 0, st>>>(h->ctl, pC, g, pB, g, pA, fd_partials_count(h));
+    k_pcg_init<<<1, 1024, 0, st>>>(h->ctl, pF, g, pRR, g, pZ, fd_partials_count(h));
     k_copy_vec<double2><<<g, 256, 0, st>>>((const double2 *)h->w_z, (double2 *)h->w_p, N, &h->ctl->done);
   }
   STST_CUDA(cudaGetLastError());
@@ -466,24 +619,9 @@ __global__ void k_x_from_f32(double2 *__restrict__ x, const float2 *__restrict__
 }
 
 static int inner_body(stst_problem *h, cudaGraphConditionalHandle cond, int use_cond) {
-  cudaStream_t st = h->stream;
-  const long long N = h->N_dof;
-  const int g = reduction_grid(N), gu = update_grid(N);
-  double *P = h->partials;
-  double *pA = P, *pB = P + STST_MAXPART, *pC = P + 2 * STST_MAXPART, *pD = P + 3 * STST_MAXPART;
-  const int *done = &h->ctl2->done;
-  const int nrz = fd_partials_count(h);
-  STST_TRY(run_plan(h->sys_plan, h->v_p, h->v_q, 1, 0, nullptr, h->v_p, pD, done, st));
-  { STST_PROF("pcg_update_xr", st);
-    k_update_xr<float2><<<gu, 256, 0, st>>>((float2 *)h->v_d, (float2 *)h->v_r, (const float2 *)h->v_p,
-                                            (const float2 *)h->v_q, (const float2 *)h->v_z, h->ctl2, N, pB, pC,
-                                            pD, g, pA, nrz); }
-  { STST_PROF("pcg_scalar", st); k_pcg_check<<<1, 1024, 0, st>>>(h->ctl2, pB, gu, pC, gu, cond, use_cond); }
-  STST_TRY(fd_apply(h, nullptr, nullptr, h->prec_mode == STST_PREC_BF16 ? 2 : 1, h->v_r, pA, done, h->w_t1, h->w_t2, h->v_z, h->v_r));
-  { STST_PROF("pcg_update_p", st);
-    k_update_p<float2><<<gu, 256, 0, st>>>((float2 *)h->v_p, (const float2 *)h->v_z, h->ctl2, N, pA, nrz); }
-  STST_CUDA(cudaGetLastError());
-  return STST_OK;
+  // FP32 mat-vec, FP32 (or BF16 tensor-core) preconditioner, flexible CG on the FP32 vectors
+  return pcg_iteration<float2>(h, h->ctl2, (float2 *)h->v_d, (float2 *)h->v_r, (float2 *)h->v_z, (float2 *)h->v_p,
+                               (float2 *)h->v_q, 1, h->prec_mode == STST_PREC_BF16 ? 2 : 1, cond, use_cond);
 }
 
 static int build_ir_graph(stst_problem *h) {
@@ -531,7 +669,7 @@ int ir_run(stst_problem *h, const double *rhs, double *x, double tol, int maxit,
   const int g = reduction_grid(N);
   const size_t bytes = sizeof(double2) * (size_t)N;
   double *P = h->partials;
-  double *pA = P, *pB = P + STST_MAXPART, *pC = P + 2 * STST_MAXPART;
+  double *pZ = P + PS_Z * STST_MAXPART, *pRR = P + PS_RR * STST_MAXPART, *pF = P + PS_RP * STST_MAXPART;
   PcgCtl c0 = {};
   c0.tol2 = tol * tol;
   c0.maxit = maxit;
@@ -543,14 +681,14 @@ int ir_run(stst_problem *h, const double *rhs, double *x, double tol, int maxit,
   STST_CUDA(cudaMemcpyAsync(h->ctl, h->ctl_host, sizeof(PcgCtl), cudaMemcpyHostToDevice, st));
   STST_CUDA(cudaMemcpyAsync(h->w_f, rhs, bytes, cudaMemcpyDeviceToDevice, st));
   STST_CUDA(cudaMemcpyAsync(h->w_x, x, bytes, cudaMemcpyDeviceToDevice, st));
-  { STST_PROF("norm2", st); k_norm2<double2><<<g, 256, 0, st>>>((const double2 *)h->w_f, N, pC); }
-  { STST_PROF("pcg_scalar", st); k_set_ff<<<1, 1024, 0, st>>>(h->ctl, pC, g); }
+  { STST_PROF("norm2", st); k_norm2<double2><<<g, 256, 0, st>>>((const double2 *)h->w_f, N, pF); }
+  { STST_PROF("pcg_scalar", st); k_set_ff<<<1, 1024, 0, st>>>(h->ctl, pF, g); }
   int total_inner = 0, k = 0, status = STST_NOT_CONVERGED;
   PcgCtl hc2 = {};
   for (k = 0; k <= maxit; ++k) {
     // FP64 residual
-    STST_TRY(run_plan(h->sys_plan, h->w_x, h->w_r, 0, 1, h->w_f, nullptr, nullptr, nullptr, st, nullptr, pB));
-    { STST_PROF("pcg_scalar", st); k_ir_outer<<<1, 1024, 0, st>>>(h->ctl, pB, g, 0); }
+    STST_TRY(run_plan(h->sys_plan, h->w_x, h->w_r, 0, 1, h->w_f, nullptr, nullptr, nullptr, st, nullptr, pRR));
+    { STST_PROF("pcg_scalar", st); k_ir_outer<<<1, 1024, 0, st>>>(h->ctl, pRR, g, 0); }
     STST_CUDA(cudaMemcpyAsync(h->ctl_host, h->ctl, sizeof(PcgCtl), cudaMemcpyDeviceToHost, st));
     if (k > 0) STST_CUDA(cudaMemcpyAsync(&h->ctl_host[1], h->ctl2, sizeof(PcgCtl), cudaMemcpyDeviceToHost, st));
     STST_CUDA(cudaStreamSynchronize(st));
@@ -564,10 +702,17 @@ int ir_run(stst_problem *h, const double *rhs, double *x, double tol, int maxit,
     hc2 = c2;
     h->ctl_host[1] = hc2;
     STST_CUDA(cudaMemcpyAsync(h->ctl2, &h->ctl_host[1], sizeof(PcgCtl), cudaMemcpyHostToDevice, st));
-    { STST_PROF("norm2", st); k_norm2<float2><<<g, 256, 0, st>>>((const float2 *)h->v_r, N, pC); }
-    STST_TRY(fd_apply(h, nullptr, nullptr, h->prec_mode == STST_PREC_BF16 ? 2 : 1, h->v_r, pA, nullptr, h->w_t1, h->w_t2, h->v_z, h->v_r));
+    { STST_PROF("norm2", st); k_norm2<float2><<<g, 256, 0, st>>>((const float2 *)h->v_r, N, pF); }
+    {
+      EpiDot ed;  // the inner solve is the flexible CG: complex <r, z>
+      ed.a = h->v_r;
+      ed.part = pZ;
+      ed.cplx = 1;
+      STST_TRY(fd_apply(h, nullptr, nullptr, h->prec_mode == STST_PREC_BF16 ? 2 : 1, ed, nullptr, h->w_t1, h->w_t2,
+                        h->v_z, h->v_r));
+    }
     { STST_PROF("pcg_scalar", st);
-      k_pcg_init<<<1, 1024, 0, st>>>(h->ctl2, pC, g, pC, g, pA, fd_partials_count(h)); }
+      k_pcg_init<<<1, 1024, 0, st>>>(h->ctl2, pF, g, pF, g, pZ, fd_partials_count(h)); }
     { STST_PROF("copy", st);
       k_copy_vec<float2><<<g, 256, 0, st>>>((const float2 *)h->v_z, (float2 *)h->v_p, N, &h->ctl2->done); }
     if (g_prof) {
