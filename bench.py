@@ -16,9 +16,14 @@ the timed region starts; the L2 cache is flushed before every step.
 trains the learned warm start on method-generated solutions, then times solves of new problems
 from the network's iterate against cold-start PCG.
 
-One JSON line on rank 0. With --impl reference the CPU oracle is timed
-instead (a bounded sample: setup plus a few PCG iterations, extrapolated to
-the iteration count of the full oracle solve, which runs once untimed).
+One JSON line on rank 0. It also carries: the accurate solve (the same step
+to relative residual 1e-10) and both solutions' errors against the FP64
+oracle's solution of the same system; the FP64 and BF16x3 preconditioners and
+the 3D+t workloads c3p2 / c3p4 timed the same way (`variants`); the oracle
+timed on the host cores (`cpu_baseline`: medians of full solves, all cores
+and one thread, with the CPU model). With --impl reference the oracle is the
+timed arm: one step is one full oracle solve of the workload (no
+extrapolation; 3D+t workloads use the stated half-size mesh).
 """
 import argparse
 import hashlib
@@ -62,8 +67,14 @@ def parse():
                          "11..14 fused with 1..4 CTAs per time index (stst_set_fused_transforms)")
     ap.add_argument("--time-solver", type=int, default=0,
                     help="0 chosen per shape, 1 sequential, 2 segmented (stst_set_time_solver)")
+    ap.add_argument("--pencil", type=int, default=0,
+                    help="FP32 preconditioner, last direction and time solves in one kernel: 0 chosen per shape, "
+                         "1 off, 2 one CTA per pencil, 3 a cluster of two (stst_set_pencil)")
     ap.add_argument("--cpu-baseline", default="on", choices=["on", "off"],
                     help="time the oracle on the host cores (off: skip it, e.g. for the 3D workloads)")
+    ap.add_argument("--variants", default="on", choices=["on", "off"],
+                    help="c2 only: also time the FP64 and BF16x3 preconditioners, the accurate solve (tolerance "
+                         "1e-10) and the 3D+t workloads c3p2 / c3p4, as extra keys of the one JSON line")
     ap.add_argument("--formulation", default="ls", choices=["ls", "uw"],
                     help="least squares (Sec. 4.3) or ultraweak (Sec. 4.4)")
     ap.add_argument("--inner-tol", type=float, default=1e-4)
@@ -599,12 +610,24 @@ def run_ours(args):
             e1.synchronize()
             pcg_only.append(e0.elapsed_time(e1))
         pcg_only_ms = statistics.mean(pcg_only)
-        # one untimed solve to 1e-12 with the same preconditioner: the accuracy the path reaches
-        x_tight = prob.vec()
-        if args.solver == "ir":
-            st_t, it_t, _, rr_t = S.stst_ir_solve(prob.h, b, x_tight, 1e-12, 60, args.inner_tol, 200)
-        else:
-            st_t, it_t, rr_t = S.stst_pcg_solve(prob.h, b, x_tight, 1e-12, 400)
+        # the accurate solve: the same solve to relative residual ACC_TOL, which brings the mixed path's
+        # solution within 1e-8 of the FP64 oracle's (timed like the steps)
+        x_acc = prob.vec()
+        acc_ms, acc_its = [], []
+        for _ in range(max(1, min(args.steps, 5))):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            x_acc.zero_()
+            prob.build_fd()
+            if args.solver == "ir":
+                st_t, it_t, _, rr_t = S.stst_ir_solve(prob.h, b, x_acc, ACC_TOL, 60, args.inner_tol, 200)
+            else:
+                st_t, it_t, rr_t = S.stst_pcg_solve(prob.h, b, x_acc, ACC_TOL, 400)
+            e1.record(stream)
+            e1.synchronize()
+            acc_ms.append(e0.elapsed_time(e1))
+            acc_its.append(it_t)
 
         # end to end through the C ABI with host buffers: pinned rhs in, solution out, every step
         b_host = b.cpu().pin_memory()
@@ -679,15 +702,24 @@ def run_ours(args):
     n_l = prob.n[1:]
     n_passes, band_apps, flops_dof = S.stst_plan_info(prob.h)
     peaks, peak_src = load_peaks()
-    clk = clocks.get("sm_mhz") or SM_MAX_MHZ_NOMINAL
     fp64_peak = N_SM * FP64_FMA_PER_CLK_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
     fp32_peak = N_SM * FP32_FMA_PER_CLK_SM * 2 * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
-    # dominant kernel of the step = largest total device time in the profiled solve
-    dom = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
+    # per-kernel shares of one profiled solve (plain launches bracketed by events), scaled to the graph-timed
+    # step so that they add up to it
+    prof_total = sum(v[1] for v in prof.values())
+    shares = {k: v[1] / prof_total for k, v in prof.items()} if prof_total > 0 else {}
+    # dominant kernel of the step = largest share
+    dom = max(shares.items(), key=lambda kv: kv[1])[0] if shares else None
     roof = None
     if dom:
         cnt, tot = prof[dom]
         per_launch_s = tot / cnt / 1e3
+        timing = "events around back-to-back profiled launches of the kernel"
+        if dom.startswith("pass"):
+            # the mat-vec's launches: events around 30 back-to-back stst_apply_sys calls, per launch
+            per_launch_s = t_sys / n_passes / 1e3
+            timing = (f"events around 30 back-to-back stst_apply_sys calls on the handle's stream, divided by "
+                      f"the {n_passes} launches of one call")
         if dom.startswith("modeprod_bf16"):
             # HBM/L2 bound on tensor cores: read FP32 tile + write FP32 result per complex unknown
             roof = {"kernel": dom, "bound": "hbm", "achieved": 16.0 * n_dof / per_launch_s / 1e9,
@@ -711,8 +743,13 @@ def run_ours(args):
                                % (N_SM, FP64_FMA_PER_CLK_SM if dom.endswith("f64") else FP32_FMA_PER_CLK_SM,
                                   SM_MAX_MHZ_NOMINAL)) if roof["bound"] == "alu" else f"hbm_gbs of {peak_src}"
         roof["launch_ms"] = per_launch_s * 1e3
+        roof["launch_timing"] = timing
         roof["traffic"] = traffic_for(dom, {"n_dof": n_dof, "band_apps_per_dof": band_apps})
-        roof["share_of_solve"] = tot / sum(v[1] for v in prof.values())
+        if roof["traffic"] and dom.startswith("pass"):
+            # the mat-vec's algorithmic bytes: x in and y out once per application, 32 B per unknown
+            roof["traffic_per_apply_sys"] = roof["traffic"] * n_passes
+            roof["traffic_over_algorithmic_bytes"] = roof["traffic"] * n_passes / (32.0 * n_dof)
+        roof["share_of_step"] = shares[dom]
     out = {
         "metric": METRIC,
         "value": ms / 1e3,
@@ -735,6 +772,10 @@ def run_ours(args):
                    "step": "build_fd (setup) + pcg_solve from x0 = 0", "l2": "flushed (512 MB write) before each step",
                    "parallelism": f"replicas x{world}"},
         "pcg_only_ms": pcg_only_ms,
+        "accurate_solve": {"tol": ACC_TOL, "ms": statistics.mean(acc_ms), "pcg_iterations": statistics.median(acc_its),
+                           "status": st_t, "relres": rr_t,
+                           "why": "the same step to relative residual 1e-10: the residual at which the mixed path's "
+                                  "solution is within 1e-8 of the FP64 oracle's (error_vs_fp64_oracle)"},
         "roofline_steps": roofline_steps(n_dof, n_l, flops_dof, t_prec, t_sys, args.prec, peaks, fp64_peak, fp32_peak),
         "apply_prec_dofs_per_s": n_dof / (t_prec / 1e3),
         "apply_prec_ms": t_prec,
@@ -745,7 +786,12 @@ def run_ours(args):
         "time_solver": dict(zip(("segments", "segment_len", "segmented"),
                                 S.stst_time_solver_info(prob.h, 0 if args.prec == "fp64" else 1))),
         "fused_2d_transforms": S.stst_fused_transforms_info(prob.h),
-        "kernels_ms_per_solve": {k: round(v[1], 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
+        "pencil_ctas": S.stst_pencil_info(prob.h),
+        "kernels_ms_per_step": {k: round(ms * v, 4) for k, v in sorted(shares.items(), key=lambda kv: -kv[1])},
+        "kernels_ms_profiled_solve": {k: round(v[1], 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
+        "kernel_time_basis": ("kernels_ms_per_step = each kernel's share of one profiled solve (plain launches, "
+                              "each bracketed by CUDA events; operator kernels timed back to back) times the "
+                              "graph-timed step; the profiled solve itself is slower (launch gaps, no graph)"),
         "kernel_launches_per_solve": {k: v[0] for k, v in prof.items()},
         "gpu_launches": launches,
         "gpu_launches_basis": launch_basis,
@@ -760,25 +806,87 @@ def run_ours(args):
                           {"table": "Table 1, p=3, n_el=64, V=0 travelling wave, 1 CPU thread at 1 GHz",
                            "seconds": 4.7142, "iterations": 8}),
     }
+    xg, xa, bn = x.cpu().numpy(), x_acc.cpu().numpy(), b.cpu().numpy()
+    prob.close()
+    del flush
+    if rank == 0 and world == 1 and args.variants == "on" and args.config == "c2" and args.solver == "pcg":
+        out["variants"] = run_variants(args)
     if rank == 0 and world == 1 and args.cpu_baseline == "on":
-        cb = cpu_baseline(args.config, iters_full=None, formulation=args.formulation, prec_op=args.prec_op)
-        x_ref = cb.pop("_x_ref", None)
-        out["cpu_baseline"] = cb
-        if x_ref is not None:
-            xg = x.cpu().numpy()
-            xt = x_tight.cpu().numpy()
-            out["error_vs_fp64_oracle"] = {
-                "solution_rel_err": float(np.linalg.norm(xg - x_ref) / np.linalg.norm(x_ref)),
-                "solution_rel_err_tol_1e-12": float(np.linalg.norm(xt - x_ref) / np.linalg.norm(x_ref)),
-                "tight_solve": {"status": st_t, "iterations": it_t, "relres": rr_t},
-                "reference": "oracle PCG (numpy FP64, exact P-hat) to relative residual 1e-12 on the same workload",
-                "gpu": f"{args.prec} preconditioner, FP64 PCG; the timed solve stops at tol {tol:g} (its error is "
-                       f"bounded by the condition number times tol), the second one at 1e-12"}
+        out["cpu_baseline"] = cpu_baseline(args.config, formulation=args.formulation, prec_op=args.prec_op)
+        out["error_vs_fp64_oracle"] = error_vs_oracle(args, xg, xa, bn, tol)
     if rank == 0:
         print(json.dumps(out), flush=True)
-    prob.close()
     if dist:
         dist.destroy_process_group()
+
+
+ACC_TOL = 1e-10
+ORACLE_REF_TOL = 1e-13
+
+
+def error_vs_oracle(args, x_timed, x_acc, b, tol):
+    """The GPU's solutions against the FP64 oracle's solution of the same system: the oracle's PCG with the
+    exact P-hat to relative residual 1e-13 on the GPU's own right-hand side (so that the comparison measures
+    the solver, not the right-hand side's rounding times the condition number), errors as max-abs relative."""
+    import numpy as np
+    from oracle import fd, pcg
+    cfg, disc, _ = oracle_problem(args.config, args.formulation)
+    F = (fd.PotentialFastDiagonalization if args.prec_op == "potential" else fd.FastDiagonalization)(disc)
+    x_ref, its, rr, _ = pcg.pcg(disc.apply, F.apply, b, tol=ORACLE_REF_TOL, maxit=400)
+    den = np.abs(x_ref).max()
+    true_res = float(np.linalg.norm(b - disc.apply(x_timed)) / np.linalg.norm(b))
+    return {"timed_solve_rel_err": float(np.abs(x_timed - x_ref).max() / den),
+            "timed_solve_true_residual": true_res,
+            "accurate_solve_rel_err": float(np.abs(x_acc - x_ref).max() / den),
+            "accurate_solve_tol": ACC_TOL,
+            "reference": f"oracle PCG (numpy FP64, exact P-hat, {its} iterations) to relative residual "
+                         f"{ORACLE_REF_TOL:g} on the GPU's right-hand side; max |x - x_ref| / max |x_ref|",
+            "gpu": f"{args.prec} preconditioner in the FP64 flexible CG; timed solve to {tol:g}, accurate solve to "
+                   f"{ACC_TOL:g}"}
+
+
+VARIANTS = [("c2", "fp64"), ("c2", "bf16"), ("c3p2", "fp32"), ("c3p4", "fp32")]
+
+
+def run_variants(args, steps=5, warmup=3):
+    """Other precisions and the 3D+t workloads, each timed like the main step (setup + PCG from x0 = 0 to the
+    workload's tolerance, L2 flushed, CUDA events on the handle's stream), so that one driver run carries
+    them: the FP64-preconditioned path is the precision-matched baseline of the mixed one."""
+    import torch
+    import paper_2311_18461_gb300 as S
+    out = {}
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    for name, prec in VARIANTS:
+        cfg, V, u0 = workload(name)
+        tol = cfg.get("tol", 1e-8)
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            prob, b = build_problem(cfg, V, u0, prec, stream)
+            x = prob.vec()
+
+            def solve():
+                x.zero_()
+                prob.build_fd()
+                return S.stst_pcg_solve(prob.h, b, x, tol, 200)
+
+            for _ in range(warmup):
+                st, it, rr = solve()
+            times, its = [], []
+            for _ in range(steps):
+                flush.fill_(1)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                st, it, rr = solve()
+                e1.record(stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+                its.append(it)
+        out[f"{name}_{prec}"] = {"workload": workload_name(name, cfg, tol), "preconditioner": prec, "n_dof": prob.n_dof,
+                                 "ms_per_step": statistics.mean(times), "pcg_iterations": statistics.median(its),
+                                 "status": st, "relres": rr, "steps": steps, "warmup": warmup}
+        prob.close()
+        torch.cuda.synchronize()
+    return out
 
 
 def _oracle_threads():
@@ -789,12 +897,39 @@ def _oracle_threads():
         return os.cpu_count()
 
 
-def oracle_problem(cfg_name, formulation="ls"):
-    """The oracle's discretisation and right-hand side of a workload."""
+def cpu_model():
+    """The host CPU's model name and logical core count (recorded beside every oracle timing)."""
+    name = None
+    try:
+        for line in open("/proc/cpuinfo"):
+            key = line.split(":")[0].strip().lower()
+            if key in ("model name", "cpu model", "hardware"):
+                name = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not name:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    name = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    import platform
+    return {"model": name or platform.processor() or platform.machine(), "logical_cores": os.cpu_count(),
+            "machine": platform.machine()}
+
+
+def oracle_problem(cfg_name, formulation="ls", n_el=None):
+    """The oracle's discretisation and right-hand side of a workload (n_el: the same workload on another mesh)."""
     from inputs import potential, initial_factors, product_fn, travelling_wave
     from oracle import rhs
     from oracle.system import Discretization
     cfg, _, _ = workload(cfg_name)
+    if n_el is not None:
+        cfg = dict(cfg, n_el=list(n_el))
     d = cfg["d"]
     disc = Discretization(cfg["n_el"], [cfg["p"]] * (d + 1), T=cfg["T"], nu=cfg["nu"], potential=potential(cfg),
                           formulation=formulation)
@@ -808,68 +943,128 @@ def oracle_problem(cfg_name, formulation="ls"):
     return cfg, disc, b
 
 
-def cpu_baseline(cfg_name, iters_full=None, sample_iters=2, formulation="ls", prec_op="phat"):
-    """The oracle timed on this host: setup + `sample_iters` PCG iterations, extrapolated to the full count.
-    prec_op "potential": the oracle's potential-aware preconditioner P_V in place of P-hat."""
+def oracle_solve_times(disc, b, tol, runs, prec_op="phat"):
+    """Full oracle solves as in the paper's Table 1: preconditioner setup (Algorithm 1 step 1 and the H_i)
+    plus PCG from x0 = 0 to relative residual tol. Returns (seconds of each run, iterations)."""
     from oracle import fd, pcg
-    cfg, disc, b = oracle_problem(cfg_name, formulation)
     FD = fd.PotentialFastDiagonalization if prec_op == "potential" else fd.FastDiagonalization
-    terms = disc.terms()
-    x_ref = None
-    if iters_full is None:
-        # one untimed full solve, to 1e-12: its residual history gives the iteration count at 1e-8,
-        # its solution is the FP64 reference the GPU result is compared with
+    times, its = [], None
+    for _ in range(runs):
+        t0 = time.perf_counter()
         F = FD(disc)
-        x_ref, _, _, hist = pcg.pcg(disc.apply, F.apply, b, tol=1e-12, maxit=400)
-        iters_full = next(i for i, h in enumerate(hist) if h <= cfg.get("tol", 1e-8))
-    t0 = time.perf_counter()
-    F = FD(disc)
-    t1 = time.perf_counter()
-    pcg.pcg(disc.apply, F.apply, b, tol=0.0, maxit=sample_iters)
-    t2 = time.perf_counter()
-    per_it = (t2 - t1) / sample_iters
-    value = (t1 - t0) + per_it * iters_full
-    out = {"value": value, "unit": "s", "cores": _oracle_threads(), "kind": "oracle",
-           "sample": f"FD setup + {sample_iters} PCG iterations of the same workload, extrapolated to the "
-                     f"{iters_full} iterations of the full oracle solve (numpy FP64, {len(terms)} Kronecker terms)"}
-    if x_ref is not None:
-        out["_x_ref"] = x_ref
+        _, its, _, _ = pcg.pcg(disc.apply, F.apply, b, tol=tol, maxit=400)
+        times.append(time.perf_counter() - t0)
+    return times, its
+
+
+SINGLE_THREAD_ENV = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS",
+                     "VECLIB_MAXIMUM_THREADS", "NUMEXPR_NUM_THREADS")
+
+
+def oracle_single_thread_times(cfg_name, formulation, prec_op, n_el, runs):
+    """oracle_solve_times in a child process whose BLAS and OpenMP pools have one thread (the pools are
+    sized when numpy loads, so the limit has to be set before that)."""
+    env = dict(os.environ)
+    for k in SINGLE_THREAD_ENV:
+        env[k] = "1"
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "cfg, disc, b = bench.oracle_problem(%r, %r, n_el=%r); "
+            "bench.oracle_solve_times(disc, b, cfg.get('tol', 1e-8), 1, %r); "
+            "t, it = bench.oracle_solve_times(disc, b, cfg.get('tol', 1e-8), %d, %r); "
+            "print(json.dumps({'t': t, 'its': it, 'n_dof': disc.N_dof}))"
+            % (ROOT, cfg_name, formulation, list(n_el), prec_op, runs, prec_op))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError("single-thread oracle run failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def _small_mesh(cfg):
+    """The same workload on half the elements per direction (the stated smaller sample)."""
+    return [max(4, n // 2) for n in cfg["n_el"]]
+
+
+def cpu_baseline(cfg_name, formulation="ls", prec_op="phat", runs=3, small_runs=5):
+    """The oracle as it stands (numpy/scipy FP64) timed on this host's cores, no extrapolation:
+      * all cores: the median of `runs` full solves of the workload itself (2D+t and smaller), or of the
+        stated half-size mesh for 3D+t workloads (a full 3D+t oracle solve takes minutes);
+      * one thread: the median of `small_runs` full solves of the workload on the half-size mesh.
+    A full solve is the preconditioner setup plus PCG from x0 = 0 to the workload's tolerance."""
+    cfg, _, _ = workload(cfg_name)
+    tol = cfg.get("tol", 1e-8)
+    big = cfg["d"] <= 2
+    small = _small_mesh(cfg)
+    _, disc_s, b_s = oracle_problem(cfg_name, formulation, n_el=small)
+    oracle_solve_times(disc_s, b_s, tol, 1, prec_op)              # warm-up: libraries loaded, caches filled
+    if big:
+        _, disc, b = oracle_problem(cfg_name, formulation)
+        t_all, its_all = oracle_solve_times(disc, b, tol, runs, prec_op)
+    else:
+        disc = disc_s
+        t_all, its_all = oracle_solve_times(disc_s, b_s, tol, runs, prec_op)
+    cores = _oracle_threads()
+    one = oracle_single_thread_times(cfg_name, formulation, prec_op, small, small_runs)
+    t_one, its_one = one["t"], one["its"]
+    mesh = "x".join(str(n) for n in cfg["n_el"])
+    smesh = "x".join(str(n) for n in small)
+    out = {"value": statistics.median(t_all), "unit": "s", "cores": cores, "kind": "oracle",
+           "sample": (f"median of {runs} full oracle solves (setup + PCG from x0 = 0 to {tol:g}, {its_all} "
+                      f"iterations) of the {'workload' if big else 'workload on the half-size mesh ' + smesh} "
+                      f"({disc.N_dof} unknowns) on {cores} threads; numpy/scipy FP64, no extrapolation"),
+           "runs_s": [round(t, 4) for t in t_all],
+           "single_thread": {"value": statistics.median(t_one), "unit": "s", "cores": 1, "runs": small_runs,
+                             "runs_s": [round(t, 4) for t in t_one], "iterations": its_one,
+                             "workload": f"{cfg_name} on the half-size mesh {smesh} ({disc_s.N_dof} unknowns)"},
+           "cpu": cpu_model(),
+           "workload_mesh": mesh if big else smesh}
     return out
 
 
 def run_reference(args):
+    """The reference arm: the oracle (the paper ships no code), timed on the host cores. One step is one
+    full oracle solve of the workload (2D+t and smaller): setup plus PCG to the workload's tolerance, no
+    extrapolation. Warm-up steps are untimed solves of the half-size mesh. 3D+t workloads, whose full
+    oracle solves take minutes, time the half-size mesh and say so."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from oracle import fd, pcg
     formulation = args.formulation
     if args.config == "c4":
-        # 128 generated problems: the oracle's bounded sample is defined on single-problem workloads
         print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times single-problem workloads "
                           "(c1, c2, c3*, c5, tw); c4's 128 problems have no bounded oracle sample"}), flush=True)
         return
-    cfg, disc, b = oracle_problem(args.config, formulation)
-    F = (fd.PotentialFastDiagonalization if args.prec_op == "potential" else fd.FastDiagonalization)(disc)
-    _, iters_full, _, _ = pcg.pcg(disc.apply, F.apply, b, tol=cfg.get("tol", 1e-8), maxit=200)
-    vals = []
-    for k in range(args.warmup + args.steps):
-        r = cpu_baseline(args.config, iters_full=iters_full, formulation=formulation, prec_op=args.prec_op)
-        if k >= args.warmup:
-            vals.append(r["value"])
-    v = statistics.mean(vals)
+    cfg, _, _ = workload(args.config)
+    tol = cfg.get("tol", 1e-8)
+    big = cfg["d"] <= 2
+    small = _small_mesh(cfg)
+    _, disc_s, b_s = oracle_problem(args.config, formulation, n_el=small)
+    oracle_solve_times(disc_s, b_s, tol, max(args.warmup, 1), args.prec_op)
+    if big:
+        _, disc, b = oracle_problem(args.config, formulation)
+    else:
+        disc, b = disc_s, b_s
+    times, its = oracle_solve_times(disc, b, tol, args.steps, args.prec_op)
+    v = statistics.mean(times)
+    cores = _oracle_threads()
+    smesh = "x".join(str(n) for n in small)
+    sample = (f"{args.steps} full oracle solves (setup + PCG from x0 = 0 to {tol:g}, {its} iterations) of the "
+              + ("workload" if big else f"workload on the half-size mesh {smesh}")
+              + f" ({disc.N_dof} unknowns), mean; warm-up: {max(args.warmup, 1)} solves of the half-size mesh; "
+              f"numpy/scipy FP64 on {cores} threads")
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": workload_name(args.config, cfg, cfg.get("tol", 1e-8))
-                                  + (", ultraweak formulation (Sec. 4.4)" if formulation == "uw" else ""),
+           "config": {"workload": workload_name(args.config, cfg, tol)
+                                  + (", ultraweak formulation (Sec. 4.4)" if formulation == "uw" else "")
+                                  + ("" if big else f", half-size mesh {smesh}"),
                       "n_dof": disc.N_dof, "preconditioner": "fp64 (oracle) " + ("P_V (potential-aware)"
                                                                                 if args.prec_op == "potential"
                                                                                 else "P-hat"),
-                      "solver": "pcg",
-                      "pcg_iterations": iters_full, "step": "build_fd (setup) + pcg_solve from x0 = 0",
+                      "solver": "pcg", "pcg_iterations": its, "step": "build_fd (setup) + pcg_solve from x0 = 0",
                       "parallelism": "oracle on the host cores, rank 0"},
-           "cpu_baseline": {"value": v, "unit": "s", "cores": r["cores"], "kind": "oracle", "sample": r["sample"]},
+           "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample,
+                            "cpu": cpu_model()},
            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -886,6 +1081,7 @@ def main():
         S.stst_set_autotune(args.autotune)
         S.stst_set_time_solver(args.time_solver)
         S.stst_set_fused_transforms(args.fused_transforms)
+        S.stst_set_pencil(args.pencil)
         if args.config == "c4":
             run_batch(args)
         elif args.config == "c5":

@@ -323,6 +323,23 @@ int stst_set_time_solver(int mode);
  * other modes. stst_fused_transforms_info: S of the handle, 0 when it uses separate kernels.
  */
 int stst_set_fused_transforms(int mode);
+/*
+ * stst_set_pencil: the last spatial direction's steps of Algorithm 1 with the FP32 preconditioner. After
+ * the forward products of directions 1..d-1, every pencil (fixed eigen-indices j_1..j_{d-1}) holds complete
+ * time series of n_d eigen-systems, so the forward product along direction d (step 2), the n_d banded time
+ * solves (step 3, Eq. independent_problems) and the backward product along d (step 4) can run in one kernel
+ * with the pencil in shared memory: one CTA per pencil, or a cluster of two CTAs that split its rows and
+ * exchange the solved halves through distributed shared memory. The time-solve kernel and one transform
+ * launch per application disappear. Mode 0 (default) chooses per shape when the preconditioner is built
+ * (whole applications timed under autotune mode 1, else the cluster of two where it fits); 1 = off (separate
+ * kernels); 2 = one CTA per pencil; 3 = a cluster of two. Needs p[0] <= 4 and the pencil in shared memory;
+ * elsewhere the separate kernels run. Same results up to rounding (the sums of each product run in the same
+ * order; the time solves are the sequential recurrences). Process-wide, for handles whose preconditioner is
+ * built afterwards; STST_ERR_ARG for other modes. stst_pencil_info: CTAs per pencil of the handle, 0 when the
+ * pencil kernel is not used.
+ */
+int stst_set_pencil(int mode);
+int stst_pencil_info(stst_handle h, int *ctas_per_pencil);
 int stst_fused_transforms_info(stst_handle h, int *fused);
 int stst_time_solver_info(stst_handle h, int precision, int *segments, int *segment_len, int *segmented);
 /* Name and description of the CUDA error behind the calling thread's last STST_ERR_CUDA (static string). */

@@ -67,6 +67,8 @@ def lib():
             "stst_set_time_solver": [I],
             "stst_set_fused_transforms": [I],
             "stst_fused_transforms_info": [P, IP],
+            "stst_set_pencil": [I],
+            "stst_pencil_info": [P, IP],
             "stst_time_solver_info": [P, I, IP, IP, IP],
             "stst_tile_info": [P, I, IP, IP, DP],
             "stst_ws_create": [ctypes.POINTER(P), I, IP, I, ctypes.c_ulonglong, P],
@@ -293,6 +295,16 @@ def stst_set_fused_transforms(mode):
 def stst_fused_transforms_info(h):
     f = ctypes.c_int()
     _chk(lib().stst_fused_transforms_info(h, ctypes.byref(f)), "stst_fused_transforms_info")
+    return f.value
+
+
+def stst_set_pencil(mode):
+    return _chk(lib().stst_set_pencil(int(mode)), "stst_set_pencil")
+
+
+def stst_pencil_info(h):
+    f = ctypes.c_int()
+    _chk(lib().stst_pencil_info(h, ctypes.byref(f)), "stst_pencil_info")
     return f.value
 
 

@@ -1318,6 +1318,63 @@ int fd_apply(stst_problem *h, const double *r, double *s, int precision, const E
     return STST_OK;
   }
   // FP32
+  if (h->pencil) {
+    // the last direction's products and the time solves in the pencil kernel; the other directions as
+    // fused 2D transforms (d = 3) or mode products
+    const int CL = h->pencil;
+    float2 *y32 = (float2 *)bufA, *z32 = (float2 *)bufB;
+    if (d == 1) {
+      if (in32 && out32) return launch_pencil<float2, float2>((const float2 *)in32, (float2 *)out32, h, CL, ed, done, st);
+      if (in32) return launch_pencil<float2, double2>((const float2 *)in32, (double2 *)s, h, CL, ed, done, st);
+      if (out32) return launch_pencil<double2, float2>((const double2 *)r, (float2 *)out32, h, CL, ed, done, st);
+      return launch_pencil<double2, double2>((const double2 *)r, (double2 *)s, h, CL, ed, done, st);
+    }
+    if (d == 3 && h->fd2d) {
+      const int S = h->fd2d;
+      if (in32) STST_TRY((launch_fd2d<float2, float2>((const float2 *)in32, y32, h, 0, none, done, st, S)));
+      else STST_TRY((launch_fd2d<double2, float2>((const double2 *)r, y32, h, 0, none, done, st, S)));
+      STST_TRY((launch_pencil<float2, float2>(y32, z32, h, CL, none, done, st)));
+      if (out32) return launch_fd2d<float2, float2>(z32, (float2 *)out32, h, 1, ed, done, st, S);
+      return launch_fd2d<float2, double2>(z32, (double2 *)s, h, 1, ed, done, st, S);
+    }
+    // mode products of directions 1 .. d-1 forward (alternating buffers), the pencil, then backward
+    float2 *bufs[2] = {y32, z32};
+    int cur = 0;
+    const float2 *src = nullptr;
+    for (int l = 1; l < d; ++l) {
+      float2 *dst = bufs[cur];
+      if (l == 1 && !in32)
+        STST_TRY((launch_modeprod<float, double2, float2>((const double2 *)r, dst, h->U32[l], h->dir[l].n, inner[l],
+                                                          outer[l], 0, none, done, st, h->mp_cfg[l])));
+      else
+        STST_TRY((launch_modeprod<float, float2, float2>(l == 1 ? (const float2 *)in32 : src, dst, h->U32[l],
+                                                         h->dir[l].n, inner[l], outer[l], 0, none, done, st,
+                                                         h->mp_cfg[l])));
+      src = dst;
+      cur ^= 1;
+    }
+    {
+      float2 *dst = bufs[cur];
+      STST_TRY((launch_pencil<float2, float2>(src, dst, h, CL, none, done, st)));
+      src = dst;
+      cur ^= 1;
+    }
+    for (int l = d - 1; l >= 1; --l) {
+      if (l == 1) {
+        if (out32)
+          return launch_modeprod<float, float2, float2>(src, (float2 *)out32, h->U32[l], h->dir[l].n, inner[l],
+                                                        outer[l], 1, ed, done, st, h->mp_cfg[l]);
+        return launch_modeprod<float, float2, double2>(src, (double2 *)s, h->U32[l], h->dir[l].n, inner[l], outer[l],
+                                                       1, ed, done, st, h->mp_cfg[l]);
+      }
+      float2 *dst = bufs[cur];
+      STST_TRY((launch_modeprod<float, float2, float2>(src, dst, h->U32[l], h->dir[l].n, inner[l], outer[l], 1, none,
+                                                       done, st, h->mp_cfg[l])));
+      src = dst;
+      cur ^= 1;
+    }
+    return STST_OK;
+  }
   if (h->fd2d) {  // modes 1 and 2 of each transform in one kernel per (t, i3) slab; mode 3 (d = 3) separate
     float2 *y32 = (float2 *)bufA;
     const int S = h->fd2d;
@@ -1381,7 +1438,8 @@ int fd_apply(stst_problem *h, const double *r, double *s, int precision, const E
 int fd_partials_count(stst_problem *h) {
   long long ncols = h->N_dof / h->dir[1].n;
   if (h->prec_mode == STST_PREC_BF16) return tc_partials_count(ncols);
-  if (h->fd2d && h->prec_mode == STST_PREC_FP32) return (int)(fd2d_slabs(h) * h->fd2d);
+  if (h->pencil && h->prec_mode == STST_PREC_FP32 && h->d == 1) return (int)(h->N_s / h->dir[1].n * h->pencil);
+  if (h->fd2d && h->prec_mode == STST_PREC_FP32 && (!h->pencil || h->d == 3)) return (int)(fd2d_slabs(h) * h->fd2d);
   const dim3 g = modeprod_grid(h->dir[1].n, ncols, h->mp_cfg[1]);
   return (int)(g.x * g.y);
 }
@@ -1537,12 +1595,81 @@ static int tune_fd2d(stst_problem *h) {
   return STST_OK;
 }
 
+// ---- the pencil kernel or not (FP32 preconditioner) -------------------------------------------------
+// h->pencil = CTAs per pencil (1 or 2), 0 for the transforms and time solves as separate kernels.
+// Measured (autotune mode 1): one whole FP32 preconditioner application of each variant, timed on work
+// vectors and cached per shape. Otherwise two CTAs per pencil where that fits, else one.
+int g_pencil_mode = 0;  // 0 chosen per shape, 1 off, 2 one CTA per pencil, 3 a cluster of two
+static std::map<std::tuple<int, int, int, int, int>, int> g_pencil_cache;
+
+static int tune_pencil(stst_problem *h) {
+  h->pencil = 0;
+  if (h->prec_mode != STST_PREC_FP32 || !h->Gp32 || g_pencil_mode == 1) return STST_OK;
+  const bool f1 = pencil_fits(h, 1), f2 = pencil_fits(h, 2);
+  if (g_pencil_mode == 2 || g_pencil_mode == 3) {
+    const int CL = g_pencil_mode - 1;
+    h->pencil = (CL == 1 ? f1 : f2) ? CL : 0;
+    return STST_OK;
+  }
+  if (g_tune_enabled != 1) {
+    h->pencil = f2 ? 2 : (f1 ? 1 : 0);
+    return STST_OK;
+  }
+  const auto key = std::make_tuple(h->n_t(), h->dir[0].p, h->dir[1].n, h->d >= 2 ? h->dir[2].n : 0,
+                                   h->d == 3 ? h->dir[3].n : 0);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_pencil_cache.find(key);
+    if (it != g_pencil_cache.end()) {
+      h->pencil = it->second;
+      return STST_OK;
+    }
+  }
+  cudaStream_t st = h->stream;
+  STST_CUDA(cudaMemsetAsync(h->w_r, 0, sizeof(double2) * h->N_dof, st));
+  cudaEvent_t e0, e1;
+  STST_CUDA(cudaEventCreate(&e0));
+  STST_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  int choice = 0, status = STST_OK;
+  for (int CL = 0; CL <= 2 && status == STST_OK; ++CL) {
+    if ((CL == 1 && !f1) || (CL == 2 && !f2)) continue;
+    h->pencil = CL;
+    auto run = [&]() { return fd_apply(h, h->w_r, h->w_z, 1, EpiDot(), nullptr, h->w_t1, h->w_t2); };
+    for (int w = 0; w < 2 && status == STST_OK; ++w) status = run();
+    cudaEventRecord(e0, st);
+    for (int w = 0; w < 5 && status == STST_OK; ++w) status = run();
+    cudaEventRecord(e1, st);
+    const cudaError_t es = cudaEventSynchronize(e1);
+    if (es != cudaSuccess) {
+      stst_last_cuda = es;
+      status = STST_ERR_CUDA;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (status == STST_OK && ms < best) {
+      best = ms;
+      choice = CL;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->pencil = choice;
+  STST_TRY(status);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_pencil_cache[key] = choice;
+  }
+  return STST_OK;
+}
+
 int tune_modeprod(stst_problem *h) {
   if (h->tuned) return STST_OK;
   STST_TRY(tune_mp_tiles(h));
   STST_TRY(tune_ts<float>(h));
   if (h->prec_mode == STST_PREC_FP64) STST_TRY(tune_ts<double>(h));
   STST_TRY(tune_fd2d(h));
+  STST_TRY(tune_pencil(h));
   h->tuned = 1;
   return STST_OK;
 }

@@ -443,6 +443,8 @@ void destroy_all(stst_problem *h) {
   cudaFree(h->Hd);
   cudaFree(h->Hg32);
   cudaFree(h->Hd32);
+  cudaFree(h->Gp32);
+  cudaFree(h->Dp32);
   for (int q = 0; q < 2; ++q) {
     cudaFree(h->Tf[q]);
     cudaFree(h->Tb[q]);
@@ -541,6 +543,10 @@ int create_impl(stst_problem *h, int d, const int *n_el, const int *p, double T,
   STST_TRY(alloc((void **)&h->Hd, sizeof(double) * nt * h->N_s));
   STST_TRY(alloc(&h->Hg32, sizeof(float2) * nt * Pt * h->N_s));
   STST_TRY(alloc((void **)&h->Hd32, sizeof(float) * nt * h->N_s));
+  if (prec_mode == STST_PREC_FP32 && (pencil_fits(h, 1) || pencil_fits(h, 2))) {
+    STST_TRY(alloc(&h->Gp32, sizeof(float2) * nt * Pt * h->N_s));
+    STST_TRY(alloc((void **)&h->Dp32, sizeof(float) * nt * h->N_s));
+  }
   for (int q = 0; q < 2; ++q) {  // transfer matrices of the segmented time solves (FP64 ones in FP64 mode)
     h->ts_S[q] = 0;
     if (q == 1 && prec_mode != STST_PREC_FP64) continue;
@@ -963,6 +969,18 @@ int stst_set_fused_transforms(int mode) {
 int stst_fused_transforms_info(stst_handle h, int *fused) {
   STST_TRY(check(h));
   if (fused) *fused = h->fd2d;
+  return STST_OK;
+}
+
+int stst_set_pencil(int mode) {
+  if (mode < 0 || mode > 3) return STST_ERR_ARG;
+  g_pencil_mode = mode;
+  return STST_OK;
+}
+
+int stst_pencil_info(stst_handle h, int *ctas_per_pencil) {
+  STST_TRY(check(h));
+  if (ctas_per_pencil) *ctas_per_pencil = h->pencil;
   return STST_OK;
 }
 

@@ -206,6 +206,9 @@ struct stst_problem {
   double *Hd;                      // FP64 inverse diagonals n_t x N_s
   void *Hg32;                      // FP32 factors
   float *Hd32;
+  void *Gp32;                      // FP32 factors in the pencil order (pencil kernel), or null
+  float *Dp32;
+  int pencil;                      // CTAs per pencil of the pencil kernel (FP32 preconditioner), 0: not used
   // parallel-in-time time solves, [0] FP32 factors, [1] FP64 factors: segments, segment length,
   // forward / backward transfer matrices, and whether the segmented kernel is used
   int ts_S[2], ts_L[2], ts_seg[2];
@@ -307,4 +310,13 @@ int launch_modeprod_tc(const TI *X, TO *Y, const __nv_bfloat16 *Bk, long long lo
                        long long inner, long long outer, const EpiDot &ed, const int *done, int *errflag,
                        cudaStream_t s);
 int tc_partials_count(long long ncols);
+
+// pencil kernel (pencil.cu): steps 2-4 of Algorithm 1 along the last spatial direction with the time solves
+bool pencil_fits(const stst_problem *h, int CL);
+size_t pencil_smem(int n, int nt, int P, int CL);
+int launch_factor_pencil(stst_problem *h, cudaStream_t s);
+template <typename TI, typename TO>
+int launch_pencil(const TI *X, TO *Y, const stst_problem *h, int CL, const EpiDot &ed, const int *done,
+                  cudaStream_t s);
+extern int g_pencil_mode;
 inline int pad16(int n) { return (n + 15) / 16 * 16; }

@@ -392,6 +392,7 @@ def test_mode_product_tiles_agree_bitwise(prec):
     outs = {}
     P.stst_set_time_solver(1)  # the same time solve for every tile
     P.stst_set_fused_transforms(1)  # separate mode products, so that every tile runs
+    P.stst_set_pencil(1)
     try:
         for mode in (0, 12, 14, 22, 24, 32, 34, 42, 44, 132, 1):
             P.stst_set_autotune(mode)
@@ -405,6 +406,7 @@ def test_mode_product_tiles_agree_bitwise(prec):
         P.stst_set_autotune(1)
         P.stst_set_time_solver(0)
         P.stst_set_fused_transforms(0)
+        P.stst_set_pencil(0)
     ref = outs[0][0]
     for mode, (o, tiles) in outs.items():
         assert np.array_equal(o, ref), (mode, tiles)
@@ -421,6 +423,7 @@ def test_fused_2d_transforms_bitwise(n_el, p):
     preconditioner output as the separate mode-product kernels; PCG with either takes the same
     iterations (only the order of the dot-product partial sums differs)."""
     out = {}
+    S.stst_set_pencil(1)  # the separate last-direction kernels, so that the fused transforms run for d = 2
     try:
         for mode in (1, 2, 11, 12, 13, 14):
             S.stst_set_fused_transforms(mode)
@@ -433,6 +436,7 @@ def test_fused_2d_transforms_bitwise(n_el, p):
             prob.close()
     finally:
         S.stst_set_fused_transforms(0)
+        S.stst_set_pencil(0)
     assert out[1][1] == 0 and out[2][1] >= 1 and out[11][1] == 1
     assert all(out[10 + k][1] in (k, out[2][1]) for k in (2, 3, 4))  # the default where k leaves a part empty
     for mode in (2, 11, 12, 13, 14):
@@ -468,6 +472,7 @@ def test_segmented_time_solve_matches_sequential(prec, tol, nt_el, pt):
     import torch
     import paper_2311_18461_gb300 as P
     out = {}
+    P.stst_set_pencil(1)  # the time-solve kernels (the pencil kernel has its own solves)
     try:
         for mode in (1, 2):
             P.stst_set_time_solver(mode)
@@ -480,6 +485,7 @@ def test_segmented_time_solve_matches_sequential(prec, tol, nt_el, pt):
             prob.close()
     finally:
         P.stst_set_time_solver(0)
+        P.stst_set_pencil(0)
     assert out[1][1][2] == 0
     if out[2][1][0] >= 2:
         assert out[2][1][2] == 1

@@ -62,15 +62,21 @@ def test_host_side_argument_checks_need_no_gpu():
             assert L.stst_set_time_solver(mode) == 0, mode
         for mode in (-1, 3):
             assert L.stst_set_time_solver(mode) == ERR_ARG, mode
+        for mode in (0, 1, 2, 3):
+            assert L.stst_set_pencil(mode) == 0, mode
+        for mode in (-1, 4):
+            assert L.stst_set_pencil(mode) == ERR_ARG, mode
     finally:
         L.stst_set_autotune(1)
         L.stst_set_time_solver(0)
         L.stst_set_fused_transforms(0)
+        L.stst_set_pencil(0)
     n = ctypes.c_longlong()
     assert L.stst_sizes(None, ctypes.byref(n), None) == ERR_HANDLE
     assert L.stst_pcg_graph_info(None, None, None) == ERR_HANDLE
     assert L.stst_build_fd(None) == ERR_HANDLE
     assert L.stst_set_potential(None, 0, None) == ERR_HANDLE
+    assert L.stst_pencil_info(None, None) == ERR_HANDLE
     out = ctypes.c_int()
     bad = [(0, 4, 1.0, 2), (9, 4, 1.0, 2), (2, 0, 1.0, 2), (2, 4, 0.0, 2), (2, 4, -1.0, 1), (2, 4, 1.0, 3),
            (1, 1, 1.0, 2)]  # the last leaves no function after dropping both ends
