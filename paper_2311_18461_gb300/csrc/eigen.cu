@@ -840,8 +840,8 @@ int fd_setup_launch(stst_problem *h) {
   }
   STST_CUDA(cudaGetLastError());
   }  // profiler scopes do not nest: the hfactor record ends here
-  // the FP32 factors in the pencil order as well (pencil kernel)
-  if (h->Gp32) STST_TRY(launch_factor_pencil(h, st));
+  // the FP32 factors in the pencil order as well, when the pencil kernel runs (or before the tuner decides)
+  if (h->Gp32 && (!h->tuned || h->pencil)) STST_TRY(launch_factor_pencil(h, st));
   // transfer matrices of the segmented (parallel-in-time) time solves
   STST_TRY(launch_time_transfer<float>(h->Hg32, h->Hd32, h->n_t(), h->N_s, h->dir[0].p, h->ts_S[0], h->ts_L[0],
                                        h->Tf[0], h->Tb[0], st));

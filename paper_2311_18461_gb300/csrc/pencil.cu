@@ -323,6 +323,7 @@ bool pencil_fits(const stst_problem *h, int CL) {
 
 int launch_factor_pencil(stst_problem *h, cudaStream_t s) {
   const long long total = (long long)h->n_t() * (h->dir[0].p + 1) * h->N_s;
+  STST_PROF("factor_pencil", s);
   k_factor_pencil<<<grid_for(total, 256), 256, 0, s>>>((const float2 *)h->Hg32, h->Hd32, (float2 *)h->Gp32, h->Dp32,
                                                        h->n_t(), h->dir[0].p, h->N_s, h->dir[h->d].n);
   STST_CUDA(cudaGetLastError());
