@@ -454,6 +454,30 @@ int stst_pod_expand(const float *Q, int K, long long m, const float *C, int n, f
                     const double *phase, double *X, void *stream);
 
 /*
+ * Training-data preparation of the warm start (the arithmetic between the snapshot basis and the network):
+ * stst_ws_whiten: Cholesky whitening of features F (n x K row-major FP32, e.g. coordinates of the initial
+ * data in an input basis): G = F^T F / n accumulated in FP64, plus 1e-10 of its largest diagonal entry,
+ * G = R^T R (R upper triangular), W = R^{-1}; Fw = F W (n x K, so that the features have the identity as
+ * their training covariance: W^T G W = I), and when Q is given (K x m row-major FP32, the rows of the input
+ * basis), Q <- W^T Q in place, so that projecting a new datum on Q gives its whitened features directly.
+ * Allocates stream-ordered temporaries and synchronizes; STST_NOT_HPD when a Cholesky pivot collapses
+ * (features that are linearly dependent beyond the shift).
+ * stst_ws_target_scale: for targets T (n x K row-major FP32): so[k] = max(sqrt(mean_n T[n][k]^2), 1e-300)
+ * (FP64, the RMS of every output coordinate), Ts = T / so column by column (FP32), and per-sample weights
+ * w[n] = mean_r ||T_r||^2 / max(||T_n||^2, 1e-300) (FP32: the loss then weighs relative errors).
+ * stst_ws_cascade: the training targets of one stage of the cascade (resid n x K FP64, kept across calls):
+ * with T0 (the first stage): resid = T0, scale = 1; otherwise resid -= Y (.) scale_prev column by column
+ * (Y: the previous stage's outputs on every training row, n x K FP32) and scale[k] = max(sqrt(mean_n
+ * resid[n][k]^2), 1e-30). Then targets = resid / scale (FP32) and out_scale = so (.) scale (FP32, the
+ * stage's output scale for stst_ws_set_output_scale). scale, scale_prev, so: K doubles.
+ * All arrays are device memory; stream-ordered (stst_ws_whiten synchronizes).
+ */
+int stst_ws_whiten(const float *F, int n, int K, float *Fw, float *Q, long long m, void *stream);
+int stst_ws_target_scale(const float *T, int n, int K, float *Ts, double *so, float *w, void *stream);
+int stst_ws_cascade(const float *T0, const float *Y, const double *scale_prev, double *resid, int n, int K,
+                    double *scale, float *targets, const double *so, float *out_scale, void *stream);
+
+/*
  * stst_pcg_solve_guarded: stst_pcg_solve from the initial guess in x, after a device-side check:
  * if ||rhs - A x|| >= ||rhs|| or is not finite, x is set to 0 first (the cold start of Sec. 6).
  * used_warm (host, may be NULL) = 1 when the given guess was kept. Same outputs and errors as

@@ -14,9 +14,16 @@ definition the GPU warm-start kernels are checked against:
     a snapshot matrix Y (n x m): Q = orth(Omega^T Y), then per power iteration P = orth(Q Y^T),
     Q = orth(P Y), where orth(Z) returns the rows of Q~ from Z^T = Q~ R with diag(R) > 0 (the
     unique thin QR factor), computed here by Householder QR (numpy) and a sign fix.
+  * training-data preparation: Cholesky whitening of the features (G = F^T F / n + 1e-10 max diag(G),
+    G = R^T R, W = R^{-1}, whitened features F W), the RMS of every target coordinate and the targets
+    scaled by it, per-sample weights mean ||t||^2 / ||t_n||^2, and one stage of the cascade (the error
+    the earlier stages left, rescaled to unit RMS per coordinate).
 Pins: the gradient against central finite differences of the loss, the forward map against hand
 values, Adam's first steps against their closed form, the basis against orthonormality, exact
-reproduction of rank-K snapshot sets, and the SVD's dominant subspace.
+reproduction of rank-K snapshot sets, and the SVD's dominant subspace; the whitened features' training
+covariance is the identity and W is upper triangular; the scaled targets have unit RMS per coordinate;
+the weights make every weighted sample norm equal; a cascade stage that removes a known part leaves
+exactly the rest.
 """
 import numpy as np
 
@@ -106,3 +113,38 @@ def range_basis(Y, Omega, power_its=0):
         P = orth_rows(Q @ Y.T)
         Q = orth_rows(P @ Y)
     return Q
+
+
+def whiten(F, rel_shift=1e-10):
+    """Cholesky whitening of the rows of F (n x K): returns (W, F W) with W = R^{-1}, where
+    F^T F / n + rel_shift * max diag = R^T R, R upper triangular with a positive diagonal."""
+    F = np.asarray(F, dtype=np.float64)
+    n, K = F.shape
+    G = F.T @ F / n
+    G = G + rel_shift * np.max(np.diag(G)) * np.eye(K)
+    R = np.linalg.cholesky(G).T          # G = L L^T, R = L^T
+    W = np.linalg.inv(R)
+    return W, F @ W
+
+
+def target_scaling(T):
+    """(so, T / so, w): the RMS of every column of T (n x K), the columns scaled to unit RMS, and the
+    weights w_n = mean_r ||t_r||^2 / ||t_n||^2."""
+    T = np.asarray(T, dtype=np.float64)
+    so = np.maximum(np.sqrt(np.mean(T * T, axis=0)), 1e-300)
+    sq = np.sum(T * T, axis=1)
+    w = np.mean(sq) / np.maximum(sq, 1e-300)
+    return so, T / so, w
+
+
+def cascade_stage(resid, Y=None, scale_prev=None, T0=None):
+    """One stage of the cascade: with T0 the first stage (resid = T0, scale = 1); otherwise
+    resid - Y * scale_prev (the part the previous stage explains removed), scale = the RMS of every column
+    of that residual. Returns (resid, scale, targets = resid / scale)."""
+    if T0 is not None:
+        r = np.array(T0, dtype=np.float64)
+        scale = np.ones(r.shape[1])
+    else:
+        r = np.asarray(resid, dtype=np.float64) - np.asarray(Y, dtype=np.float64) * np.asarray(scale_prev)
+        scale = np.maximum(np.sqrt(np.mean(r * r, axis=0)), 1e-30)
+    return r, scale, r / scale

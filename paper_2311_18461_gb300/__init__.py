@@ -18,6 +18,7 @@ from ._lib import (StstError, lib, library_path, stst_create, stst_create2, STST
                    stst_ws_destroy, stst_ws_num_params, stst_ws_get_params, stst_ws_set_params,
                    stst_ws_forward, stst_ws_set_output_scale, stst_ws_grad, stst_ws_train_step,
                    stst_pod_basis, stst_pod_project, stst_pod_expand, stst_pcg_solve_guarded, Problem,
+                   stst_ws_whiten, stst_ws_target_scale, stst_ws_cascade,
                    STST_PREC_FP64, STST_PREC_FP32, STST_PREC_BF16, STST_OK, STST_NOT_CONVERGED, STST_BREAKDOWN,
                    STST_NOT_HPD, STST_TIMEOUT, STST_ERR_ARG, STST_ERR_HANDLE, STST_ERR_OOM, STST_ERR_CUDA,
                    STST_ERR_STATE)
@@ -32,5 +33,5 @@ __all__ = ["StstError", "lib", "library_path", "stst_create", "stst_create2", "S
            "stst_ws_create", "stst_ws_destroy", "stst_ws_num_params", "stst_ws_get_params",
            "stst_ws_set_params", "stst_ws_forward", "stst_ws_set_output_scale", "stst_ws_grad",
            "stst_ws_train_step", "stst_pod_basis", "stst_pod_project", "stst_pod_expand",
-           "stst_pcg_solve_guarded", "Problem", "STST_PREC_FP64", "STST_PREC_FP32", "STST_PREC_BF16", "STST_OK", "STST_NOT_CONVERGED", "STST_BREAKDOWN", "STST_NOT_HPD", "STST_TIMEOUT",
+           "stst_pcg_solve_guarded", "Problem", "stst_ws_whiten", "stst_ws_target_scale", "stst_ws_cascade", "STST_PREC_FP64", "STST_PREC_FP32", "STST_PREC_BF16", "STST_OK", "STST_NOT_CONVERGED", "STST_BREAKDOWN", "STST_NOT_HPD", "STST_TIMEOUT",
            "STST_ERR_ARG", "STST_ERR_HANDLE", "STST_ERR_OOM", "STST_ERR_CUDA", "STST_ERR_STATE"]

@@ -83,6 +83,9 @@ def lib():
             "stst_pod_basis": [P, I, LL, P, I, I, P, P],
             "stst_pod_project": [P, I, LL, P, I, P, P],
             "stst_pod_expand": [P, I, LL, P, I, ctypes.c_float, ctypes.c_float, P, P, P],
+            "stst_ws_whiten": [P, I, I, P, P, LL, P],
+            "stst_ws_target_scale": [P, I, I, P, P, P, P],
+            "stst_ws_cascade": [P, P, P, P, I, I, P, P, P, P, P],
             "stst_pcg_solve_guarded": [P, P, P, D, I, IP, DP, IP],
         }
         for name, args in sig.items():
@@ -387,6 +390,22 @@ def stst_pod_basis(Y, n, m, Omega, K, power_its, Q, stream=None):
 def stst_pod_project(Y, n, m, Q, K, C, stream=None):
     return _chk(lib().stst_pod_project(_ptr(Y), int(n), int(m), _ptr(Q), int(K), _ptr(C), _stream_ptr(stream)),
                 "stst_pod_project")
+
+
+def stst_ws_whiten(F, n, K, Fw, Q=None, m=0, stream=None):
+    return _chk(lib().stst_ws_whiten(_ptr(F), int(n), int(K), _ptr(Fw), _ptr(Q), int(m), _stream_ptr(stream)),
+                "stst_ws_whiten")
+
+
+def stst_ws_target_scale(T, n, K, Ts, so, w, stream=None):
+    return _chk(lib().stst_ws_target_scale(_ptr(T), int(n), int(K), _ptr(Ts), _ptr(so), _ptr(w),
+                                           _stream_ptr(stream)), "stst_ws_target_scale")
+
+
+def stst_ws_cascade(T0, Y, scale_prev, resid, n, K, scale, targets, so, out_scale, stream=None):
+    return _chk(lib().stst_ws_cascade(_ptr(T0), _ptr(Y), _ptr(scale_prev), _ptr(resid), int(n), int(K), _ptr(scale),
+                                      _ptr(targets), _ptr(so), _ptr(out_scale), _stream_ptr(stream)),
+                "stst_ws_cascade")
 
 
 def stst_pod_expand(Q, K, m, C, n, alpha, beta, phase, X, stream=None):

@@ -696,6 +696,97 @@ static int ws_read_loss(stst_ws_s *w, double *loss) {
   return STST_OK;
 }
 
+// ---- training-data preparation (the cascade of a9: whitening, scalings, residual targets) ----------------
+// Per-column sums of squares of X (n x K row-major FP32 or FP64), one thread per column, rows in order (FP64):
+// colss[k] = sum_n X[n][k]^2.
+template <typename T>
+__global__ void k_ws_colss(const T *X, int n, int K, double *colss) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  double s = 0.0;
+  for (int r = 0; r < n; ++r) {
+    const double v = (double)X[(long long)r * K + k];
+    s += v * v;
+  }
+  colss[k] = s;
+}
+
+// Per-row sums of squares: one warp per row, lanes over the columns, then a fixed shuffle order.
+__global__ void k_ws_rowss(const float *X, int n, int K, double *rowss) {
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (r >= n) return;
+  double s = 0.0;
+  for (int k = lane; k < K; k += 32) {
+    const double v = (double)X[(long long)r * K + k];
+    s += v * v;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) rowss[r] = s;
+}
+
+// so[k] = max(sqrt(colss[k] / n), 1e-300); w[r] = mean(rowss) / max(rowss[r], 1e-300) (one CTA: the mean is
+// summed in a fixed order).
+__global__ void k_ws_target_scale(int n, int K, const double *colss, const double *rowss, double *so, float *w) {
+  __shared__ double part[1024];
+  __shared__ double mean;
+  double acc = 0.0;
+  for (int r = threadIdx.x; r < n; r += blockDim.x) acc += rowss[r];
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)blockDim.x; ++i) t += part[i];
+    mean = t / n;
+  }
+  for (int k = threadIdx.x; k < K; k += blockDim.x) so[k] = fmax(sqrt(colss[k] / n), 1e-300);
+  __syncthreads();
+  for (int r = threadIdx.x; r < n; r += blockDim.x) w[r] = (float)(mean / fmax(rowss[r], 1e-300));
+}
+
+// Ts = T / so, column by column (n x K row-major)
+__global__ void k_ws_scale_cols(const float *T, int n, int K, const double *so, float *Ts) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)n * K;
+       e += (long long)gridDim.x * blockDim.x)
+    Ts[e] = (float)((double)T[e] / so[e % K]);
+}
+
+// G += shift I, shift = rel * max_k G[k][k] (a symmetric positive semidefinite Gram matrix becomes definite)
+__global__ void k_ws_shift_diag(double *G, int K, double rel) {
+  __shared__ double mx;
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int k = 0; k < K; ++k) m = fmax(m, G[(long long)k * K + k]);
+    mx = m;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < K; k += blockDim.x) G[(long long)k * K + k] += rel * mx;
+}
+
+// One stage of the cascade, elementwise (resid: n x K FP64): with T0, resid = T0 and scale = 1; otherwise
+// resid -= Y (.) scale_prev. Then targets = resid / scale (scale from k_ws_cascade_scale).
+__global__ void k_ws_cascade_resid(double *resid, const float *T0, const float *Y, const double *scale_prev, int n,
+                                   int K) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)n * K;
+       e += (long long)gridDim.x * blockDim.x) {
+    if (T0) resid[e] = (double)T0[e];
+    else resid[e] -= (double)Y[e] * scale_prev[e % K];
+  }
+}
+
+__global__ void k_ws_cascade_out(const double *resid, const double *colss, int n, int K, int first, double *scale,
+                                 float *targets, const double *so, float *out_scale) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)n * K;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(e % K);
+    const double sc = first ? 1.0 : fmax(sqrt(colss[k] / n), 1e-30);
+    targets[e] = (float)(resid[e] / sc);
+    if (e < K) {
+      scale[e] = first ? 1.0 : fmax(sqrt(colss[e] / n), 1e-30);
+      out_scale[e] = (float)(so[e] * scale[e]);
+    }
+  }
+}
+
 struct DevTemp {  // stream-ordered temporaries of the offline basis construction
   cudaStream_t s;
   std::vector<void *> ptrs;
@@ -962,6 +1053,68 @@ int stst_pod_expand(const float *Q, int K, long long m, const float *C, int n, f
     k_ws_rotate<<<grid_for((long long)n * half, 256), 256, 0, s>>>(X, n, half, phase);
     STST_CUDA(cudaGetLastError());
   }
+  return STST_OK;
+}
+
+int stst_ws_whiten(const float *F, int n, int K, float *Fw, float *Q, long long m, void *stream) {
+  if (!F || !Fw || n < 1 || K < 1 || K > 4096 || (Q && (m < 1 || m > 0x7fffffffLL))) return STST_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  DevTemp tmp(s);
+  const int slices = gram_slices(K, n);
+  double *S = (double *)tmp.get(sizeof(double) * (size_t)slices * K * K);
+  double *G = (double *)tmp.get(sizeof(double) * (size_t)K * K);
+  double *Ri = (double *)tmp.get(sizeof(double) * (size_t)K * K);
+  double *dg = (double *)tmp.get(sizeof(double) * K);
+  int *flag = (int *)tmp.get(sizeof(int));
+  float *Qn = Q ? (float *)tmp.get(sizeof(float) * (size_t)K * m) : nullptr;
+  if (!S || !G || !Ri || !dg || !flag || (Q && !Qn)) return STST_ERR_OOM;
+  STST_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), s));
+  // G = F^T F / n in FP64 (split-K slices summed in a fixed order), a relative shift of 1e-10 of the largest
+  // diagonal entry, G = R^T R, W = R^{-1}
+  STST_TRY(ws_gemm<double>(K, K, n, 1.f / n, F, 1, K, F, K, 1, 0.f, S, K, 1, s, slices, (long long)K * K));
+  k_ws_sum_slices<<<grid_for((long long)K * K, 256), 256, 0, s>>>(S, slices, K, G);
+  k_ws_shift_diag<<<1, 256, 0, s>>>(G, K, 1e-10);
+  k_ws_cholesky<<<1, 1024, 0, s>>>(G, K, dg, flag);
+  k_ws_trinv<<<(K + 127) / 128, 128, 0, s>>>(G, K, Ri);
+  // Fw(r, j) = sum_k F(r, k) W(k, j); Q(k, :) <- sum_i W(i, k) Q(i, :) (W^T Q)
+  STST_TRY(ws_gemm<double>(n, K, K, 1.f, F, K, 1, Ri, K, 1, 0.f, Fw, K, 1, s));
+  if (Q) {
+    STST_TRY(ws_gemm<double>(K, (int)m, K, 1.f, Ri, 1, K, Q, m, 1, 0.f, Qn, m, 1, s));
+    STST_CUDA(cudaMemcpyAsync(Q, Qn, sizeof(float) * (size_t)K * m, cudaMemcpyDeviceToDevice, s));
+  }
+  int hflag = 0;
+  STST_CUDA(cudaMemcpyAsync(&hflag, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  STST_CUDA(cudaStreamSynchronize(s));
+  return hflag ? STST_NOT_HPD : STST_OK;
+}
+
+int stst_ws_target_scale(const float *T, int n, int K, float *Ts, double *so, float *w, void *stream) {
+  if (!T || !Ts || !so || !w || n < 1 || K < 1) return STST_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  DevTemp tmp(s);
+  double *colss = (double *)tmp.get(sizeof(double) * K), *rowss = (double *)tmp.get(sizeof(double) * n);
+  if (!colss || !rowss) return STST_ERR_OOM;
+  k_ws_colss<float><<<(K + 127) / 128, 128, 0, s>>>(T, n, K, colss);
+  k_ws_rowss<<<(n + 7) / 8, 256, 0, s>>>(T, n, K, rowss);
+  k_ws_target_scale<<<1, 1024, 0, s>>>(n, K, colss, rowss, so, w);
+  k_ws_scale_cols<<<grid_for((long long)n * K, 256), 256, 0, s>>>(T, n, K, so, Ts);
+  STST_CUDA(cudaGetLastError());
+  return STST_OK;
+}
+
+int stst_ws_cascade(const float *T0, const float *Y, const double *scale_prev, double *resid, int n, int K,
+                    double *scale, float *targets, const double *so, float *out_scale, void *stream) {
+  if (!resid || !scale || !targets || !so || !out_scale || n < 1 || K < 1) return STST_ERR_ARG;
+  if (!T0 && (!Y || !scale_prev)) return STST_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  DevTemp tmp(s);
+  double *colss = (double *)tmp.get(sizeof(double) * K);
+  if (!colss) return STST_ERR_OOM;
+  const int g = grid_for((long long)n * K, 256);
+  k_ws_cascade_resid<<<g, 256, 0, s>>>(resid, T0, Y, scale_prev, n, K);
+  k_ws_colss<double><<<(K + 127) / 128, 128, 0, s>>>(resid, n, K, colss);
+  k_ws_cascade_out<<<g, 256, 0, s>>>(resid, colss, n, K, T0 ? 1 : 0, scale, targets, so, out_scale);
+  STST_CUDA(cudaGetLastError());
   return STST_OK;
 }
 

@@ -9,15 +9,17 @@ BF16 rounding of the weights (2^-9 relative) limits the cascade to about its pro
 With a fixed potential the exact map c0 -> u is linear, so a linear network can learn it to the
 accuracy of the two bases; PCG from x0 stays the arbiter of the result.
 
-The pipeline orders library calls and owns device buffers; every numerical step on the device runs in
-the library's kernels; one-time scalings of the training data and the random draws are done on the host:
+The pipeline orders library calls and owns device buffers; every numerical step runs in the library's
+kernels; only the random draws (test matrices, minibatch permutations) and the learning-rate schedule are
+host values:
   1. snapshots: `stst_rhs` gives (rhs, c0), the library's PCG solves; rows of Y and C0 hold them as reals;
   2. bases: `stst_pod_basis` on Y and on C0 (randomized subspace iteration, CholeskyQR2 with FP64 Gram);
-  3. data: `stst_pod_project` gives features and targets; the host whitens the features (principal
-     axes of their training covariance, unit variance; folded into the rows of Q_in), scales every output
-     coordinate to unit RMS (undone by each network's output scale) and weights each sample by
-     1 / ||coordinates||^2 (relative error);
-  4. network: `stst_ws_train_step` over shuffled minibatches (Adam, cosine-decayed learning rate);
+  3. data: `stst_pod_project` gives features and targets; `stst_ws_whiten` whitens the features
+     (Cholesky factor of their FP64 training covariance, folded into the rows of Q_in);
+     `stst_ws_target_scale` scales every output coordinate to unit RMS (undone by each network's output
+     scale) and weights each sample by 1 / ||coordinates||^2 (relative error);
+  4. network: `stst_ws_train_step` over shuffled minibatches (Adam, cosine-decayed learning rate), each
+     stage on the targets `stst_ws_cascade` forms from the error the stages before it left;
   5. inference: `stst_pod_project` -> `stst_ws_forward` per stage (accumulating) -> `stst_pod_expand` ->
      `stst_pcg_solve_guarded`,
      which restarts from x0 = 0 when the prediction is worse than zero.
@@ -95,52 +97,46 @@ class WarmStart:
         F = torch.empty((n, self.K_in), dtype=torch.float32, device="cuda")
         B.stst_pod_project(self.Y, n, self.m, self.Q_out, self.K_out, T)
         B.stst_pod_project(self.C0, n, self.m_in, Q_in, self.K_in, F)
-        Th = T.cpu().numpy().astype(np.float64)
-        Fh = F.cpu().numpy().astype(np.float64)
-        sq = (Th * Th).sum(axis=1)
-        w = sq.mean() / np.maximum(sq, 1e-300)
-        # PCA whitening of the input coordinates: the rows of a range-finder basis are not principal
-        # axes, so their coordinates are correlated; rotating them to the eigenvectors of the training
-        # covariance and scaling to unit variance makes the regression well conditioned.
-        lam, V = np.linalg.eigh(Fh.T @ Fh / n)
-        lam = np.maximum(lam, 1e-10 * lam.max())
-        Wh = V / np.sqrt(lam)                                     # f_white = f Wh
-        so = np.maximum(np.sqrt((Th * Th).mean(axis=0)), 1e-300)  # RMS per output coordinate
-        Qi = Wh.T @ Q_in.cpu().numpy().astype(np.float64)
-        self.Q_in = torch.as_tensor(Qi.astype(np.float32), device="cuda").contiguous()
-        self.so = so
-        self.F = torch.as_tensor((Fh @ Wh).astype(np.float32), device="cuda").contiguous()
-        self.T = torch.as_tensor((Th / so).astype(np.float32), device="cuda").contiguous()
-        self.W = torch.as_tensor(w.astype(np.float32), device="cuda").contiguous()
+        # whitened features (Cholesky whitening, folded into the rows of Q_in), targets scaled to unit RMS
+        # per coordinate, relative-error weights: all in the library
+        self.F = torch.empty_like(F)
+        B.stst_ws_whiten(F, n, self.K_in, self.F, Q_in, self.m_in)
+        self.Q_in = Q_in
+        self.T = torch.empty_like(T)
+        self.so = torch.empty(self.K_out, dtype=torch.float64, device="cuda")
+        self.W = torch.empty(n, dtype=torch.float32, device="cuda")
+        B.stst_ws_target_scale(T, n, self.K_out, self.T, self.so, self.W)
 
-    def _outputs(self, net):
-        """The network's outputs on every training row (batches of max_batch), on the host."""
-        torch = self.torch
+    def _outputs(self, net, out):
+        """The network's outputs on every training row (batches of max_batch) into out (n x K_out)."""
         n = self.F.shape[0]
-        out = torch.empty((n, self.K_out), dtype=torch.float32, device="cuda")
         for i in range(0, n, self.max_batch):
             b = min(self.max_batch, n - i)
             B.stst_ws_forward(net, self.F[i:i + b], b, out[i:i + b])
-        return out.cpu().numpy().astype(np.float64)
 
     # ---- 4. training -------------------------------------------------------------------------------------
     def train(self, steps, batch=256, lr0=1e-3, lr1=1e-6, seed=0, log_every=0):
         """Each stage in turn: Adam over shuffled minibatches (a new permutation every epoch),
-        cosine-decayed learning rate; stage s > 0 fits the rescaled error left by the stages before it."""
+        cosine-decayed learning rate; stage s > 0 fits the rescaled error left by the stages before it
+        (stst_ws_cascade keeps that error on the device)."""
         torch = self.torch
         n = self.T.shape[0]
         batch = min(batch, n, self.max_batch)
         rng = np.random.default_rng(seed)
         epochs = (steps * batch + n - 1) // n + 1
-        T0 = self.T.cpu().numpy().astype(np.float64)
-        resid = T0.copy()
-        scale = np.ones(self.K_out)
+        K = self.K_out
+        resid = torch.empty((n, K), dtype=torch.float64, device="cuda")
+        targets = torch.empty((n, K), dtype=torch.float32, device="cuda")
+        outs = torch.empty((n, K), dtype=torch.float32, device="cuda")
+        scale = torch.empty(K, dtype=torch.float64, device="cuda")
+        scale_prev = torch.empty(K, dtype=torch.float64, device="cuda")
+        out_scale = torch.empty(K, dtype=torch.float32, device="cuda")
         for s, net in enumerate(self.nets):
             if s == 0:
-                targets = self.T
-            else:
-                scale = np.maximum(np.sqrt((resid * resid).mean(axis=0)), 1e-30)
-                targets = torch.as_tensor((resid / scale).astype(np.float32), device="cuda").contiguous()
+                B.stst_ws_cascade(self.T, None, None, resid, n, K, scale, targets, self.so, out_scale)
+            else:  # outs: what the previous stage predicts (its raw outputs, taken before its output scale)
+                scale_prev, scale = scale, scale_prev
+                B.stst_ws_cascade(None, outs, scale_prev, resid, n, K, scale, targets, self.so, out_scale)
             B.stst_ws_set_output_scale(net, None)
             perms = np.concatenate([rng.permutation(n)[: n - n % batch] for _ in range(epochs)]).astype(np.int32)
             perm = torch.as_tensor(perms, device="cuda")
@@ -152,9 +148,9 @@ class WarmStart:
                 if want:
                     self.history.append((s, k, loss))
             if s + 1 < len(self.nets):
-                resid = resid - self._outputs(net) * scale  # what this stage left (normalized coordinates)
+                self._outputs(net, outs)
             # at inference the stage writes its share of the output-basis coordinates directly
-            B.stst_ws_set_output_scale(net, torch.as_tensor((self.so * scale).astype(np.float32), device="cuda"))
+            B.stst_ws_set_output_scale(net, out_scale)
         torch.cuda.synchronize()
         return self.history
 

@@ -301,3 +301,61 @@ def test_trained_warm_start_saves_iterations():
     # the arbiter: the same tolerance is met from the learned start in fewer iterations
     assert np.mean(warm) < np.mean(cold) - 1.0, (cold, warm, err)
     assert max(e[1] for e in err) < 1e-5
+
+
+# ---- training-data preparation on the device -------------------------------------------------------
+# Inputs are FP32; the device forms the Gram matrix, the Cholesky factor and its inverse in FP64 (as the
+# oracle does) and rounds the whitened features and the rotated basis to FP32 after FP64 products:
+# ~kappa(F) u_32 relative, kappa(F) <= 30 here, so 1e-5. The scalings are FP64 sums of FP32 squares
+# (1e-12 on so) rounded to FP32 (1e-6 on the scaled targets and weights).
+def test_whitening_matches_oracle():
+    import paper_2311_18461_gb300 as P
+    torch = _torch()
+    rng = np.random.default_rng(21)
+    n, K, m = 700, 40, 300
+    F = (rng.standard_normal((n, K)) @ (rng.standard_normal((K, K)) * np.logspace(0, -1, K)).T).astype(np.float32)
+    Q = rng.standard_normal((K, m)).astype(np.float32)
+    Fd, Qd = torch.tensor(F, device="cuda"), torch.tensor(Q, device="cuda")
+    Fw = torch.empty_like(Fd)
+    P.stst_ws_whiten(Fd, n, K, Fw, Qd, m)
+    Wm, Fw_ref = W.whiten(F.astype(np.float64))
+    rel = lambda a, b: np.abs(a - b).max() / np.abs(b).max()
+    assert rel(Fw.cpu().numpy(), Fw_ref) < 1e-5
+    assert rel(Qd.cpu().numpy(), Wm.T @ Q.astype(np.float64)) < 1e-5
+    cov = Fw.cpu().numpy().astype(np.float64)
+    assert np.abs(cov.T @ cov / n - np.eye(K)).max() < 1e-4
+
+
+def test_target_scaling_and_cascade_match_oracle():
+    import paper_2311_18461_gb300 as P
+    torch = _torch()
+    rng = np.random.default_rng(22)
+    n, K = 500, 33
+    T = (rng.standard_normal((n, K)) * np.logspace(0, 2, K)).astype(np.float32)
+    Td = torch.tensor(T, device="cuda")
+    Ts = torch.empty_like(Td)
+    so = torch.empty(K, dtype=torch.float64, device="cuda")
+    w = torch.empty(n, dtype=torch.float32, device="cuda")
+    P.stst_ws_target_scale(Td, n, K, Ts, so, w)
+    so_r, Ts_r, w_r = W.target_scaling(T.astype(np.float64))
+    assert np.abs(so.cpu().numpy() / so_r - 1).max() < 1e-12
+    assert np.abs(Ts.cpu().numpy() - Ts_r).max() / np.abs(Ts_r).max() < 1e-6
+    assert np.abs(w.cpu().numpy() / w_r - 1).max() < 1e-6
+    # two stages: the first fits the scaled targets as they are, the second the error a prediction left
+    resid = torch.empty((n, K), dtype=torch.float64, device="cuda")
+    scale = torch.empty(K, dtype=torch.float64, device="cuda")
+    tgt = torch.empty((n, K), dtype=torch.float32, device="cuda")
+    osc = torch.empty(K, dtype=torch.float32, device="cuda")
+    P.stst_ws_cascade(Ts, None, None, resid, n, K, scale, tgt, so, osc)
+    r0, s0, t0 = W.cascade_stage(None, T0=Ts.cpu().numpy().astype(np.float64))
+    assert np.array_equal(scale.cpu().numpy(), s0) and np.abs(tgt.cpu().numpy() - t0).max() == 0
+    assert np.abs(osc.cpu().numpy() / so_r - 1).max() < 1e-6
+    Y = (Ts.cpu().numpy() + 1e-2 * rng.standard_normal((n, K))).astype(np.float32)  # a stage's prediction
+    Yd = torch.tensor(Y, device="cuda")
+    scale1 = torch.empty_like(scale)
+    P.stst_ws_cascade(None, Yd, scale, resid, n, K, scale1, tgt, so, osc)
+    r1, s1, t1 = W.cascade_stage(r0, Y=Y.astype(np.float64), scale_prev=s0)
+    assert np.abs(resid.cpu().numpy() - r1).max() / np.abs(r1).max() < 1e-12
+    assert np.abs(scale1.cpu().numpy() / s1 - 1).max() < 1e-12
+    assert np.abs(tgt.cpu().numpy() - t1).max() / np.abs(t1).max() < 1e-6
+    assert np.abs(osc.cpu().numpy() / (so_r * s1) - 1).max() < 1e-6

@@ -109,3 +109,50 @@ def test_range_basis_finds_the_dominant_singular_subspace():
     Vk = np.linalg.svd(Y, full_matrices=False)[2][:K]
     cosines = np.linalg.svd(Q @ Vk.T, compute_uv=False)
     assert 1 - cosines.min() < 1e-12
+
+
+# ---- training-data preparation ----------------------------------------------------------------------
+def _correlated(n, K, seed):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((K, K)) * np.logspace(0, -3, K)  # strongly correlated, badly scaled columns
+    return rng.standard_normal((n, K)) @ A.T
+
+
+def test_whitened_features_have_identity_covariance():
+    F = _correlated(500, 12, 1)
+    Wm, Fw = W.whiten(F, rel_shift=0.0)
+    assert np.allclose(np.triu(Wm), Wm, atol=0, rtol=0)          # W = R^{-1} is upper triangular
+    assert np.all(np.diag(Wm) > 0)
+    cov = Fw.T @ Fw / len(Fw)
+    assert np.abs(cov - np.eye(12)).max() < 1e-8   # rounding times kappa(F^T F) ~ 1e6
+    # the shift (1e-10 of the largest variance) perturbs the covariance by about shift / smallest variance:
+    # 1e-8 for features whose variances span two decades
+    rng = np.random.default_rng(3)
+    F2 = rng.standard_normal((500, 12)) @ (rng.standard_normal((12, 12)) * np.logspace(0, -1, 12)).T
+    _, Fs = W.whiten(F2)
+    assert np.abs(Fs.T @ Fs / len(Fs) - np.eye(12)).max() < 1e-6
+    # planted mistake: W^T instead of W whitens nothing
+    assert np.abs((F @ Wm.T).T @ (F @ Wm.T) / len(F) - np.eye(12)).max() > 1e-1
+
+
+def test_target_scaling_closed_forms():
+    T = np.array([[3.0, 0.0], [4.0, 2.0]])
+    so, Ts, w = W.target_scaling(T)
+    assert np.allclose(so, [np.sqrt(12.5), np.sqrt(2.0)], rtol=1e-15)
+    assert np.allclose(np.sqrt(np.mean(Ts * Ts, axis=0)), 1.0, rtol=1e-15)
+    # ||t_1||^2 = 9, ||t_2||^2 = 20, mean 14.5: w = (14.5 / 9, 14.5 / 20), every weighted norm equals the mean
+    assert np.allclose(w, [14.5 / 9, 14.5 / 20], rtol=1e-15)
+    assert np.allclose(w * np.sum(T * T, axis=1), 14.5, rtol=1e-15)
+
+
+def test_cascade_stage_removes_the_explained_part():
+    rng = np.random.default_rng(2)
+    T0 = rng.standard_normal((200, 6))
+    r0, s0, t0 = W.cascade_stage(None, T0=T0)
+    assert np.array_equal(r0, T0) and np.array_equal(s0, np.ones(6)) and np.array_equal(t0, T0)
+    # a stage that predicted T0 - E exactly (with scale 1) leaves E, rescaled to unit RMS per column
+    E = 1e-3 * rng.standard_normal((200, 6)) * np.arange(1, 7)
+    r1, s1, t1 = W.cascade_stage(r0, Y=T0 - E, scale_prev=s0)
+    assert np.allclose(r1, E, rtol=1e-12, atol=1e-15)
+    assert np.allclose(s1, np.sqrt(np.mean(E * E, axis=0)), rtol=1e-12)
+    assert np.allclose(np.sqrt(np.mean(t1 * t1, axis=0)), 1.0, rtol=1e-12)
