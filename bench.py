@@ -83,6 +83,8 @@ def parse():
     ap.add_argument("--stages", type=int, default=3, help="network stages of the c5 warm start")
     ap.add_argument("--train-steps", type=int, default=6000, help="Adam steps per stage (c5)")
     ap.add_argument("--basis", type=int, default=1024, help="basis size K of the c5 warm start")
+    ap.add_argument("--hidden", default="", help="c5: comma-separated widths of tanh hidden layers (empty: linear "
+                                                 "stages)")
     return ap.parse_args()
 
 
@@ -399,7 +401,8 @@ def run_warmstart(args):
     rng = np.random.default_rng(seed)
     train = [wavepacket_params(rng, 2) for _ in range(args.train)]
     K = args.basis
-    ws = WarmStart(prob, K, K, hidden=(), stages=args.stages, max_batch=256, seed=seed)
+    hidden = tuple(int(v) for v in args.hidden.split(",") if v.strip())
+    ws = WarmStart(prob, K, K, hidden=hidden, stages=args.stages, max_batch=256, seed=seed)
     t0 = time.time()
     its_train = ws.collect([lambda par=par: u0_qp(par) for par in train], tol=tol)
     torch.cuda.synchronize()
@@ -495,8 +498,10 @@ def run_warmstart(args):
                                f"wavepacket u0 (centre, width, momentum, phase drawn), tol {tol:g}",
                    "step": "one new problem: network inference (project c0, forward of every stage, expand) + "
                            "guarded PCG from the predicted iterate",
-                   "model": f"{args.stages} linear stages {K}->{K}, {ws.n_params} parameters, BF16 weights, "
-                            f"FP32 accumulation", "training_solves": args.train,
+                   "model": (f"{args.stages} stages {K}->" + "".join(f"{h}->" for h in hidden) + f"{K}"
+                             + (" (tanh between layers)" if hidden else " (linear)")
+                             + f", {ws.n_params} parameters, BF16 weights, FP32 accumulation"),
+                   "training_solves": args.train,
                    "l2": "flushed (512 MB write) before each step", "parallelism": f"replicas x{world}"},
         "warm": {"ms": ms, "pcg_iterations_mean": statistics.mean(it_w), "x0_rel_err_median": statistics.median(e0s),
                  "final_rel_diff_vs_cold_max": max(diffs), "warm_start_kept": int(sum(used))},

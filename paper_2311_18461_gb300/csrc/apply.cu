@@ -57,69 +57,84 @@ struct PassK {
   double *dot_partials;
   double *dot2_partials;
   const int *done;
+  int balanced;  // 1: CTA b takes the contiguous range [b total / grid, (b + 1) total / grid); 0: grid-stride
 };
+
+// One output element idx of every output of the level (index arithmetic in I: 32-bit when the tensor has
+// fewer than 2^31 elements, which saves the long software sequence of a 64-bit division).
+template <typename R, int P, typename I>
+__device__ __forceinline__ void pass_element(const PassK &k, I idx, double &dacc, double &d2acc) {
+  using T = typename C2<R>::T;
+  const I inner = (I)k.inner, nmo = (I)k.n_mode_out;
+  const I c = idx % inner;
+  const I t = idx / inner;
+  const int j = (int)(t % nmo);
+  const I o = t / nmo;
+  const long long base = (long long)o * k.n_mode_in * k.inner + c;
+  for (int b = 0; b < k.n_out; ++b) {
+    R ax = 0, ay = 0;
+    for (int ci = k.c_start[b]; ci < k.c_start[b + 1]; ++ci) {
+      // the matrix already carries the contribution's coefficient
+      const T *in = (const T *)k.in[k.c_in[ci]];
+      const R *m = (const R *)k.c_mat[ci] + j * (2 * P + 1);
+      if (k.c_imag[ci]) {  // + i * (m x)
+#pragma unroll
+        for (int q = 0; q <= 2 * P; ++q) {
+          int jj = j + k.row_off - P + q;
+          if (jj >= 0 && jj < k.n_mode_in) {
+            T xv = in[base + (long long)jj * k.inner];
+            R mv = m[q];
+            ax -= mv * xv.y;
+            ay += mv * xv.x;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q <= 2 * P; ++q) {
+          int jj = j + k.row_off - P + q;
+          if (jj >= 0 && jj < k.n_mode_in) {
+            T xv = in[base + (long long)jj * k.inner];
+            R mv = m[q];
+            ax += mv * xv.x;
+            ay += mv * xv.y;
+          }
+        }
+      }
+    }
+    T *out = (T *)k.out[b];
+    if (k.epi == 1) {  // out = b - v
+      T bv = ((const T *)k.b)[idx];
+      ax = bv.x - ax;
+      ay = bv.y - ay;
+    }
+    T res;
+    res.x = ax;
+    res.y = ay;
+    out[idx] = res;
+    if (k.dotvec) {
+      T dv = ((const T *)k.dotvec)[idx];
+      dacc += (double)dv.x * (double)ax + (double)dv.y * (double)ay;  // Re(conj(d) * out)
+    }
+    if (k.dot2_partials) d2acc += (double)ax * ax + (double)ay * ay;
+  }
+}
 
 template <typename R, int P>
 __global__ void __launch_bounds__(512) k_pass(const __grid_constant__ PassK k) {
-  using T = typename C2<R>::T;
   if (k.done && *k.done) return;
   __shared__ double sh[32];
   const long long total = k.outer * k.n_mode_out * k.inner;
   double dacc = 0.0, d2acc = 0.0;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    long long c = idx % k.inner;
-    long long t = idx / k.inner;
-    int j = (int)(t % k.n_mode_out);
-    long long o = t / k.n_mode_out;
-    const long long base = o * k.n_mode_in * k.inner + c;
-    for (int b = 0; b < k.n_out; ++b) {
-      R ax = 0, ay = 0;
-      for (int ci = k.c_start[b]; ci < k.c_start[b + 1]; ++ci) {
-        // the matrix already carries the contribution's coefficient
-        const T *in = (const T *)k.in[k.c_in[ci]];
-        const R *m = (const R *)k.c_mat[ci] + j * (2 * P + 1);
-        if (k.c_imag[ci]) {  // + i * (m x)
-#pragma unroll
-          for (int q = 0; q <= 2 * P; ++q) {
-            int jj = j + k.row_off - P + q;
-            if (jj >= 0 && jj < k.n_mode_in) {
-              T xv = in[base + (long long)jj * k.inner];
-              R mv = m[q];
-              ax -= mv * xv.y;
-              ay += mv * xv.x;
-            }
-          }
-        } else {
-#pragma unroll
-          for (int q = 0; q <= 2 * P; ++q) {
-            int jj = j + k.row_off - P + q;
-            if (jj >= 0 && jj < k.n_mode_in) {
-              T xv = in[base + (long long)jj * k.inner];
-              R mv = m[q];
-              ax += mv * xv.x;
-              ay += mv * xv.y;
-            }
-          }
-        }
-      }
-      T *out = (T *)k.out[b];
-      if (k.epi == 1) {  // out = b - v
-        T bv = ((const T *)k.b)[idx];
-        ax = bv.x - ax;
-        ay = bv.y - ay;
-      }
-      T res;
-      res.x = ax;
-      res.y = ay;
-      out[idx] = res;
-      if (k.dotvec) {
-        T dv = ((const T *)k.dotvec)[idx];
-        dacc += (double)dv.x * (double)ax + (double)dv.y * (double)ay;  // Re(conj(d) * out)
-      }
-      if (k.dot2_partials) d2acc += (double)ax * ax + (double)ay * ay;
-    }
-  }
+  // balanced: equal contiguous ranges per CTA (no SM left with a lighter share when a launch holds only one or
+  // two elements per resident thread); otherwise the grid-stride order, whose shared sweep keeps the window of
+  // concurrently read inputs compact when every thread handles many elements
+  const long long first = k.balanced ? (blockIdx.x * total) / gridDim.x + threadIdx.x
+                                     : blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long last = k.balanced ? ((blockIdx.x + 1) * total) / gridDim.x : total;
+  const long long step = k.balanced ? (long long)blockDim.x : (long long)gridDim.x * blockDim.x;
+  // 32-bit indices: run_plan only launches levels whose elements, plus one step past the end, fit (a 2^31
+  // element complex128 tensor is 34 GB, and a solve keeps about ten vectors)
+  for (int idx = (int)first; idx < (int)last; idx += (int)step) pass_element<R, P, int>(k, idx, dacc, d2acc);
   if (k.dot_partials) {
     double s = block_sum(dacc, sh);
     if (threadIdx.x == 0) k.dot_partials[blockIdx.x] = s;
@@ -128,6 +143,30 @@ __global__ void __launch_bounds__(512) k_pass(const __grid_constant__ PassK k) {
     double s = block_sum(d2acc, sh);
     if (threadIdx.x == 0) k.dot2_partials[blockIdx.x] = s;
   }
+}
+
+// resident CTAs of k_pass<R, P> with `threads` threads on the whole GPU (occupancy API, cached)
+template <typename R>
+static int pass_resident(int p, int threads) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int>, int> cache;
+  const auto key = std::make_tuple((int)sizeof(R), p, threads);
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int per_sm = 0, dev = 0, sms = 152;
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (p) {
+#define CASE(PP) case PP: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pass<R, PP>, threads, 0); break;
+    CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+#undef CASE
+    default: break;
+  }
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int r = (e == cudaSuccess && per_sm > 0) ? per_sm * sms : 0;
+  cache[key] = r;
+  return r;
 }
 
 template <typename R>
@@ -213,7 +252,9 @@ int run_plan(const Plan &plan, const void *x, void *y, int precision, int epi, c
     k.dot_partials = nullptr;
     k.dot2_partials = nullptr;
     k.done = done;
+    k.balanced = 0;
     long long total = pp.outer * (long long)pp.n_mode_out * pp.inner;
+    if (total + 152LL * 16 * 512 > 0x7fffffffLL) return STST_ERR_ARG;  // k_pass indexes in 32 bits
     int grid = reduction_grid(total);
     if (ip == np - 1) {
       k.out[0] = y;
@@ -229,6 +270,17 @@ int run_plan(const Plan &plan, const void *x, void *y, int precision, int epi, c
     // the final level's grid is capped (its per-CTA partials are reduced by every consumer CTA): it runs
     // 512-thread CTAs, twice the warps per SM for the same number of partials
     const int threads = (ip == np - 1) ? 512 : 256;
+    // at most two elements per resident thread: equal contiguous ranges, the inner levels in one resident wave
+    // (c2: 4.87 -> 4.78 ms per solve measured with this rule; at the 3D sizes, ~14 elements per thread, the
+    // grid-stride order stays faster)
+    {
+      const int res = precision == 1 ? pass_resident<float>(pp.p, threads) : pass_resident<double>(pp.p, threads);
+      const long long slots = (long long)(ip == np - 1 ? grid : (res > 0 ? res : grid)) * threads;
+      if (res > 0 && total <= 2 * slots) {
+        k.balanced = 1;
+        if (ip != np - 1 && grid > res) grid = res;
+      }
+    }
     int st = precision == 1 ? launch_pass_t<float>(k, pp.p, grid, s, threads)
                             : launch_pass_t<double>(k, pp.p, grid, s, threads);
     if (st != STST_OK) return st;
@@ -1664,6 +1716,12 @@ static int tune_pencil(stst_problem *h) {
 }
 
 int tune_modeprod(stst_problem *h) {
+  // the mat-vec's occupancy queries are cached here, outside any stream capture
+  for (int l = 0; l <= h->d; ++l)
+    for (int threads : {256, 512}) {
+      pass_resident<double>(h->dir[l].p, threads);
+      pass_resident<float>(h->dir[l].p, threads);
+    }
   if (h->tuned) return STST_OK;
   STST_TRY(tune_mp_tiles(h));
   STST_TRY(tune_ts<float>(h));

@@ -70,3 +70,34 @@ def test_batch_reports_per_problem_outcomes():
         S.stst_batch_destroy(batch)
     with pytest.raises(S.StstError):
         S.stst_batch_create([inst[0][0].h, inst[0][0].h], rhs[:2], xs[:2])
+
+
+def test_batch_c4_mesh_range_against_the_oracle():
+    """The ends of the batched workload's range (n_el in {16..96}^2 x {16..96}, p in {2, 3, 4}, a random
+    separable potential and a wavepacket per instance): a 96^2 x 96, p = 4 instance (950,796 unknowns) with
+    the FP32 preconditioner and 16^2 x 16 instances with the BF16x3 and FP32 ones, solved in one launch to
+    relative residual 1e-11; every solution within 1e-8 of the oracle's (PCG with the exact P-hat to 1e-13
+    on the same right-hand side)."""
+    specs = [([96, 96, 96], 4, S.STST_PREC_FP32), ([16, 16, 16], 2, S.STST_PREC_BF16),
+             ([16, 16, 16], 3, S.STST_PREC_FP32)]
+    inst = []
+    for k, (n_el, p, prec) in enumerate(specs):
+        rng = np.random.default_rng(4 + k)
+        V = random_smooth_potential(rng, 2)
+        prob = S.Problem(2, n_el, p, prec_mode=prec)
+        prob.set_potential(sample_potential(prob, V), len(V))
+        b = prob.rhs(None, sample_initial(prob, wavepacket_factors(wavepacket_params(rng, 2))))
+        inst.append((prob, V, b, n_el, p))
+    xs = [prob.vec() for prob, *_ in inst]
+    batch = S.stst_batch_create([prob.h for prob, *_ in inst], [b for _, _, b, _, _ in inst], xs)
+    try:
+        status, iters, relres, sts = S.stst_batch_solve(batch, len(inst), 1e-11, 400)
+    finally:
+        S.stst_batch_destroy(batch)
+    assert status == 0 and all(s == 0 for s in sts) and all(r <= 1e-11 for r in relres)
+    for (prob, V, b, n_el, p), x in zip(inst, xs):
+        disc = oracle_disc(n_el, p, potential=V)
+        bn = to_np(b)
+        xo, _, _, _ = opcg.pcg(disc.apply, ofd.FastDiagonalization(disc).apply, bn, tol=1e-13, maxit=400)
+        assert rel_err(to_np(x), xo) < 1e-8, (n_el, p)
+        prob.close()
