@@ -340,6 +340,24 @@ int stst_set_fused_transforms(int mode);
  */
 int stst_set_pencil(int mode);
 int stst_pencil_info(stst_handle h, int *ctas_per_pencil);
+/*
+ * stst_set_tensor_products: mode products of Algorithm 1 (steps 2 and 4) on the tensor cores with the FP32
+ * preconditioner. Per direction l the product with U_l (or U_l^T) is a real GEMM whose rows are the real
+ * and imaginary parts of 64 complex columns; the TMA unit copies each 64-column tile (all n_l rows of one
+ * outer index) into shared memory, every value is split into two TF32 parts, and three tcgen05 TF32
+ * products (high x high, high x low, low x high; FP32 accumulation in tensor memory) give about the
+ * accuracy of the FP32 SIMT products. It applies where the input is FP32 with an even inner extent (the row
+ * pitch of the copy must be a multiple of 16 bytes) and n_l <= 80 (its shared memory); elsewhere the SIMT
+ * tile runs. Mode 0 (default): a candidate of the tile autotuner (autotune mode 1), kept per direction when
+ * faster; 1 = off; 2 = used wherever it applies. Results agree with the SIMT products up to rounding (the
+ * sums run in another order). Process-wide, for handles whose preconditioner is built afterwards;
+ * STST_ERR_ARG for other modes. stst_tensor_products_info: bit l of *dirs (host) is set when direction l's
+ * mode products use the tensor cores (FP32 preconditioner; where they run as separate products, not inside
+ * the fused 2D transforms or the pencil kernel, see stst_set_fused_transforms and stst_set_pencil; a mode
+ * product whose input is not 16-byte aligned runs on the SIMT tile).
+ */
+int stst_set_tensor_products(int mode);
+int stst_tensor_products_info(stst_handle h, int *dirs);
 int stst_fused_transforms_info(stst_handle h, int *fused);
 int stst_time_solver_info(stst_handle h, int precision, int *segments, int *segment_len, int *segmented);
 /* Name and description of the CUDA error behind the calling thread's last STST_ERR_CUDA (static string). */

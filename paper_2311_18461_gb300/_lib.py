@@ -69,6 +69,8 @@ def lib():
             "stst_fused_transforms_info": [P, IP],
             "stst_set_pencil": [I],
             "stst_pencil_info": [P, IP],
+            "stst_set_tensor_products": [I],
+            "stst_tensor_products_info": [P, IP],
             "stst_time_solver_info": [P, I, IP, IP, IP],
             "stst_tile_info": [P, I, IP, IP, DP],
             "stst_ws_create": [ctypes.POINTER(P), I, IP, I, ctypes.c_ulonglong, P],
@@ -308,6 +310,16 @@ def stst_set_pencil(mode):
 def stst_pencil_info(h):
     f = ctypes.c_int()
     _chk(lib().stst_pencil_info(h, ctypes.byref(f)), "stst_pencil_info")
+    return f.value
+
+
+def stst_set_tensor_products(mode):
+    return _chk(lib().stst_set_tensor_products(int(mode)), "stst_set_tensor_products")
+
+
+def stst_tensor_products_info(h):
+    f = ctypes.c_int()
+    _chk(lib().stst_tensor_products_info(h, ctypes.byref(f)), "stst_tensor_products_info")
     return f.value
 
 

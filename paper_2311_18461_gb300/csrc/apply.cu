@@ -6,6 +6,7 @@
 //  * k_timesolve: the N_s independent banded Hermitian solves H_i x_i = y_i (Algorithm 1, step 3,
 //    Eq. independent_problems) with precomputed Cholesky factors, one thread per system.
 #include "common.cuh"
+#include <type_traits>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -514,6 +515,7 @@ static int launch_modeprod(const TI *X, TO *Y, const R *U, int n, long long inne
 // cached for the process. Runs outside graph capture (stst_build_fd, stst_batch_create).
 MpCfg modeprod_default(int n) {
   MpCfg c;
+  c.tc = 0;
   c.cpt = 4;
   c.rpt = (n + 31) / 32;
   if (c.rpt > 4) c.rpt = 4;
@@ -522,6 +524,7 @@ MpCfg modeprod_default(int n) {
 }
 
 int g_tune_enabled = 1;
+int g_tf32_mode = 0;  // TF32 tensor-core mode products: 0 a tuner candidate, 1 off, 2 forced where they apply
 static std::mutex g_tune_mu;
 static std::map<std::tuple<int, int, long long, long long>, std::pair<MpCfg, float>> g_tune_cache;
 
@@ -529,7 +532,7 @@ template <typename R>
 static int tune_one(stst_problem *h, int l, long long inner, long long outer, MpCfg *best, float *best_us) {
   using T = typename C2<R>::T;
   const int n = h->dir[l].n;
-  const auto key = std::make_tuple((int)sizeof(R), n, inner, outer);
+  const auto key = std::make_tuple((int)sizeof(R) + 16 * g_tf32_mode, n, inner, outer);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
@@ -583,6 +586,35 @@ static int tune_one(stst_problem *h, int l, long long inner, long long outer, Mp
       }
     }
   }
+  cand.tc = 0;
+  // the TF32 tensor-core kernel (FP32 only), where the shape allows it; the best SIMT tile stays the fallback
+  if constexpr (sizeof(R) == 4) {
+    if (status == STST_OK && g_tf32_mode != 1 && h->Utf[l] && tf32_eligible(n, inner, outer, X)) {
+      int *ef = h->flags + 1;
+      for (int w = 0; w < 2 && status == STST_OK; ++w)
+        status = launch_modeprod_tf32<float2>((const float2 *)X, (float2 *)Y, h->Utf[l], 0, n, inner, outer, EpiDot(),
+                                              nullptr, ef, st);
+      if (status == STST_OK) {
+        cudaEventRecord(e0, st);
+        for (int w = 0; w < 5 && status == STST_OK; ++w)
+          status = launch_modeprod_tf32<float2>((const float2 *)X, (float2 *)Y, h->Utf[l], 0, n, inner, outer,
+                                                EpiDot(), nullptr, ef, st);
+        cudaEventRecord(e1, st);
+        const cudaError_t es = cudaEventSynchronize(e1);
+        if (es != cudaSuccess) {
+          stst_last_cuda = es;
+          status = STST_ERR_CUDA;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const float us = ms * 1000.f / 5.f;
+        if (status == STST_OK && (us < cand_us || g_tf32_mode == 2)) {
+          cand_us = us;
+          cand.tc = 1;
+        }
+      }
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   STST_TRY(status);
@@ -597,7 +629,10 @@ static int tune_one(stst_problem *h, int l, long long inner, long long outer, Mp
 
 static int tune_mp_tiles(stst_problem *h) {
   if (h->prec_mode == STST_PREC_BF16 || g_tune_enabled != 1) {
+    long long acc = h->n_t();
     for (int l = 1; l <= h->d; ++l) {
+      const long long inner = acc, outer = h->N_dof / (acc * h->dir[l].n);
+      acc *= h->dir[l].n;
       h->mp_cfg[l] = modeprod_default(h->dir[l].n);
       // a forced tile: 10 rpt + cpt, or 132 for the wide tile (FP32 preconditioner only)
       int rpt = g_tune_enabled / 10, cpt = g_tune_enabled % 10;
@@ -609,12 +644,17 @@ static int tune_mp_tiles(stst_problem *h) {
         MpCfg c;
         c.cpt = cpt;
         c.rpt = rpt;
+        c.tc = 0;
         int dev = 0, optin = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         const size_t rs = h->prec_mode == STST_PREC_FP64 ? sizeof(double) : sizeof(float);
         if (modeprod_smem(h->dir[l].n, c, rs) <= (size_t)optin) h->mp_cfg[l] = c;
       }
+      // forced TF32 tensor-core products (FP32 preconditioner), used where the shape and input allow them
+      if (g_tf32_mode == 2 && h->prec_mode == STST_PREC_FP32 && h->Utf[l] &&
+          tf32_eligible(h->dir[l].n, inner, outer, h->w_t1))
+        h->mp_cfg[l].tc = 1;
     }
     return STST_OK;
   }
@@ -1285,6 +1325,23 @@ static int time_solve(stst_problem *h, void *Y, const int *done, cudaStream_t st
   return launch_timesolve<R>(Y, G, D, h->n_t(), h->N_s, h->dir[0].p, done, st);
 }
 
+// FP32 mode product of direction l: the TF32 tensor-core kernel where the tuner chose it and the shape and
+// input allow it (FP32 input with aligned rows), else the SIMT tile
+template <typename TI, typename TO>
+static int mp32(stst_problem *h, int l, const TI *X, TO *Y, long long inner, long long outer, int backward,
+                const EpiDot &ed, const int *done, cudaStream_t s) {
+  const int n = h->dir[l].n;
+  if constexpr (std::is_same<TI, float2>::value) {
+    if (h->mp_cfg[l].tc && h->Utf[l]) {
+      if (tf32_eligible(n, inner, outer, X))
+        return launch_modeprod_tf32<TO>(X, Y, h->Utf[l], backward, n, inner, outer, ed, done, h->flags + 1, s);
+      // the partial sums of the epilogue were counted for the tensor-core grid
+      if (ed.part) return STST_ERR_ARG;
+    }
+  }
+  return launch_modeprod<float, TI, TO>(X, Y, h->U32[l], n, inner, outer, backward, ed, done, s, h->mp_cfg[l]);
+}
+
 int fd_apply(stst_problem *h, const double *r, double *s, int precision, const EpiDot &ed, const int *done,
              void *bufA, void *bufB, float *out32, const float *in32) {
   const int d = h->d;
@@ -1396,12 +1453,9 @@ int fd_apply(stst_problem *h, const double *r, double *s, int precision, const E
     for (int l = 1; l < d; ++l) {
       float2 *dst = bufs[cur];
       if (l == 1 && !in32)
-        STST_TRY((launch_modeprod<float, double2, float2>((const double2 *)r, dst, h->U32[l], h->dir[l].n, inner[l],
-                                                          outer[l], 0, none, done, st, h->mp_cfg[l])));
+        STST_TRY((mp32<double2, float2>(h, l, (const double2 *)r, dst, inner[l], outer[l], 0, none, done, st)));
       else
-        STST_TRY((launch_modeprod<float, float2, float2>(l == 1 ? (const float2 *)in32 : src, dst, h->U32[l],
-                                                         h->dir[l].n, inner[l], outer[l], 0, none, done, st,
-                                                         h->mp_cfg[l])));
+        STST_TRY((mp32<float2, float2>(h, l, l == 1 ? (const float2 *)in32 : src, dst, inner[l], outer[l], 0, none, done, st)));
       src = dst;
       cur ^= 1;
     }
@@ -1414,14 +1468,12 @@ int fd_apply(stst_problem *h, const double *r, double *s, int precision, const E
     for (int l = d - 1; l >= 1; --l) {
       if (l == 1) {
         if (out32)
-          return launch_modeprod<float, float2, float2>(src, (float2 *)out32, h->U32[l], h->dir[l].n, inner[l],
-                                                        outer[l], 1, ed, done, st, h->mp_cfg[l]);
-        return launch_modeprod<float, float2, double2>(src, (double2 *)s, h->U32[l], h->dir[l].n, inner[l], outer[l],
-                                                       1, ed, done, st, h->mp_cfg[l]);
+          return mp32<float2, float2>(h, l, src, (float2 *)out32, inner[l], outer[l], 1, ed, done, st);
+        return mp32<float2, double2>(h, l, src, (double2 *)s, inner[l], outer[l], 1, ed, done, st);
       }
       float2 *dst = bufs[cur];
-      STST_TRY((launch_modeprod<float, float2, float2>(src, dst, h->U32[l], h->dir[l].n, inner[l], outer[l], 1, none,
-                                                       done, st, h->mp_cfg[l])));
+      STST_TRY((mp32<float2, float2>(h, l, src, dst, inner[l], outer[l], 1, none,
+                                                       done, st)));
       src = dst;
       cur ^= 1;
     }
@@ -1434,11 +1486,11 @@ int fd_apply(stst_problem *h, const double *r, double *s, int precision, const E
     else STST_TRY((launch_fd2d<double2, float2>((const double2 *)r, y32, h, 0, none, done, st, S)));
     if (d == 3) {
       float2 *z32 = (float2 *)bufB;
-      STST_TRY((launch_modeprod<float, float2, float2>(y32, z32, h->U32[3], h->dir[3].n, inner[3], outer[3], 0, none,
-                                                       done, st, h->mp_cfg[3])));
+      STST_TRY((mp32<float2, float2>(h, 3, y32, z32, inner[3], outer[3], 0, none,
+                                                       done, st)));
       STST_TRY(time_solve<float>(h, (void *)z32, done, st));
-      STST_TRY((launch_modeprod<float, float2, float2>(z32, y32, h->U32[3], h->dir[3].n, inner[3], outer[3], 1, none,
-                                                       done, st, h->mp_cfg[3])));
+      STST_TRY((mp32<float2, float2>(h, 3, z32, y32, inner[3], outer[3], 1, none,
+                                                       done, st)));
     } else {
       STST_TRY(time_solve<float>(h, (void *)y32, done, st));
     }
@@ -1452,15 +1504,13 @@ int fd_apply(stst_problem *h, const double *r, double *s, int precision, const E
     float2 *dst = bufs[cur];
     if (l == 1) {
       if (in32) {
-        STST_TRY((launch_modeprod<float, float2, float2>((const float2 *)in32, dst, h->U32[l], h->dir[l].n, inner[l],
-                                                         outer[l], 0, none, done, st, h->mp_cfg[l])));
+        STST_TRY((mp32<float2, float2>(h, l, (const float2 *)in32, dst, inner[l], outer[l], 0, none, done, st)));
       } else {
-        STST_TRY((launch_modeprod<float, double2, float2>((const double2 *)r, dst, h->U32[l], h->dir[l].n, inner[l],
-                                                          outer[l], 0, none, done, st, h->mp_cfg[l])));
+        STST_TRY((mp32<double2, float2>(h, l, (const double2 *)r, dst, inner[l], outer[l], 0, none, done, st)));
       }
     } else {
-      STST_TRY((launch_modeprod<float, float2, float2>(src32, dst, h->U32[l], h->dir[l].n, inner[l], outer[l], 0, none,
-                                                       done, st, h->mp_cfg[l])));
+      STST_TRY((mp32<float2, float2>(h, l, src32, dst, inner[l], outer[l], 0, none,
+                                                       done, st)));
     }
     src32 = dst;
     cur ^= 1;
@@ -1469,16 +1519,14 @@ int fd_apply(stst_problem *h, const double *r, double *s, int precision, const E
   for (int l = d; l >= 1; --l) {
     if (l == 1) {
       if (out32) {
-        STST_TRY((launch_modeprod<float, float2, float2>(src32, (float2 *)out32, h->U32[l], h->dir[l].n, inner[l],
-                                                         outer[l], 1, ed, done, st, h->mp_cfg[l])));
+        STST_TRY((mp32<float2, float2>(h, l, src32, (float2 *)out32, inner[l], outer[l], 1, ed, done, st)));
       } else {
-        STST_TRY((launch_modeprod<float, float2, double2>(src32, (double2 *)s, h->U32[l], h->dir[l].n, inner[l],
-                                                          outer[l], 1, ed, done, st, h->mp_cfg[l])));
+        STST_TRY((mp32<float2, double2>(h, l, src32, (double2 *)s, inner[l], outer[l], 1, ed, done, st)));
       }
     } else {
       float2 *dst = bufs[cur];
-      STST_TRY((launch_modeprod<float, float2, float2>(src32, dst, h->U32[l], h->dir[l].n, inner[l], outer[l], 1, none,
-                                                       done, st, h->mp_cfg[l])));
+      STST_TRY((mp32<float2, float2>(h, l, src32, dst, inner[l], outer[l], 1, none,
+                                                       done, st)));
       src32 = dst;
       cur ^= 1;
     }
@@ -1492,6 +1540,9 @@ int fd_partials_count(stst_problem *h) {
   if (h->prec_mode == STST_PREC_BF16) return tc_partials_count(ncols);
   if (h->pencil && h->prec_mode == STST_PREC_FP32 && h->d == 1) return (int)(h->N_s / h->dir[1].n * h->pencil);
   if (h->fd2d && h->prec_mode == STST_PREC_FP32 && (!h->pencil || h->d == 3)) return (int)(fd2d_slabs(h) * h->fd2d);
+  if (h->prec_mode == STST_PREC_FP32 && h->mp_cfg[1].tc && h->Utf[1] &&
+      tf32_eligible(h->dir[1].n, h->n_t(), ncols / h->n_t(), h->w_t1))
+    return tf32_partials_count(h->dir[1].n, h->n_t(), ncols / h->n_t());
   const dim3 g = modeprod_grid(h->dir[1].n, ncols, h->mp_cfg[1]);
   return (int)(g.x * g.y);
 }
@@ -1615,10 +1666,10 @@ static int tune_fd2d(stst_problem *h) {
         STST_TRY((launch_fd2d<float2, float2>(X, Y, h, 0, EpiDot(), nullptr, st, S)));
         return launch_fd2d<float2, float2>(Y, X, h, 1, EpiDot(), nullptr, st, S);
       }
-      STST_TRY((launch_modeprod<float, float2, float2>(X, Z, h->U32[1], h->dir[1].n, inner[1], outer[1], 0, EpiDot(), nullptr, st, h->mp_cfg[1])));
-      STST_TRY((launch_modeprod<float, float2, float2>(Z, Y, h->U32[2], h->dir[2].n, inner[2], outer[2], 0, EpiDot(), nullptr, st, h->mp_cfg[2])));
-      STST_TRY((launch_modeprod<float, float2, float2>(Y, Z, h->U32[2], h->dir[2].n, inner[2], outer[2], 1, EpiDot(), nullptr, st, h->mp_cfg[2])));
-      return launch_modeprod<float, float2, float2>(Z, X, h->U32[1], h->dir[1].n, inner[1], outer[1], 1, EpiDot(), nullptr, st, h->mp_cfg[1]);
+      STST_TRY((mp32<float2, float2>(h, 1, X, Z, inner[1], outer[1], 0, EpiDot(), nullptr, st)));
+      STST_TRY((mp32<float2, float2>(h, 2, Z, Y, inner[2], outer[2], 0, EpiDot(), nullptr, st)));
+      STST_TRY((mp32<float2, float2>(h, 2, Y, Z, inner[2], outer[2], 1, EpiDot(), nullptr, st)));
+      return mp32<float2, float2>(h, 1, Z, X, inner[1], outer[1], 1, EpiDot(), nullptr, st);
     };
     for (int w = 0; w < 2 && status == STST_OK; ++w) status = run();
     cudaEventRecord(e0, st);

@@ -429,6 +429,7 @@ void destroy_all(stst_problem *h) {
     cudaFree(h->U[l]);
     cudaFree(h->U32[l]);
     cudaFree(h->Ubf[l]);
+    cudaFree(h->Utf[l]);
     cudaFree(h->lam[l]);
   }
   for (int k = 0; k < 3; ++k) {
@@ -533,6 +534,7 @@ int create_impl(stst_problem *h, int d, const int *n_el, const int *p, double T,
     STST_TRY(alloc((void **)&h->U[l], sizeof(double) * D.n * D.n));
     STST_TRY(alloc((void **)&h->U32[l], sizeof(float) * D.n * D.n));
     STST_TRY(alloc((void **)&h->Ubf[l], sizeof(__nv_bfloat16) * 4 * pad16(D.n) * pad16(D.n)));
+    STST_TRY(alloc((void **)&h->Utf[l], sizeof(float) * tf32_planes_floats(D.n)));
     STST_TRY(alloc((void **)&h->lam[l], sizeof(double) * D.n));
   }
   int nmax = 1;
@@ -981,6 +983,24 @@ int stst_set_pencil(int mode) {
 int stst_pencil_info(stst_handle h, int *ctas_per_pencil) {
   STST_TRY(check(h));
   if (ctas_per_pencil) *ctas_per_pencil = h->pencil;
+  return STST_OK;
+}
+
+extern int g_tf32_mode;
+
+int stst_set_tensor_products(int mode) {
+  if (mode < 0 || mode > 2) return STST_ERR_ARG;
+  g_tf32_mode = mode;
+  return STST_OK;
+}
+
+int stst_tensor_products_info(stst_handle h, int *dirs) {
+  STST_TRY(check(h));
+  int mask = 0;
+  if (h->prec_mode == STST_PREC_FP32)
+    for (int l = 1; l <= h->d; ++l)
+      if (h->mp_cfg[l].tc) mask |= 1 << l;
+  if (dirs) *dirs = mask;
   return STST_OK;
 }
 

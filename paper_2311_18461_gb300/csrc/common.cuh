@@ -133,9 +133,11 @@ __device__ __forceinline__ void epi_dot_store(const double (&acc)[4], const EpiD
 }
 
 // ---- PCG control block (device) ---------------------------------------------------------------
-// Tile of the SIMT mode product: cpt columns per thread (8 cpt per CTA), rpt groups of 32 output rows.
+// Tile of the SIMT mode product: cpt columns per thread (8 cpt per CTA), rpt groups of 32 output rows;
+// tc = 1: the TF32 tensor-core kernel instead, where the shape and the input allow it (FP32 preconditioner).
 struct MpCfg {
   int cpt, rpt;
+  int tc;
 };
 
 // Plain CG (FP64 preconditioner): rho = <r, z> real, alpha = rho / pq, beta = rho_new / rho.
@@ -200,6 +202,7 @@ struct stst_problem {
   double *U[STST_MAXD + 1];
   float *U32[STST_MAXD + 1];
   __nv_bfloat16 *Ubf[STST_MAXD + 1];
+  float *Utf[STST_MAXD + 1];       // TF32 planes of U' (FP32 preconditioner): [fwd hi | bwd hi | fwd lo | bwd lo]
   double *lam[STST_MAXD + 1];
   double *oa_work;                 // refinement workspace
   void *Hg;                        // FP64 factors: n_t x p x N_s complex
@@ -310,6 +313,15 @@ int launch_modeprod_tc(const TI *X, TO *Y, const __nv_bfloat16 *Bk, long long lo
                        long long inner, long long outer, const EpiDot &ed, const int *done, int *errflag,
                        cudaStream_t s);
 int tc_partials_count(long long ncols);
+
+// TF32 tensor-core mode products fed by TMA (modeprod_tf32.cu)
+int launch_u_to_tf32(const double *U, int n, float *out, cudaStream_t s);
+size_t tf32_planes_floats(int n);
+bool tf32_eligible(int n, long long inner, long long outer, const void *X);
+template <typename TO>
+int launch_modeprod_tf32(const float2 *X, TO *Y, const float *planes, int backward, int n, long long inner,
+                         long long outer, const EpiDot &ed, const int *done, int *errflag, cudaStream_t s);
+int tf32_partials_count(int n, long long inner, long long outer);
 
 // pencil kernel (pencil.cu): steps 2-4 of Algorithm 1 along the last spatial direction with the time solves
 bool pencil_fits(const stst_problem *h, int CL);

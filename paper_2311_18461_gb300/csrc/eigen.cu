@@ -809,6 +809,7 @@ int fd_setup_launch(stst_problem *h) {
     }
     { STST_PROF("to_f32", st); STST_TRY(launch_to_f32(h->U[l], h->U32[l], (long long)h->dir[l].n * h->dir[l].n, st)); }
     if (h->prec_mode == STST_PREC_BF16) STST_TRY(launch_u_to_bf16(h->U[l], h->dir[l].n, h->Ubf[l], st));
+    if (h->prec_mode == STST_PREC_FP32) STST_TRY(launch_u_to_tf32(h->U[l], h->dir[l].n, h->Utf[l], st));
   }
   const BandMat &Lt = h->mats[0][0], &Mt = h->mats[0][1], &KAt = h->mats[0][2];
   const float *Lt32 = h->mats32[0][0], *Mt32 = h->mats32[0][1], *KAt32 = h->mats32[0][2];

@@ -393,6 +393,7 @@ def test_mode_product_tiles_agree_bitwise(prec):
     P.stst_set_time_solver(1)  # the same time solve for every tile
     P.stst_set_fused_transforms(1)  # separate mode products, so that every tile runs
     P.stst_set_pencil(1)
+    P.stst_set_tensor_products(1)  # SIMT tiles only
     try:
         for mode in (0, 12, 14, 22, 24, 32, 34, 42, 44, 132, 1):
             P.stst_set_autotune(mode)
@@ -407,6 +408,7 @@ def test_mode_product_tiles_agree_bitwise(prec):
         P.stst_set_time_solver(0)
         P.stst_set_fused_transforms(0)
         P.stst_set_pencil(0)
+        P.stst_set_tensor_products(0)
     ref = outs[0][0]
     for mode, (o, tiles) in outs.items():
         assert np.array_equal(o, ref), (mode, tiles)
@@ -424,6 +426,7 @@ def test_fused_2d_transforms_bitwise(n_el, p):
     iterations (only the order of the dot-product partial sums differs)."""
     out = {}
     S.stst_set_pencil(1)  # the separate last-direction kernels, so that the fused transforms run for d = 2
+    S.stst_set_tensor_products(1)  # the SIMT mode products, which sum in the fused kernel's order
     try:
         for mode in (1, 2, 11, 12, 13, 14):
             S.stst_set_fused_transforms(mode)
@@ -437,6 +440,7 @@ def test_fused_2d_transforms_bitwise(n_el, p):
     finally:
         S.stst_set_fused_transforms(0)
         S.stst_set_pencil(0)
+        S.stst_set_tensor_products(0)
     assert out[1][1] == 0 and out[2][1] >= 1 and out[11][1] == 1
     assert all(out[10 + k][1] in (k, out[2][1]) for k in (2, 3, 4))  # the default where k leaves a part empty
     for mode in (2, 11, 12, 13, 14):
