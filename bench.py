@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--pencil", type=int, default=0,
                     help="FP32 preconditioner, last direction and time solves in one kernel: 0 chosen per shape, "
                          "1 off, 2 one CTA per pencil, 3 a cluster of two (stst_set_pencil)")
+    ap.add_argument("--tensor-products", type=int, default=0,
+                    help="FP32 preconditioner, TF32 tensor-core mode products: 0 an autotuner candidate, 1 off, "
+                         "2 wherever they apply (stst_set_tensor_products)")
     ap.add_argument("--cpu-baseline", default="on", choices=["on", "off"],
                     help="time the oracle on the host cores (off: skip it, e.g. for the 3D workloads)")
     ap.add_argument("--variants", default="on", choices=["on", "off"],
@@ -1087,6 +1090,7 @@ def main():
         S.stst_set_time_solver(args.time_solver)
         S.stst_set_fused_transforms(args.fused_transforms)
         S.stst_set_pencil(args.pencil)
+        S.stst_set_tensor_products(args.tensor_products)
         if args.config == "c4":
             run_batch(args)
         elif args.config == "c5":
