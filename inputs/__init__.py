@@ -12,6 +12,8 @@ stand in for them exactly; sizes follow the 2D+t performance study, Table 1):
   c3p2 / c3p4   3D+t, p=2 / 4, 32^3 x 64 elements, V = 0 or a Gaussian bump, wavepacket (seed 1)
   c4     128 2D+t instances, n_el in {16..96}^2 x {16..96}, p in {2,3,4}, seeded per instance (4 + i)
   c5     2D+t, p=3, 48^2 x 48, harmonic V, wavepackets with drawn centre/width/momentum/phase
+  geometry (module inputs.geometry): analytic maps F of the unit box (identity, affine, quarter annulus,
+         perturbed box) with their first and second derivatives, for the mapped-domain system
   tw     the travelling wave of the paper's performance study (Sec. 6.2, Table 1): 2D+t, V = 0,
          u = a exp(-i (|x|^2 + t^2) / w^2), w = 0.2, with its Dirichlet and initial values imposed
 """

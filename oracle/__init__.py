@@ -18,6 +18,8 @@ Modules, each citing the passage of the paper it restates:
   fd        -- the preconditioner P-hat (Eq. prec_definition) and Algorithm 1; its potential-aware
                variant P_V for potentials that are sums of one-direction factors (an extension: the
                construction of Eq. prec_definition applied to i d_t + sum_l (-nu d_ll + v_l))
+  geometry  -- the system on a mapped domain F((0,1)^d): physical-domain spatial matrices of Eq. space_mat
+               by quadrature with the map's Jacobian and Hessian (Sec. 3.2, Eq. syst_mat; potential-free)
   pcg       -- preconditioned conjugate gradients (Sec. 5.3, Sec. 6); flexible CG for preconditioners
                applied inexactly (Notay 2000; not in the paper)
   rhs       -- load vector F(S B_i) and liftings of initial / boundary data (Sec. 2.2, Sec. 4.3)
