@@ -25,7 +25,7 @@
  *    16-byte aligned; calls are ordered on the handle's CUDA stream. The
  *    library owns all factors and workspaces of a handle; no call after
  *    stst_create allocates device memory, except stst_set_potential (which
- *    re-plans) and stst_batch_create.
+ *    re-plans), stst_set_geometry and stst_batch_create.
  *  - Return value: STST_OK (0); a positive value is a numerical outcome, a
  *    negative value is a usage or CUDA error (see stst_strerror).
  */
@@ -139,6 +139,35 @@ int stst_assemble_1d(int p, int n_el, double length, int bc, const double *weigh
  * the operator as i d_t + sum_l H_l and costs as many band applications as V = 0.
  */
 int stst_set_potential(stst_handle h, int rank, const double *v_qp);
+
+/*
+ * stst_set_geometry: the system on a mapped domain Omega = F((0,1)^d) (Sec. 3.2: the isoparametric
+ * push-forward through G(tau, eta) = (T tau, F(eta)); Eq. syst_mat with the spatial matrices of
+ * Eq. space_mat integrated over Omega). The matrix keeps the form M_s (x) L_t + nu^2 B_s (x) M_t +
+ * nu L_s (x) (W_t + W_t^*) with the parametric time matrices; M_s, L_s, B_s are assembled by quadrature
+ * from the map's derivatives: jac[q][m][a] = dF_m / d eta_a and hess[q][m][a][b] = d^2 F_m / (d eta_a
+ * d eta_b) (device, row-major per point) at the spatial quadrature points q, the tensor grid of the
+ * directions' points (stst_quadrature_points) with direction 1 fastest: q = q_1 + Q_1 (q_2 + Q_2 q_3),
+ * Q_l = n_el[l] (p[l] + 2). The library keeps the three matrices as stencils of (2 p_l + 1) entries per
+ * direction and row and applies them in place of the parametric mat-vec (stst_apply_sys, stst_pcg_solve,
+ * FP64). The preconditioner keeps the structure of the parametric P-hat (the paper's fast solver is
+ * for F = id only, Sec. 5), with one change: the eigenvalues of direction l (Algorithm 1 step 1) are
+ * multiplied by s_l = int |det J| G^{ll} / int |det J| (G = J^{-1} J^{-T}), the mean scale of the physical
+ * Laplacian along l. For an affine map with sides a_l, s_l = 1 / a_l^2 and the scaled P-hat is the box's own
+ * preconditioner up to a constant factor; without the scales the parametric P-hat mismatches the
+ * operator's time-space balance and PCG needs more iterations the finer the mesh. Setting or removing a
+ * geometry marks the preconditioner stale: call stst_build_fd again. jac = NULL removes the geometry. Least-squares formulation without potential only; stst_rhs, stst_rhs_lift and
+ * stst_rhs_noalloc (parametric integrals) and stst_ir_solve (FP32 mat-vec) return STST_ERR_STATE while a
+ * geometry is set: the caller supplies the mapped-domain load vector. Allocates (about
+ * 3 N_s (2p+1)^d doubles and three vectors) and synchronizes the handle's stream.
+ * Errors: STST_ERR_ARG (hess NULL, (2p+1)^d > 729, or a map whose Jacobian determinant vanishes or
+ * changes sign at a quadrature point: the previous operator stays); STST_ERR_STATE (a potential is set,
+ * or the ultraweak formulation); STST_ERR_OOM.
+ * stst_geometry_info: whether a geometry is set, the stored entries per row, and the d eigenvalue scales
+ * s_l (host outputs, each may be NULL; the scales are 1 without a geometry).
+ */
+int stst_set_geometry(stst_handle h, const double *jac, const double *hess);
+int stst_geometry_info(stst_handle h, int *mapped, int *entries_per_row, double *prec_scales);
 
 /*
  * stst_set_prec_operator: the spatial operator the preconditioner is built from (an extension).

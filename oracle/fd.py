@@ -33,13 +33,21 @@ def dense_P(disc):
 
 
 class FastDiagonalization:
-    """Algorithm 1 (setup = step 1 and the H_i; apply = steps 2-4)."""
+    """Algorithm 1 (setup = step 1 and the H_i; apply = steps 2-4).
 
-    def __init__(self, disc):
+    scales: None, or per-direction factors s_l multiplying the eigenvalues of step 1 (a mapped domain:
+    `oracle.geometry.prec_scales`). With s_l = 1 / a_l^2 this is the preconditioner of the box with sides
+    a_l divided by prod_l a_l (its stiffness L_l / a_l and mass a_l M_l have the eigenvectors of (L_l, M_l)
+    scaled by a_l^{-1/2} and the eigenvalues scaled by 1 / a_l^2); PCG does not see the constant factor.
+    """
+
+    def __init__(self, disc, scales=None):
         self.disc = disc
         self.U, self.lam = [None], [None]
         for l in range(1, disc.d + 1):
             lam, U = scipy.linalg.eigh(disc.sp[l]["L"], disc.sp[l]["M"])   # step 1, Eq. space_eig
+            if scales is not None:
+                lam = scales[l - 1] * lam
             self.U.append(U)
             self.lam.append(lam)
         # Lambda_s in vec order (x_1 fastest): spatial array of shape (n_d, ..., n_1)

@@ -38,6 +38,28 @@ def metric_terms(J, H):
     return np.abs(det), G, h
 
 
+def prec_scales(gmap, disc_or_grids):
+    """Per-direction scales s_l of the parametric preconditioner's eigenvalues on a mapped domain:
+    s_l = int |det J| G^{ll} / int |det J| over the parametric box (the mean of the metric's diagonal). For
+    an affine map with sides a_l this is 1 / a_l^2, which makes the scaled P-hat the box's own (up to a
+    constant factor); for a curved map it matches the mean scale of the physical Laplacian in each
+    direction. disc_or_grids: a Discretization (its quadrature) or the list of 1D (points, weights)."""
+    if hasattr(disc_or_grids, "quad"):
+        qw = [disc_or_grids.quad(l) for l in range(1, disc_or_grids.d + 1)]
+    else:
+        qw = disc_or_grids
+    grids = [x for x, _ in qw]
+    mesh = np.meshgrid(*grids[::-1], indexing="ij")
+    pts = np.stack([m.ravel() for m in mesh[::-1]], axis=1)
+    wq = qw[0][1]
+    for l in range(1, len(qw)):
+        wq = np.kron(qw[l][1], wq)
+    J, H = gmap.jac_hess(pts)
+    adet, G, _ = metric_terms(J, H)
+    w = wq * adet
+    return [float(np.sum(w * G[:, l, l]) / np.sum(w)) for l in range(len(qw))]
+
+
 class GeoDiscretization:
     """Space-time spline discretisation of (0, T) x F((0,1)^d), potential-free.
 

@@ -47,6 +47,8 @@ def lib():
             "stst_quadrature_points": [P, I, P],
             "stst_assemble_1d": [I, I, D, I, P, P, P, P, P, P, IP, P],
             "stst_set_potential": [P, I, P],
+            "stst_set_geometry": [P, P, P],
+            "stst_geometry_info": [P, IP, IP, DP],
             "stst_build_fd": [P],
             "stst_apply_sys": [P, P, P],
             "stst_apply_prec": [P, P, P],
@@ -186,6 +188,18 @@ def stst_assemble_1d(p, n_el, length, bc, weight, M, L, J, K, K2, stream=None):
 
 def stst_set_potential(h, rank, v_qp):
     return _chk(lib().stst_set_potential(h, int(rank), _ptr(v_qp)), "stst_set_potential")
+
+
+def stst_set_geometry(h, jac, hess):
+    return _chk(lib().stst_set_geometry(h, _ptr(jac), _ptr(hess)), "stst_set_geometry")
+
+
+def stst_geometry_info(h, with_scales=False):
+    """(mapped, stored entries per row), and with_scales the list of P-hat's eigenvalue scales s_l."""
+    m, w = ctypes.c_int(), ctypes.c_int()
+    sc = (ctypes.c_double * 3)()
+    _chk(lib().stst_geometry_info(h, ctypes.byref(m), ctypes.byref(w), sc), "stst_geometry_info")
+    return (m.value, w.value, list(sc)) if with_scales else (m.value, w.value)
 
 
 def stst_build_fd(h):
@@ -474,6 +488,11 @@ class Problem:
 
     def set_potential(self, v_qp, rank):
         return stst_set_potential(self.h, rank, v_qp)
+
+    def set_geometry(self, jac, hess):
+        """Mapped domain: the map's first and second derivatives at the spatial quadrature grid (device
+        float64 tensors, shapes (N_q, d, d) and (N_q, d, d, d)); None removes it."""
+        return stst_set_geometry(self.h, jac, hess)
 
     def set_prec_operator(self, op):
         """0: the paper's P-hat; 1: the potential-aware P_V (rebuild with build_fd)."""

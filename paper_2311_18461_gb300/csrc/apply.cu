@@ -196,6 +196,7 @@ int reduction_grid(long long total) {
 int run_plan(const Plan &plan, const void *x, void *y, int precision, int epi, const void *b, const void *dotvec,
              double *dot_partials, const int *done, cudaStream_t s, const void *dot2vec, double *dot2_partials) {
   (void)dot2vec;
+  if (plan.geo) return run_geo(*plan.geo, x, y, precision, epi, b, dotvec, dot_partials, done, s, dot2_partials);
   const int np = (int)plan.passes.size();
   if (np == 0) return STST_ERR_STATE;  // dropped by a failed re-plan (see stst_set_potential)
   for (int ip = 0; ip < np; ++ip) {

@@ -331,6 +331,20 @@ int free_pool(stst_problem *h) {
 // The plans and the solver graphs captured from them hold pointers into the band matrices and the
 // intermediate pool. They are dropped whenever those change: run_plan refuses an empty plan
 // (STST_ERR_STATE) and the graphs are rebuilt by the next solve.
+// the captured solver graphs alone (their kernels or arguments change, the plans stay)
+void invalidate_graphs(stst_problem *h) {
+  h->pcg_graph_valid = 0;
+  if (h->pcg_exec) {
+    cudaGraphExecDestroy(h->pcg_exec);
+    h->pcg_exec = nullptr;
+  }
+  h->ir_graph_valid = 0;
+  if (h->ir_exec) {
+    cudaGraphExecDestroy(h->ir_exec);
+    h->ir_exec = nullptr;
+  }
+}
+
 void invalidate_plans(stst_problem *h) {
   h->sys_plan.passes.clear();
   h->lift_plan.passes.clear();
@@ -352,6 +366,7 @@ int replan(stst_problem *h, const std::vector<Term> &terms) {
   invalidate_plans(h);
   const int s = replan_impl(h, terms);
   if (s != STST_OK) invalidate_plans(h);
+  h->sys_plan.geo = h->geo;
   return s;
 }
 
@@ -436,6 +451,8 @@ void destroy_all(stst_problem *h) {
     cudaFree(h->tfull[k].d);
     cudaFree(h->tfull32[k]);
   }
+  free_geo(h->geo);
+  h->geo = nullptr;
   for (double *p : h->pot_bufs) cudaFree(p);
   free_pool(h);
   for (void *q : h->scaled) cudaFree(q);
@@ -599,6 +616,9 @@ int create_impl(stst_problem *h, int d, const int *n_el, const int *p, double T,
 }
 
 }  // namespace
+
+// for the mapped-domain operator (geometry.cu): its setup changes the kernels the solver graphs hold
+void invalidate_solver_graphs(stst_problem *h) { invalidate_graphs(h); }
 
 extern "C" {
 
@@ -789,6 +809,7 @@ int stst_set_potential(stst_handle h, int rank, const double *v_qp) {
   STST_TRY(check(h));
   ApiScope scope(h);
   if (rank < 0 || rank > 3 || (rank > 0 && !v_qp)) return STST_ERR_ARG;
+  if (h->geo && rank > 0) return STST_ERR_STATE;  // the mapped-domain operator has no potential terms
   // the samples are read and checked before anything of the handle changes: a rejected potential
   // leaves the previous operator in place
   std::vector<double> host;
@@ -1049,12 +1070,14 @@ int stst_rhs(stst_handle h, const double *f_qp, const double *u0_qp, double *rhs
   STST_TRY(check(h));
   ApiScope scope(h);
   if (!rhs) return STST_ERR_ARG;
+  if (h->geo) return STST_ERR_STATE;  // parametric integrals: the caller assembles a mapped-domain load vector
   return rhs_compute(h, f_qp, u0_qp, rhs, c0);
 }
 
 int stst_rhs_lift(stst_handle h, const double *f_qp, const double *u_qp, double *rhs, double *xd) {
   STST_TRY(check(h));
   ApiScope scope(h);
+  if (h->geo) return STST_ERR_STATE;
   return rhs_lift_compute(h, f_qp, u_qp, rhs, xd);
 }
 

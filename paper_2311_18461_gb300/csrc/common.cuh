@@ -74,9 +74,12 @@ struct PassParams {
   const int *done;            // if non-null and *done: skip
 };
 
+struct GeoOp;  // the mapped-domain operator (geometry.cu)
+
 struct Plan {
   std::vector<PassParams> passes;
   int n_levels = 0;
+  const GeoOp *geo = nullptr;  // set: run_plan applies the mapped-domain operator instead of the passes
 };
 
 // ---- inner products in the epilogue of a preconditioner application -------------------------------
@@ -221,6 +224,7 @@ struct stst_problem {
 
   // plans
   Plan sys_plan, lift_plan;
+  GeoOp *geo;                      // mapped-domain operator (stst_set_geometry), or null: the parametric one
   std::vector<void *> pool;        // intermediate tensors of the plans (FP64 sized)
   std::vector<void *> scaled;      // coefficient-scaled band matrices of the plans
 
@@ -313,6 +317,13 @@ int launch_modeprod_tc(const TI *X, TO *Y, const __nv_bfloat16 *Bk, long long lo
                        long long inner, long long outer, const EpiDot &ed, const int *done, int *errflag,
                        cudaStream_t s);
 int tc_partials_count(long long ncols);
+
+// mapped-domain operator (geometry.cu)
+int run_geo(const GeoOp &g, const void *x, void *y, int precision, int epi, const void *b, const void *dotvec,
+            double *dot_partials, const int *done, cudaStream_t s, double *dot2_partials);
+void free_geo(GeoOp *g);
+double geo_prec_scale(const GeoOp *g, int l);  // P-hat's eigenvalue scale of direction l (1 without a geometry)
+int launch_scale_vec(double *a, double c, long long n, cudaStream_t s);  // a *= c in place
 
 // TF32 tensor-core mode products fed by TMA (modeprod_tf32.cu)
 int launch_u_to_tf32(const double *U, int n, float *out, cudaStream_t s);

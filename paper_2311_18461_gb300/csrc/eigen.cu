@@ -811,6 +811,13 @@ int fd_setup_launch(stst_problem *h) {
     if (h->prec_mode == STST_PREC_BF16) STST_TRY(launch_u_to_bf16(h->U[l], h->dir[l].n, h->Ubf[l], st));
     if (h->prec_mode == STST_PREC_FP32) STST_TRY(launch_u_to_tf32(h->U[l], h->dir[l].n, h->Utf[l], st));
   }
+  // a mapped domain: the eigenvalues scaled per direction by the mean of the metric's diagonal
+  // (stst_set_geometry), after any sharing of eigenpairs between directions
+  if (h->geo)
+    for (int l = 1; l <= d; ++l) {
+      const double sc = geo_prec_scale(h->geo, l);
+      if (sc != 1.0) STST_TRY(launch_scale_vec(h->lam[l], sc, h->dir[l].n, st));
+    }
   const BandMat &Lt = h->mats[0][0], &Mt = h->mats[0][1], &KAt = h->mats[0][2];
   const float *Lt32 = h->mats32[0][0], *Mt32 = h->mats32[0][1], *KAt32 = h->mats32[0][2];
   int n1 = h->dir[1].n, n2 = d >= 2 ? h->dir[2].n : 1;

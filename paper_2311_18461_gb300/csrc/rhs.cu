@@ -550,6 +550,7 @@ __global__ void k_contract_time_pot(const double2 *__restrict__ in, double2 *__r
 extern "C" int stst_rhs_noalloc(stst_handle h, const double *f_qp, const double *u0_qp, double *rhs, double *c0) {
   if (!h || h->magic != STST_MAGIC) return STST_ERR_HANDLE;
   if (!rhs) return STST_ERR_ARG;
+  if (h->geo) return STST_ERR_STATE;  // parametric integrals (as stst_rhs)
   ApiScope scope(h);
   cudaStream_t st = h->stream;
   const int d = h->d;

@@ -141,3 +141,40 @@ def test_parametric_phat_preconditions_the_mapped_system(gmap, n_el, p):
     assert rr <= 1e-12
     assert np.abs(x - xd).max() <= 1e-9 * np.abs(xd).max()
     assert it < 120
+
+
+def test_prec_scales_of_an_affine_map_are_the_inverse_squared_sides():
+    a, b = 0.7, 1.9
+    disc = Discretization([3, 5, 4], [2, 3, 3])
+    s = geometry.prec_scales(Affine([a, b]), disc)
+    assert abs(s[0] - 1 / a ** 2) <= 1e-14 / a ** 2 and abs(s[1] - 1 / b ** 2) <= 1e-14 / b ** 2
+
+
+def test_scaled_phat_is_the_box_preconditioner():
+    """P-hat with eigenvalue scales 1 / a_l^2 is (prod a_l) times the inverse of P-hat assembled straight
+    from Eq. prec_definition with the box's own one-direction matrices (mass a_l M_l, stiffness L_l / a_l)."""
+    n_el, p, sides = [4, 5, 6], [2, 3, 2], [0.6, 1.7]
+    disc = Discretization(n_el, p)
+    F = fd.FastDiagonalization(disc, scales=[1 / a ** 2 for a in sides])
+    Ms, Ls = np.ones((1, 1)), np.zeros((1, 1))
+    for l, a in zip((1, 2), sides):
+        M, L = a * disc.sp[l]["M"], disc.sp[l]["L"] / a
+        Ls = np.kron(M, Ls) + np.kron(L, Ms)
+        Ms = np.kron(M, Ms)
+    P = np.kron(Ms, disc.Lt) + np.kron(Ls.T @ np.linalg.solve(Ms, Ls), disc.Mt) + np.kron(Ls, disc.Wsym)
+    r = np.random.default_rng(4).standard_normal(disc.N_dof) + 0j
+    want = np.prod(sides) * np.linalg.solve(P, r)
+    assert np.abs(F.apply(r) - want).max() <= 1e-10 * np.abs(want).max()
+
+
+def test_scaled_phat_restores_the_parametric_iteration_count_on_a_box():
+    n_el, p, sides = [8, 12, 12], [3, 3, 3], [1.0, 0.5 * math.pi]
+    disc = Discretization(n_el, p)
+    g = geometry.GeoDiscretization(n_el, p, Affine(sides))
+    f = np.random.default_rng(5).standard_normal(disc.N_dof) + 0j
+    _, it_unit, _, _ = pcg.pcg(disc.apply, fd.FastDiagonalization(disc).apply, f, tol=1e-8, maxit=2000)
+    sc = geometry.prec_scales(Affine(sides), disc)
+    _, it_scaled, _, _ = pcg.pcg(g.apply, fd.FastDiagonalization(disc, scales=sc).apply, f, tol=1e-8, maxit=2000)
+    _, it_plain, _, _ = pcg.pcg(g.apply, fd.FastDiagonalization(disc).apply, f, tol=1e-8, maxit=2000)
+    assert abs(it_scaled - it_unit) <= 2, (it_scaled, it_unit)
+    assert it_plain > 2 * it_scaled
