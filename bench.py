@@ -70,6 +70,9 @@ def parse():
     ap.add_argument("--pencil", type=int, default=0,
                     help="FP32 preconditioner, last direction and time solves in one kernel: 0 chosen per shape, "
                          "1 off, 2 one CTA per pencil, 3 a cluster of two (stst_set_pencil)")
+    ap.add_argument("--fused-matvec", type=int, default=0,
+                    help="FP64 mat-vec levels in one launch with grid barriers: 0 one launch per level (default), "
+                         "1 one launch for all levels (stst_set_fused_matvec)")
     ap.add_argument("--tensor-products", type=int, default=0,
                     help="FP32 preconditioner, TF32 tensor-core mode products: 0 an autotuner candidate, 1 off, "
                          "2 wherever they apply (stst_set_tensor_products)")
@@ -723,11 +726,13 @@ def run_ours(args):
         cnt, tot = prof[dom]
         per_launch_s = tot / cnt / 1e3
         timing = "events around back-to-back profiled launches of the kernel"
+        # the fused mat-vec runs all levels of one application in a single launch
+        per_apply = 1 if dom.startswith("pass_fused") else n_passes
         if dom.startswith("pass"):
             # the mat-vec's launches: events around 30 back-to-back stst_apply_sys calls, per launch
-            per_launch_s = t_sys / n_passes / 1e3
+            per_launch_s = t_sys / per_apply / 1e3
             timing = (f"events around 30 back-to-back stst_apply_sys calls on the handle's stream, divided by "
-                      f"the {n_passes} launches of one call")
+                      f"the {per_apply} launch(es) of one call")
         if dom.startswith("modeprod_bf16"):
             # HBM/L2 bound on tensor cores: read FP32 tile + write FP32 result per complex unknown
             roof = {"kernel": dom, "bound": "hbm", "achieved": 16.0 * n_dof / per_launch_s / 1e9,
@@ -738,7 +743,7 @@ def run_ours(args):
             roof = {"kernel": dom, "bound": "alu", "achieved": flops / per_launch_s / 1e12,
                     "peak": peak, "unit": "TFLOP/s"}
         elif dom.startswith("pass"):
-            flops = flops_dof * n_dof / n_passes
+            flops = flops_dof * n_dof / per_apply
             peak = fp64_peak if dom.endswith("f64") else fp32_peak
             roof = {"kernel": dom, "bound": "alu", "achieved": flops / per_launch_s / 1e12,
                     "peak": peak, "unit": "TFLOP/s"}
@@ -755,8 +760,8 @@ def run_ours(args):
         roof["traffic"] = traffic_for(dom, {"n_dof": n_dof, "band_apps_per_dof": band_apps})
         if roof["traffic"] and dom.startswith("pass"):
             # the mat-vec's algorithmic bytes: x in and y out once per application, 32 B per unknown
-            roof["traffic_per_apply_sys"] = roof["traffic"] * n_passes
-            roof["traffic_over_algorithmic_bytes"] = roof["traffic"] * n_passes / (32.0 * n_dof)
+            roof["traffic_per_apply_sys"] = roof["traffic"] * per_apply
+            roof["traffic_over_algorithmic_bytes"] = roof["traffic"] * per_apply / (32.0 * n_dof)
         roof["share_of_step"] = shares[dom]
     out = {
         "metric": METRIC,
@@ -1140,6 +1145,7 @@ def main():
         S.stst_set_fused_transforms(args.fused_transforms)
         S.stst_set_pencil(args.pencil)
         S.stst_set_tensor_products(args.tensor_products)
+        S.stst_set_fused_matvec(args.fused_matvec)
         if args.config == "c4":
             run_batch(args)
         elif args.config == "c5":

@@ -386,6 +386,20 @@ int stst_pencil_info(stst_handle h, int *ctas_per_pencil);
  * product whose input is not 16-byte aligned runs on the SIMT tile).
  */
 int stst_set_tensor_products(int mode);
+/*
+ * stst_set_fused_matvec: the levels of the sum-factorised mat-vec (Eq. kron_vec_multi applied as a few
+ * passes of banded one-direction products) in one launch, with a grid barrier between levels, instead of
+ * one launch per level. Mode 0 (default): one launch per level; 1: one launch wherever the last level's
+ * 512-thread partial-sum grid fits the GPU at once (measured on c2: 112.7 us per mat-vec against 108.6 us
+ * for the separate launches, the two barriers cost more than the launch ramps they remove; kept as an
+ * option). FP64 mat-vecs only (the FP32 one of
+ * stst_ir_solve's inner solve keeps one launch per level). The outputs and the PCG's partial sums are
+ * bitwise those of the unfused launches. Handles in a batch (stst_batch_create) never fuse: their
+ * branches run concurrently. A barrier that waits too long sets a flag that the solve reports as
+ * STST_TIMEOUT. Process-wide, read at every mat-vec; captured solver graphs keep the form they were
+ * captured with. STST_ERR_ARG for other modes.
+ */
+int stst_set_fused_matvec(int mode);
 int stst_tensor_products_info(stst_handle h, int *dirs);
 int stst_fused_transforms_info(stst_handle h, int *fused);
 int stst_time_solver_info(stst_handle h, int precision, int *segments, int *segment_len, int *segmented);

@@ -72,6 +72,7 @@ def lib():
             "stst_set_pencil": [I],
             "stst_pencil_info": [P, IP],
             "stst_set_tensor_products": [I],
+            "stst_set_fused_matvec": [I],
             "stst_tensor_products_info": [P, IP],
             "stst_time_solver_info": [P, I, IP, IP, IP],
             "stst_tile_info": [P, I, IP, IP, DP],
@@ -325,6 +326,10 @@ def stst_pencil_info(h):
     f = ctypes.c_int()
     _chk(lib().stst_pencil_info(h, ctypes.byref(f)), "stst_pencil_info")
     return f.value
+
+
+def stst_set_fused_matvec(mode):
+    return _chk(lib().stst_set_fused_matvec(int(mode)), "stst_set_fused_matvec")
 
 
 def stst_set_tensor_products(mode):

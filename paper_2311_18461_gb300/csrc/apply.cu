@@ -183,6 +183,106 @@ static int launch_pass_t(const PassK &k, int p, int grid, cudaStream_t s, int th
   return STST_OK;
 }
 
+// ------------------------------------------------------------------------------------------------
+// All levels of one mat-vec in a single launch, opt-in (the c2 mat-vec's three levels otherwise pay
+// three launch ramps and tails; its SMs were busy 84-92% of each launch's elapsed cycles; measured: the two
+// grid barriers cost more than they save, 112.7 against 108.6 us per c2 mat-vec). Grid = the last
+// level's partial-sum grid with 512 threads, every CTA resident (checked against the occupancy on the
+// host); each level runs the unfused launch's element order rule (balanced contiguous ranges when a
+// level holds at most two elements per thread, else grid-stride), so every output and every per-CTA
+// partial is the unfused one, bitwise. Levels are separated by a grid barrier (count + generation in
+// global memory); its wait is bounded: on expiry it sets bit 3 of *err and the kernel carries on (the
+// results are then invalid and the caller reports the flag). Intermediate tensors are written in one
+// level and read in a later one, never read before they are written, so no SM holds a stale line.
+// ------------------------------------------------------------------------------------------------
+#define FUSED_MAXLEV 4
+struct FusedK {
+  PassK lv[FUSED_MAXLEV];
+  int p[FUSED_MAXLEV];
+  int n;
+  unsigned *bar;
+  int *err;
+};
+
+__device__ __forceinline__ void grid_barrier(unsigned *bar, int *err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *vgen = bar + 1;
+    const unsigned gen = *vgen;  // read before arriving: the last arrival advances it only after this
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u) + 1u;
+    if (arrived == gridDim.x) {
+      bar[0] = 0u;  // nobody touches the count again before the generation moves
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      for (int it = 0; *vgen == gen; ++it) {
+        if (it > (1 << 22)) {
+          atomicOr(err, 8);
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+template <typename R>
+__global__ void __launch_bounds__(512) k_pass_fused(const __grid_constant__ FusedK f) {
+  if (f.lv[0].done && *f.lv[0].done) return;
+  __shared__ double sh[32];
+  for (int lv = 0; lv < f.n; ++lv) {
+    const PassK &k = f.lv[lv];
+    const long long total = k.outer * k.n_mode_out * k.inner;
+    double dacc = 0.0, d2acc = 0.0;
+    const long long first = k.balanced ? (blockIdx.x * total) / gridDim.x + threadIdx.x
+                                       : blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long last = k.balanced ? ((blockIdx.x + 1) * total) / gridDim.x : total;
+    const long long step = k.balanced ? (long long)blockDim.x : (long long)gridDim.x * blockDim.x;
+    switch (f.p[lv]) {
+#define CASE(PP)                                                                                        \
+  case PP:                                                                                              \
+    for (int idx = (int)first; idx < (int)last; idx += (int)step) pass_element<R, PP, int>(k, idx, dacc, d2acc); \
+    break;
+      CASE(1) CASE(2) CASE(3) CASE(4) CASE(5) CASE(6) CASE(7) CASE(8)
+#undef CASE
+      default: break;
+    }
+    if (lv + 1 < f.n) {
+      grid_barrier(f.bar, f.err);
+    } else {
+      if (k.dot_partials) {
+        double s = block_sum(dacc, sh);
+        if (threadIdx.x == 0) k.dot_partials[blockIdx.x] = s;
+      }
+      if (k.dot2_partials) {
+        double s = block_sum(d2acc, sh);
+        if (threadIdx.x == 0) k.dot2_partials[blockIdx.x] = s;
+      }
+    }
+  }
+}
+
+int g_fused_matvec = 0;  // 0: one launch per level, 1: one launch for all levels where possible
+
+// CTAs of k_pass_fused<R> that fit at once (occupancy API, cached)
+template <typename R>
+static int fused_resident() {
+  static std::mutex mu;
+  static int cache[2] = {-1, -1};
+  std::lock_guard<std::mutex> lk(mu);
+  int &c = cache[sizeof(R) == 8 ? 1 : 0];
+  if (c >= 0) return c;
+  int per_sm = 0, dev = 0, sms = 152;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pass_fused<R>, 512, 0) != cudaSuccess) per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  c = per_sm * sms;
+  return c;
+}
+
 // Number of CTAs of every kernel that produces per-CTA partial sums: two per SM. Every consumer of
 // the partials reduces all of them (some redundantly in each of its CTAs), so fewer, fuller CTAs
 // keep that cheap; 16 warps per SM still cover the FP64 pipe latency of the mat-vec's last level.
@@ -199,6 +299,23 @@ int run_plan(const Plan &plan, const void *x, void *y, int precision, int epi, c
   if (plan.geo) return run_geo(*plan.geo, x, y, precision, epi, b, dotvec, dot_partials, done, s, dot2_partials);
   const int np = (int)plan.passes.size();
   if (np == 0) return STST_ERR_STATE;  // dropped by a failed re-plan (see stst_set_potential)
+  // one launch for all levels (opt-in, stst_set_fused_matvec): the handle allows it, every level's band
+  // half-width has a case, and the last level's partial-sum grid of 512-thread CTAs is resident at once
+  bool fused = false;
+  FusedK fk;
+  int fgrid = 0;
+  if (plan.fuse && plan.gbar && plan.gerr && g_fused_matvec == 1 && np >= 2 && np <= FUSED_MAXLEV) {
+    const PassParams &pl = plan.passes[np - 1];
+    const long long tl = pl.outer * (long long)pl.n_mode_out * pl.inner;
+    const int gl = reduction_grid(tl);
+    bool ok = true;
+    for (int ip = 0; ok && ip < np; ++ip) {
+      const PassParams &q = plan.passes[ip];
+      const long long t = q.outer * (long long)q.n_mode_out * q.inner;
+      if (q.p < 1 || q.p > 8 || t + 152LL * 16 * 512 > 0x7fffffffLL) ok = false;
+    }
+    fused = ok && precision == 0 && gl <= fused_resident<double>();  // FP64 (the FP32 variant spills)
+  }
   for (int ip = 0; ip < np; ++ip) {
     const PassParams &pp = plan.passes[ip];
     PassK k;
@@ -282,6 +399,22 @@ int run_plan(const Plan &plan, const void *x, void *y, int precision, int epi, c
         k.balanced = 1;
         if (ip != np - 1 && grid > res) grid = res;
       }
+    }
+    if (fused) {
+      fk.lv[ip] = k;
+      fk.p[ip] = pp.p;
+      if (ip == np - 1) {
+        // the last level's rule decides the partials; the inner levels keep their own rule (outputs
+        // do not depend on the element order)
+        fgrid = grid;
+        fk.n = np;
+        fk.bar = plan.gbar;
+        fk.err = plan.gerr;
+        STST_PROF("pass_fused_f64", s);
+        k_pass_fused<double><<<fgrid, 512, 0, s>>>(fk);
+        STST_CUDA(cudaGetLastError());
+      }
+      continue;
     }
     int st = precision == 1 ? launch_pass_t<float>(k, pp.p, grid, s, threads)
                             : launch_pass_t<double>(k, pp.p, grid, s, threads);

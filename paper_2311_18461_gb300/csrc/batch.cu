@@ -169,6 +169,13 @@ extern "C" int stst_batch_create(stst_batch *out, int count, const stst_handle *
   b->magic = STST_BATCH_MAGIC;
   b->count = count;
   b->hs.assign(handles, handles + count);
+  // the branches run concurrently: no kernel of theirs may wait for CTAs that other branches keep off
+  // the SMs, so the handles' mat-vecs stay one launch per level (no grid barriers)
+  for (int i = 0; i < count; ++i) {
+    handles[i]->no_fuse = 1;
+    handles[i]->sys_plan.fuse = 0;
+    handles[i]->lift_plan.fuse = 0;
+  }
   b->stream = (cudaStream_t)stream;
   if (!b->stream) {
     if (cudaStreamCreate(&b->stream) != cudaSuccess) {

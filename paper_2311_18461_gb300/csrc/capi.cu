@@ -367,6 +367,11 @@ int replan(stst_problem *h, const std::vector<Term> &terms) {
   const int s = replan_impl(h, terms);
   if (s != STST_OK) invalidate_plans(h);
   h->sys_plan.geo = h->geo;
+  for (Plan *pl : {&h->sys_plan, &h->lift_plan}) {
+    pl->fuse = h->no_fuse ? 0 : 1;
+    pl->gbar = h->gbar;
+    pl->gerr = h->flags + 1;
+  }
   return s;
 }
 
@@ -468,6 +473,7 @@ void destroy_all(stst_problem *h) {
     cudaFree(h->Tb[q]);
   }
   cudaFree(h->flags);
+  cudaFree(h->gbar);
   double *ws[] = {h->w_x, h->w_r, h->w_z, h->w_zold, h->w_p, h->w_q, h->w_f, h->w_t1, h->w_t2};
   for (double *w : ws) cudaFree(w);
   float *vs[] = {h->v_d, h->v_r, h->v_z, h->v_p, h->v_q};
@@ -540,6 +546,8 @@ int create_impl(stst_problem *h, int d, const int *n_el, const int *p, double T,
   }
   STST_CUDA(cudaMalloc(&h->flags, sizeof(int) * 4));
   STST_CUDA(cudaMemsetAsync(h->flags, 0, sizeof(int) * 4, st));
+  STST_CUDA(cudaMalloc(&h->gbar, sizeof(unsigned) * 2));
+  STST_CUDA(cudaMemsetAsync(h->gbar, 0, sizeof(unsigned) * 2, st));
   for (int l = 1; l <= d; ++l) {
     add_band(h, l, MK_M, nullptr);    // SM_M
     add_band(h, l, MK_L, nullptr);    // SM_L
@@ -1008,6 +1016,12 @@ int stst_pencil_info(stst_handle h, int *ctas_per_pencil) {
 }
 
 extern int g_tf32_mode;
+
+int stst_set_fused_matvec(int mode) {
+  if (mode < 0 || mode > 1) return STST_ERR_ARG;
+  g_fused_matvec = mode;
+  return STST_OK;
+}
 
 int stst_set_tensor_products(int mode) {
   if (mode < 0 || mode > 2) return STST_ERR_ARG;

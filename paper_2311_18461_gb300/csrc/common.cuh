@@ -80,6 +80,11 @@ struct Plan {
   std::vector<PassParams> passes;
   int n_levels = 0;
   const GeoOp *geo = nullptr;  // set: run_plan applies the mapped-domain operator instead of the passes
+  // one launch for all levels with grid barriers between them (k_pass_fused): allowed (the handle is not
+  // in a batch, whose branches run concurrently), the barrier state (count, generation) and its error flag
+  int fuse = 0;
+  unsigned *gbar = nullptr;
+  int *gerr = nullptr;
 };
 
 // ---- inner products in the epilogue of a preconditioner application -------------------------------
@@ -225,6 +230,8 @@ struct stst_problem {
   // plans
   Plan sys_plan, lift_plan;
   GeoOp *geo;                      // mapped-domain operator (stst_set_geometry), or null: the parametric one
+  unsigned *gbar;                  // grid-barrier state of the fused mat-vec: arrival count, generation
+  int no_fuse;                     // set by stst_batch_create: the handle's kernels may run concurrently
   std::vector<void *> pool;        // intermediate tensors of the plans (FP64 sized)
   std::vector<void *> scaled;      // coefficient-scaled band matrices of the plans
 
@@ -305,6 +312,7 @@ int launch_time_transfer(const void *G, const R *D, int nt, long long Ns, int P,
 int ensure_dyn_smem(const void *kern, size_t bytes);
 MpCfg modeprod_default(int n);
 int tune_modeprod(stst_problem *h);  // times the mode-product tiles once per shape (outside graph capture)
+extern int g_fused_matvec;  // 0: one launch per mat-vec level (default), 1: all levels in one launch
 extern int g_tune_enabled;
 extern int g_ts_mode;
 extern int g_fd2d_mode;

@@ -527,8 +527,9 @@ static int build_pcg_graph(stst_problem *h) {
   return STST_OK;
 }
 
-// Waits for the stream and reads the handle's bounded-wait flag (flags[1], bit 2: the tensor-core mode
-// product gave up waiting for its MMAs) into flags_host[1], clearing it on the device for the next call.
+// Waits for the stream and reads the handle's bounded-wait flag (flags[1], bit 2: a tensor-core mode
+// product gave up waiting for its copies or MMAs; bit 3: a grid barrier of the fused mat-vec gave up)
+// into flags_host[1], clearing it on the device for the next call.
 static int take_timeout_flag(stst_problem *h) {
   cudaStream_t st = h->stream;
   STST_CUDA(cudaMemcpyAsync(h->flags_host + 1, h->flags + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -570,7 +571,7 @@ int pcg_run(stst_problem *h, const double *rhs, double *x, double tol, int maxit
   const PcgCtl &c = *h->ctl_host;
   if (iters) *iters = c.it;
   if (relres) *relres = c.ff > 0 ? sqrt(c.rr / c.ff) : 0.0;
-  if (h->flags_host[1] & 4) return STST_TIMEOUT;
+  if (h->flags_host[1] & 12) return STST_TIMEOUT;  // bit 2: tensor-core waits, bit 3: grid barriers
   if (c.status != STST_OK) return c.status;
   if (!c.done) return STST_NOT_CONVERGED;
   return STST_OK;
@@ -734,6 +735,6 @@ int ir_run(stst_problem *h, const double *rhs, double *x, double tol, int maxit,
   if (iters) *iters = total_inner;
   if (outer) *outer = k;
   if (relres) *relres = c.ff > 0 ? sqrt(c.rr / c.ff) : 0.0;
-  if (h->flags_host[1] & 4) return STST_TIMEOUT;
+  if (h->flags_host[1] & 12) return STST_TIMEOUT;  // bit 2: tensor-core waits, bit 3: grid barriers
   return status;
 }
