@@ -400,6 +400,31 @@ int stst_set_tensor_products(int mode);
  * captured with. STST_ERR_ARG for other modes.
  */
 int stst_set_fused_matvec(int mode);
+
+/*
+ * stst_persistent_solve: the PCG of Sec. 5.3 and Sec. 6 (P-hat preconditioner, x_0 = 0, relative residual
+ * tol, at most maxit iterations) for `count` problems in ONE kernel launch: problem i is solved from start
+ * to end by one thread-block cluster of cluster_ctas CTAs (1, 2, 4, 8 or 16; 0 = 8), whose threads share
+ * every phase of the loop (the mat-vec's levels, <p, A p>, the updates, Algorithm 1 steps 2-4 with the
+ * sequential banded time solves, <r, z>) and meet at the cluster's hardware barrier between phases; the
+ * vectors stay in L2. For small problems, where a solve of separate kernels pays each kernel's latency
+ * (Table 1 sizes), and for many problems at once. Handles: distinct, built (stst_build_fd) with the FP64
+ * preconditioner (STST_PREC_FP64: plain CG, the paper's method), no geometry, degrees up to 4; any
+ * potential, formulation and sizes (a larger problem only takes longer: one cluster per problem).
+ * Measured (2D+t, p = 3): about 70 us per iteration at n_el = 8, below the graph solve's cost; at
+ * n_el = 16 and above the graph solve (the whole GPU per problem) is faster; the cluster's phases are
+ * bound by their L2 round trips and the FP64 rate of a few SMs. rhs[i], x[i]:
+ * device vectors of handle i (x[i] receives the solution). iters, status, relres: host arrays of count
+ * (may be NULL). Uses the handles' work vectors, synchronizes their streams, launches on `stream`
+ * (NULL: the first handle's stream), allocates and frees about 7 KB per problem, and returns when the
+ * solves are done: the largest per-problem status (STST_OK, STST_NOT_CONVERGED, STST_BREAKDOWN), or
+ * STST_ERR_ARG / STST_ERR_HANDLE / STST_ERR_STATE (a handle not built, not FP64, with a geometry, or a
+ * plan of more than four levels) / STST_ERR_CUDA. Results equal stst_pcg_solve's up to rounding (its
+ * sums run in another order).
+ */
+int stst_persistent_solve(int count, const stst_handle *handles, const double *const *rhs, double *const *x,
+                          double tol, int maxit, int cluster_ctas, int *iters, int *status, double *relres,
+                          void *stream);
 int stst_tensor_products_info(stst_handle h, int *dirs);
 int stst_fused_transforms_info(stst_handle h, int *fused);
 int stst_time_solver_info(stst_handle h, int precision, int *segments, int *segment_len, int *segmented);

@@ -14,7 +14,7 @@ from ._lib import (StstError, lib, library_path, stst_create, stst_create2, STST
                    stst_set_autotune,
                    stst_set_time_solver, stst_set_fused_transforms, stst_fused_transforms_info,
                    stst_set_pencil, stst_pencil_info, stst_set_tensor_products, stst_tensor_products_info,
-                   stst_set_geometry, stst_geometry_info, stst_set_fused_matvec,
+                   stst_set_geometry, stst_geometry_info, stst_set_fused_matvec, stst_persistent_solve,
                    stst_time_solver_info, stst_last_cuda_error, stst_tile_info, stst_ws_create,
                    stst_ws_destroy, stst_ws_num_params, stst_ws_get_params, stst_ws_set_params,
                    stst_ws_forward, stst_ws_set_output_scale, stst_ws_grad, stst_ws_train_step,
@@ -31,6 +31,7 @@ __all__ = ["StstError", "lib", "library_path", "stst_create", "stst_create2", "S
            "stst_plan_info", "stst_pcg_graph_info", "stst_set_prec_operator", "stst_batch_create", "stst_batch_solve", "stst_batch_destroy",
            "stst_set_autotune", "stst_set_time_solver", "stst_set_fused_transforms",
            "stst_fused_transforms_info", "stst_set_pencil", "stst_pencil_info", "stst_set_tensor_products", "stst_set_geometry", "stst_set_fused_matvec",
+           "stst_persistent_solve",
            "stst_geometry_info",
            "stst_tensor_products_info", "stst_time_solver_info", "stst_last_cuda_error", "stst_tile_info",
            "stst_ws_create", "stst_ws_destroy", "stst_ws_num_params", "stst_ws_get_params",

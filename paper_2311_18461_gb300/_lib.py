@@ -73,6 +73,7 @@ def lib():
             "stst_pencil_info": [P, IP],
             "stst_set_tensor_products": [I],
             "stst_set_fused_matvec": [I],
+            "stst_persistent_solve": [I, P, P, P, D, I, I, IP, IP, DP, P],
             "stst_tensor_products_info": [P, IP],
             "stst_time_solver_info": [P, I, IP, IP, IP],
             "stst_tile_info": [P, I, IP, IP, DP],
@@ -326,6 +327,21 @@ def stst_pencil_info(h):
     f = ctypes.c_int()
     _chk(lib().stst_pencil_info(h, ctypes.byref(f)), "stst_pencil_info")
     return f.value
+
+
+def stst_persistent_solve(handles, rhs, x, tol=1e-8, maxit=200, cluster_ctas=0, stream=None):
+    """All problems in one launch, one thread-block cluster each; returns (status, iterations, relres,
+    statuses): the largest per-problem status, then per-problem lists (errors raise StstError)."""
+    n = len(handles)
+    hs = (ctypes.c_void_p * n)(*[h.value if isinstance(h, ctypes.c_void_p) else h for h in handles])
+    rs = (ctypes.c_void_p * n)(*[_ptr(t) for t in rhs])
+    xs = (ctypes.c_void_p * n)(*[_ptr(t) for t in x])
+    it = (ctypes.c_int * n)()
+    stv = (ctypes.c_int * n)()
+    rr = (ctypes.c_double * n)()
+    s = _chk(lib().stst_persistent_solve(n, hs, rs, xs, float(tol), int(maxit), int(cluster_ctas), it, stv, rr,
+                                         _stream_ptr(stream)), "stst_persistent_solve")
+    return s, list(it), list(rr), list(stv)
 
 
 def stst_set_fused_matvec(mode):

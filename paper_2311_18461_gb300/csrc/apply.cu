@@ -293,6 +293,67 @@ int reduction_grid(long long total) {
   return g;
 }
 
+// The kernel parameters of level ip of a plan: its contributions output-major, its inputs and outputs
+// in the pool (the first level reads x); the last level's output, epilogue and partials are the
+// caller's. STST_ERR_ARG when the level has more contributions than the parameters hold.
+static int make_level(const Plan &plan, int ip, const void *x, int precision, const int *done, PassK &k) {
+  const PassParams &pp = plan.passes[ip];
+  k.n_out = pp.n_out;
+  int c = 0;
+  k.c_start[0] = 0;
+  // contributions are stored output-major in PassParams (app == contribution)
+  for (int a = 0; a < pp.n_app; ++a) {
+    k.c_in[a] = pp.app_in[a];
+    k.c_imag[a] = pp.app_imag[a];
+    k.c_mat[a] = precision == 1 ? (const void *)pp.mat32[a] : (const void *)pp.mat[a];
+  }
+  for (int bo = 0; bo < pp.n_out; ++bo) {
+    for (int a = 0; a < pp.n_app; ++a) {
+      if (pp.coef[a][bo] != 0.0) c++;
+    }
+    k.c_start[bo + 1] = c;
+  }
+  // reorder contributions output-major
+  {
+    int pos = 0;
+    int tin[PASS_MAXAPP], tim[PASS_MAXAPP];
+    double tco[PASS_MAXAPP];
+    const void *tma[PASS_MAXAPP];
+    for (int bo = 0; bo < pp.n_out; ++bo)
+      for (int a = 0; a < pp.n_app; ++a)
+        if (pp.coef[a][bo] != 0.0) {
+          if (pos >= PASS_MAXAPP) return STST_ERR_ARG;
+          tin[pos] = pp.app_in[a];
+          tim[pos] = pp.app_imag[a];
+          tco[pos] = pp.coef[a][bo];
+          tma[pos] = precision == 1 ? (const void *)pp.cmat32[a][bo] : (const void *)pp.cmat[a][bo];
+          pos++;
+        }
+    for (int q = 0; q < pos; ++q) {
+      k.c_in[q] = tin[q];
+      k.c_imag[q] = tim[q];
+      k.c_coef[q] = tco[q];
+      k.c_mat[q] = tma[q];
+    }
+  }
+  for (int a = 0; a < pp.n_in; ++a) k.in[a] = pp.in[a];
+  for (int bo = 0; bo < pp.n_out; ++bo) k.out[bo] = pp.out[bo];
+  if (ip == 0) k.in[0] = x;
+  k.n_mode_out = pp.n_mode_out;
+  k.n_mode_in = pp.n_mode_in;
+  k.row_off = pp.row_off;
+  k.inner = pp.inner;
+  k.outer = pp.outer;
+  k.epi = 0;
+  k.b = nullptr;
+  k.dotvec = nullptr;
+  k.dot_partials = nullptr;
+  k.dot2_partials = nullptr;
+  k.done = done;
+  k.balanced = 0;
+  return STST_OK;
+}
+
 int run_plan(const Plan &plan, const void *x, void *y, int precision, int epi, const void *b, const void *dotvec,
              double *dot_partials, const int *done, cudaStream_t s, const void *dot2vec, double *dot2_partials) {
   (void)dot2vec;
@@ -319,59 +380,7 @@ int run_plan(const Plan &plan, const void *x, void *y, int precision, int epi, c
   for (int ip = 0; ip < np; ++ip) {
     const PassParams &pp = plan.passes[ip];
     PassK k;
-    k.n_out = pp.n_out;
-    int c = 0;
-    k.c_start[0] = 0;
-    // contributions are stored output-major in PassParams (app == contribution)
-    for (int a = 0; a < pp.n_app; ++a) {
-      k.c_in[a] = pp.app_in[a];
-      k.c_imag[a] = pp.app_imag[a];
-      k.c_mat[a] = precision == 1 ? (const void *)pp.mat32[a] : (const void *)pp.mat[a];
-    }
-    for (int bo = 0; bo < pp.n_out; ++bo) {
-      for (int a = 0; a < pp.n_app; ++a) {
-        if (pp.coef[a][bo] != 0.0) c++;
-      }
-      k.c_start[bo + 1] = c;
-    }
-    // reorder contributions output-major
-    {
-      int pos = 0;
-      int tin[PASS_MAXAPP], tim[PASS_MAXAPP];
-      double tco[PASS_MAXAPP];
-      const void *tma[PASS_MAXAPP];
-      for (int bo = 0; bo < pp.n_out; ++bo)
-        for (int a = 0; a < pp.n_app; ++a)
-          if (pp.coef[a][bo] != 0.0) {
-            if (pos >= PASS_MAXAPP) return STST_ERR_ARG;
-            tin[pos] = pp.app_in[a];
-            tim[pos] = pp.app_imag[a];
-            tco[pos] = pp.coef[a][bo];
-            tma[pos] = precision == 1 ? (const void *)pp.cmat32[a][bo] : (const void *)pp.cmat[a][bo];
-            pos++;
-          }
-      for (int q = 0; q < pos; ++q) {
-        k.c_in[q] = tin[q];
-        k.c_imag[q] = tim[q];
-        k.c_coef[q] = tco[q];
-        k.c_mat[q] = tma[q];
-      }
-    }
-    for (int a = 0; a < pp.n_in; ++a) k.in[a] = pp.in[a];
-    for (int bo = 0; bo < pp.n_out; ++bo) k.out[bo] = pp.out[bo];
-    if (ip == 0) k.in[0] = x;
-    k.n_mode_out = pp.n_mode_out;
-    k.n_mode_in = pp.n_mode_in;
-    k.row_off = pp.row_off;
-    k.inner = pp.inner;
-    k.outer = pp.outer;
-    k.epi = 0;
-    k.b = nullptr;
-    k.dotvec = nullptr;
-    k.dot_partials = nullptr;
-    k.dot2_partials = nullptr;
-    k.done = done;
-    k.balanced = 0;
+    STST_TRY(make_level(plan, ip, x, precision, done, k));
     long long total = pp.outer * (long long)pp.n_mode_out * pp.inner;
     if (total + 152LL * 16 * 512 > 0x7fffffffLL) return STST_ERR_ARG;  // k_pass indexes in 32 bits
     int grid = reduction_grid(total);
@@ -1915,4 +1924,414 @@ int tune_modeprod(stst_problem *h) {
   STST_TRY(tune_pencil(h));
   h->tuned = 1;
   return STST_OK;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Persistent PCG for small problems (Sec. 5.3 and Sec. 6: CG preconditioned by P-hat, x_0 = 0): the whole
+// solve of one problem in one thread-block cluster, many problems in one launch (one cluster each).
+// Every phase is a loop over the problem's elements by the cluster's threads, phases are separated by
+// the cluster's hardware barrier, and the vectors stay in L2: they are read with ld.global.cg and written
+// with st.global.cg, because an SM's L1 would otherwise keep lines of a vector another SM has rewritten.
+// Per iteration: the mat-vec's levels (the handle's plan), <p, A p>, the x and r updates with ||r||^2,
+// Algorithm 1 (forward mode products, the banded time solves with the FP64 factors, backward mode
+// products) with <r, z>, and p = z + beta p; sums over the cluster go through per-CTA partials read back
+// in rank order (deterministic). The FP64 preconditioner (plain CG) only.
+// ------------------------------------------------------------------------------------------------
+#include <cooperative_groups.h>
+namespace cg = cooperative_groups;
+
+#define PERSIST_MAXC 16
+
+struct PersistResult {
+  int iters, status;
+  double relres;
+};
+
+struct PersistProb {
+  PassK lv[FUSED_MAXLEV];
+  int lv_p[FUSED_MAXLEV];
+  int n_lv;
+  int d, P_t;
+  int n[STST_MAXD + 1];              // n[0] = n_t, n[l] = n_l
+  long long inner[STST_MAXD + 1];    // inner extent of mode l (l >= 1) in the time-fastest layout
+  long long N_s, N;
+  const double *U[STST_MAXD + 1];
+  const double2 *G;                  // FP64 time factors (the layout of k_timesolve)
+  const double *D;
+  const double2 *b;
+  double2 *x, *r, *p, *q, *z, *t1, *t2;
+  double *part;                      // 3 x PERSIST_MAXC partial sums
+  double tol;
+  int maxit;
+  PersistResult *res;
+};
+
+__device__ __forceinline__ double2 ldcg2(const double2 *a) { return __ldcg(a); }
+__device__ __forceinline__ void stcg2(double2 *a, double2 v) { __stcg(a, v); }
+
+// one output element of a mat-vec level, as pass_element but with L2 loads and stores
+template <int P>
+__device__ __forceinline__ void persist_level_element(const PassK &k, long long idx) {
+  const long long inner = k.inner, nmo = k.n_mode_out;
+  const long long c = idx % inner, t = idx / inner;
+  const int j = (int)(t % nmo);
+  const long long o = t / nmo;
+  const long long base = o * k.n_mode_in * inner + c;
+  for (int bo = 0; bo < k.n_out; ++bo) {
+    double ax = 0.0, ay = 0.0;
+    for (int ci = k.c_start[bo]; ci < k.c_start[bo + 1]; ++ci) {
+      const double2 *in = (const double2 *)k.in[k.c_in[ci]];
+      const double *m = (const double *)k.c_mat[ci] + j * (2 * P + 1);
+      const bool im = k.c_imag[ci] != 0;
+#pragma unroll
+      for (int qq = 0; qq <= 2 * P; ++qq) {
+        const int jj = j + k.row_off - P + qq;
+        if (jj >= 0 && jj < k.n_mode_in) {
+          const double2 xv = ldcg2(in + base + (long long)jj * inner);
+          const double mv = m[qq];
+          if (im) {
+            ax -= mv * xv.y;
+            ay += mv * xv.x;
+          } else {
+            ax += mv * xv.x;
+            ay += mv * xv.y;
+          }
+        }
+      }
+    }
+    stcg2((double2 *)k.out[bo] + idx, make_double2(ax, ay));
+  }
+}
+
+#define PERSIST_MAXT 128  // time steps a thread stages in its local memory (longer series read L2 step by step)
+
+// The banded time solve of system i with the recurrences of k_timesolve (Algorithm 1 step 3).
+template <int P>
+__device__ __forceinline__ void persist_time_solve_sys(const PersistProb &pr, double2 *Y, long long i) {
+  const int nt = pr.n[0];
+  const long long Ns = pr.N_s;
+  // the system's series in thread-local memory: its loads are all issued before the recurrence
+  double2 ybuf[PERSIST_MAXT];
+  const bool staged = nt <= PERSIST_MAXT;
+  if (staged)
+    for (int t = 0; t < nt; ++t) ybuf[t] = ldcg2(Y + i * nt + t);
+  double2 w[P];
+#pragma unroll
+  for (int a = 0; a < P; ++a) w[a] = make_double2(0.0, 0.0);
+  for (int t = 0; t < nt; ++t) {  // G z = y: z_t = (y_t - sum_k G[t][t-k] z_{t-k}) / G[t][t]
+    const double2 y = staged ? ybuf[t] : ldcg2(Y + i * nt + t);
+    double ax = y.x, ay = y.y;
+#pragma unroll
+    for (int k = 1; k <= P; ++k) {
+      const double2 g = pr.G[((long long)t * P + (k - 1)) * Ns + i];
+      const double2 zz = w[k - 1];
+      ax -= g.x * zz.x - g.y * zz.y;
+      ay -= g.x * zz.y + g.y * zz.x;
+    }
+    const double dinv = pr.D[(long long)t * Ns + i];
+    const double2 zt = make_double2(ax * dinv, ay * dinv);
+#pragma unroll
+    for (int a = P - 1; a > 0; --a) w[a] = w[a - 1];
+    w[0] = zt;
+    if (staged) ybuf[t] = zt;
+    else stcg2(Y + i * nt + t, zt);
+  }
+#pragma unroll
+  for (int a = 0; a < P; ++a) w[a] = make_double2(0.0, 0.0);
+  for (int t = nt - 1; t >= 0; --t) {  // G^H x = z: x_t = (z_t - sum_k conj(G[t+k][t]) x_{t+k}) / G[t][t]
+    const double2 zt = staged ? ybuf[t] : ldcg2(Y + i * nt + t);
+    double ax = zt.x, ay = zt.y;
+#pragma unroll
+    for (int k = 1; k <= P; ++k) {
+      if (t + k < nt) {
+        const double2 g = pr.G[((long long)(t + k) * P + (k - 1)) * Ns + i];
+        const double2 xv = w[k - 1];
+        ax -= g.x * xv.x + g.y * xv.y;  // conj(g) x
+        ay -= g.x * xv.y - g.y * xv.x;
+      }
+    }
+    const double dinv = pr.D[(long long)t * Ns + i];
+    const double2 xt = make_double2(ax * dinv, ay * dinv);
+#pragma unroll
+    for (int a = P - 1; a > 0; --a) w[a] = w[a - 1];
+    w[0] = xt;
+    stcg2(Y + i * nt + t, xt);
+  }
+}
+
+// mode product along direction l: forward y[o, j, c] = sum_i U[i][j] x[o, i, c], backward with U^T
+__device__ __forceinline__ void persist_mode_product(const PersistProb &pr, int l, const double2 *X, double2 *Y,
+                                                     int backward, long long first, long long step) {
+  const int n = pr.n[l];
+  const long long inner = pr.inner[l];
+  const double *U = pr.U[l];
+  for (long long idx = first; idx < pr.N; idx += step) {
+    const long long c = idx % inner, t = idx / inner;
+    const int j = (int)(t % n);
+    const long long o = t / n;
+    const double2 *xs = X + o * n * inner + c;
+    double ax = 0.0, ay = 0.0;
+    int i = 0;
+    for (; i + 8 <= n; i += 8) {  // eight loads in flight per step
+      double2 v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = ldcg2(xs + (long long)(i + q) * inner);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const double u = backward ? U[j * n + i + q] : U[(i + q) * n + j];
+        ax += u * v[q].x;
+        ay += u * v[q].y;
+      }
+    }
+    for (; i < n; ++i) {
+      const double u = backward ? U[j * n + i] : U[i * n + j];
+      const double2 v = ldcg2(xs + (long long)i * inner);
+      ax += u * v.x;
+      ay += u * v.y;
+    }
+    stcg2(Y + idx, make_double2(ax, ay));
+  }
+}
+
+// sum of v over the cluster (every thread gets it): block sums written per CTA, read back in rank order
+__device__ __forceinline__ double cluster_sum(double v, double *slot, double *sh, cg::cluster_group &cl) {
+  const double s = block_sum(v, sh);
+  if (threadIdx.x == 0) __stcg(slot + cl.block_rank(), s);
+  cl.sync();
+  double t = 0.0;
+  const int C = (int)cl.num_blocks();
+  for (int a = 0; a < C; ++a) t += __ldcg(slot + a);
+  return t;
+}
+
+__global__ void __launch_bounds__(256) k_persist_pcg(const PersistProb *__restrict__ probs) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks();
+  const PersistProb &pr = probs[blockIdx.x / C];
+  __shared__ double sh[32];
+  const long long first = (long long)cl.block_rank() * blockDim.x + threadIdx.x;
+  const long long step = (long long)C * blockDim.x;
+  const long long N = pr.N;
+  double *pPQ = pr.part, *pRR = pr.part + PERSIST_MAXC, *pRZ = pr.part + 2 * PERSIST_MAXC;
+  // x_0 = 0, r = b, ||b||^2
+  double acc = 0.0;
+  for (long long e = first; e < N; e += step) {
+    const double2 bv = pr.b[e];
+    stcg2(pr.x + e, make_double2(0.0, 0.0));
+    stcg2(pr.r + e, bv);
+    acc += bv.x * bv.x + bv.y * bv.y;
+  }
+  const double ff = cluster_sum(acc, pRR, sh, cl);
+  int status = STST_OK, it = 0;
+  double rr = ff;
+  // z = P-hat^{-1} r (Algorithm 1 steps 2-4); <r, z>
+  auto precondition = [&](double &rz) {
+    const double2 *src = pr.r;
+    double2 *bufs[2] = {pr.t1, pr.t2};
+    int cur = 0;
+    for (int l = 1; l <= pr.d; ++l) {
+      persist_mode_product(pr, l, src, bufs[cur], 0, first, step);
+      cl.sync();
+      src = bufs[cur];
+      cur ^= 1;
+    }
+    double2 *y = (double2 *)src;
+    for (long long i = first; i < pr.N_s; i += step) {
+      switch (pr.P_t) {
+#define CASE(PP) case PP: persist_time_solve_sys<PP>(pr, y, i); break;
+        CASE(1) CASE(2) CASE(3) CASE(4)
+#undef CASE
+        default: break;
+      }
+    }
+    cl.sync();
+    for (int l = pr.d; l >= 1; --l) {
+      double2 *dst = l == 1 ? pr.z : bufs[cur];
+      persist_mode_product(pr, l, src, dst, 1, first, step);
+      cl.sync();
+      src = dst;
+      cur ^= 1;
+    }
+    double a = 0.0;
+    for (long long e = first; e < N; e += step) {
+      const double2 rv = ldcg2(pr.r + e), zv = ldcg2(pr.z + e);
+      a += rv.x * zv.x + rv.y * zv.y;  // Re <r, z> (real for the Hermitian P-hat)
+    }
+    rz = cluster_sum(a, pRZ, sh, cl);
+  };
+  if (ff == 0.0) {
+    rr = 0.0;
+  } else {
+    double rho;
+    precondition(rho);
+    for (long long e = first; e < N; e += step) stcg2(pr.p + e, ldcg2(pr.z + e));
+    cl.sync();
+    while (it < pr.maxit) {
+      // q = A p by the plan's levels
+      for (int lv = 0; lv < pr.n_lv; ++lv) {
+        const PassK &k = pr.lv[lv];
+        const long long total = k.outer * k.n_mode_out * k.inner;
+        for (long long e = first; e < total; e += step) {
+          switch (pr.lv_p[lv]) {
+#define CASE(PP) case PP: persist_level_element<PP>(k, e); break;
+            CASE(1) CASE(2) CASE(3) CASE(4)
+#undef CASE
+            default: break;
+          }
+        }
+        cl.sync();
+      }
+      double a = 0.0;
+      for (long long e = first; e < N; e += step) {
+        const double2 pv = ldcg2(pr.p + e), qv = ldcg2(pr.q + e);
+        a += pv.x * qv.x + pv.y * qv.y;
+      }
+      const double pq = cluster_sum(a, pPQ, sh, cl);
+      if (!(pq > 0.0) || !isfinite(pq)) {
+        status = STST_BREAKDOWN;
+        break;
+      }
+      const double alpha = rho / pq;
+      a = 0.0;
+      for (long long e = first; e < N; e += step) {
+        const double2 pv = ldcg2(pr.p + e), qv = ldcg2(pr.q + e);
+        double2 xv = ldcg2(pr.x + e), rv = ldcg2(pr.r + e);
+        xv.x += alpha * pv.x;
+        xv.y += alpha * pv.y;
+        rv.x -= alpha * qv.x;
+        rv.y -= alpha * qv.y;
+        stcg2(pr.x + e, xv);
+        stcg2(pr.r + e, rv);
+        a += rv.x * rv.x + rv.y * rv.y;
+      }
+      rr = cluster_sum(a, pRR, sh, cl);
+      ++it;
+      if (rr <= pr.tol * pr.tol * ff) break;
+      double rho_new;
+      precondition(rho_new);
+      const double beta = rho_new / rho;
+      rho = rho_new;
+      for (long long e = first; e < N; e += step) {
+        const double2 zv = ldcg2(pr.z + e);
+        double2 pv = ldcg2(pr.p + e);
+        pv.x = zv.x + beta * pv.x;
+        pv.y = zv.y + beta * pv.y;
+        stcg2(pr.p + e, pv);
+      }
+      cl.sync();
+    }
+    if (status == STST_OK && rr > pr.tol * pr.tol * ff) status = STST_NOT_CONVERGED;
+  }
+  if (cl.block_rank() == 0 && threadIdx.x == 0) {
+    pr.res->iters = it;
+    pr.res->status = status;
+    pr.res->relres = ff > 0.0 ? sqrt(rr / ff) : 0.0;
+  }
+}
+
+extern "C" int stst_persistent_solve(int count, const stst_handle *handles, const double *const *rhs,
+                                     double *const *x, double tol, int maxit, int cluster_ctas, int *iters,
+                                     int *status, double *relres, void *stream) {
+  if (count < 1 || !handles || !rhs || !x || !(tol >= 0.0) || maxit < 0) return STST_ERR_ARG;
+  const int C = cluster_ctas == 0 ? 8 : cluster_ctas;
+  if (C != 1 && C != 2 && C != 4 && C != 8 && C != 16) return STST_ERR_ARG;
+  std::vector<PersistProb> probs((size_t)count);
+  for (int i = 0; i < count; ++i) {
+    stst_problem *h = handles[i];
+    if (!h || h->magic != STST_MAGIC) return STST_ERR_HANDLE;
+    if (!rhs[i] || !x[i]) return STST_ERR_ARG;
+    for (int j = 0; j < i; ++j)
+      if (handles[j] == h) return STST_ERR_ARG;  // the work vectors are per handle
+    if (!h->fd_ready || h->prec_mode != STST_PREC_FP64 || h->geo) return STST_ERR_STATE;
+    const Plan &plan = h->sys_plan;
+    const int np = (int)plan.passes.size();
+    if (np < 1 || np > FUSED_MAXLEV) return STST_ERR_STATE;
+    PersistProb &pr = probs[i];
+    for (int ip = 0; ip < np; ++ip) {
+      const PassParams &pp = plan.passes[ip];
+      if (pp.p < 1 || pp.p > 4) return STST_ERR_STATE;  // degrees up to 4 (the kernel's cases)
+      STST_TRY(make_level(plan, ip, h->w_p, 0, nullptr, pr.lv[ip]));
+      pr.lv_p[ip] = pp.p;
+    }
+    pr.lv[np - 1].out[0] = h->w_q;
+    pr.n_lv = np;
+    pr.d = h->d;
+    pr.P_t = h->dir[0].p;
+    if (pr.P_t < 1 || pr.P_t > 4) return STST_ERR_STATE;
+    long long acc = h->n_t();
+    pr.n[0] = h->n_t();
+    for (int l = 1; l <= h->d; ++l) {
+      pr.n[l] = h->dir[l].n;
+      pr.inner[l] = acc;
+      acc *= h->dir[l].n;
+      pr.U[l] = h->U[l];
+    }
+    pr.N_s = h->N_s;
+    pr.N = h->N_dof;
+    pr.G = (const double2 *)h->Hg;
+    pr.D = h->Hd;
+    pr.b = (const double2 *)rhs[i];
+    pr.x = (double2 *)x[i];
+    pr.r = (double2 *)h->w_r;
+    pr.p = (double2 *)h->w_p;
+    pr.q = (double2 *)h->w_q;
+    pr.z = (double2 *)h->w_z;
+    pr.t1 = (double2 *)h->w_t1;
+    pr.t2 = (double2 *)h->w_t2;
+    pr.tol = tol;
+    pr.maxit = maxit;
+  }
+  for (int i = 0; i < count; ++i) STST_CUDA(cudaStreamSynchronize(handles[i]->stream));
+  cudaStream_t st = stream ? (cudaStream_t)stream : handles[0]->stream;
+  // descriptors, partial sums and results: one allocation, freed before returning
+  const size_t bytes_probs = sizeof(PersistProb) * count;
+  const size_t bytes_part = sizeof(double) * 3 * PERSIST_MAXC * count;
+  const size_t bytes_res = sizeof(PersistResult) * count;
+  char *dmem = nullptr;
+  STST_CUDA(cudaMalloc(&dmem, bytes_probs + bytes_part + bytes_res));
+  PersistProb *dprobs = (PersistProb *)dmem;
+  double *dpart = (double *)(dmem + bytes_probs);
+  PersistResult *dres = (PersistResult *)(dmem + bytes_probs + bytes_part);
+  for (int i = 0; i < count; ++i) {
+    probs[i].part = dpart + (size_t)3 * PERSIST_MAXC * i;
+    probs[i].res = dres + i;
+  }
+  std::vector<PersistResult> hres((size_t)count);
+  int s = STST_OK;
+  if (cudaMemcpyAsync(dprobs, probs.data(), bytes_probs, cudaMemcpyHostToDevice, st) != cudaSuccess) s = STST_ERR_CUDA;
+  if (s == STST_OK) {
+    if (C == 16) cudaFuncSetAttribute(k_persist_pcg, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(count * C));
+    cfg.blockDim = dim3(256);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    STST_PROF("persist_pcg", st);
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, k_persist_pcg, (const PersistProb *)dprobs);
+    if (e != cudaSuccess) {
+      stst_last_cuda = e;
+      s = STST_ERR_CUDA;
+    }
+  }
+  if (s == STST_OK &&
+      (cudaMemcpyAsync(hres.data(), dres, bytes_res, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+       cudaStreamSynchronize(st) != cudaSuccess))
+    s = STST_ERR_CUDA;
+  cudaStreamSynchronize(st);
+  cudaFree(dmem);
+  if (s != STST_OK) return s;
+  int worst = STST_OK;
+  for (int i = 0; i < count; ++i) {
+    if (iters) iters[i] = hres[i].iters;
+    if (status) status[i] = hres[i].status;
+    if (relres) relres[i] = hres[i].relres;
+    if (hres[i].status > worst) worst = hres[i].status;
+  }
+  return worst;
 }
