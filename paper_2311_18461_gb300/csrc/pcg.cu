@@ -154,6 +154,8 @@ int update_grid(long long n) {
 // flexible, of conj(p) r_new = <r_new, p>. No CTA of this kernel reads a scalar or partial that another
 // CTA of it writes: the <r, p_old> partials are double-buffered by iteration parity (iteration k writes
 // half k & 1 of prp and reads the other half, written by iteration k - 1).
+__device__ __forceinline__ double dfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 template <typename T, bool FLEX>
 __global__ void __launch_bounds__(256) k_update_xr(T *__restrict__ x, T *__restrict__ r, const T *__restrict__ p,
                                                    const T *__restrict__ q, PcgCtl *ctl, long long n, double *prr,
@@ -205,28 +207,37 @@ __global__ void __launch_bounds__(256) k_update_xr(T *__restrict__ x, T *__restr
     pq = v[0];
     num_re = v[1];
   }
-  const bool bad = !(pq > 0.0) || !isfinite(pq) || !isfinite(num_re) || !isfinite(num_im);
-  const double a_re = bad ? 0.0 : num_re / pq, a_im = bad ? 0.0 : num_im / pq;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    ctl->pq = pq;
-    ctl->rho = num_re;
-    ctl->sig_re = num_re;
-    ctl->sig_im = num_im;
-    ctl->alpha = a_re;
-    ctl->alpha_im = a_im;
-    if (bad) ctl->status = STST_BREAKDOWN;  // the check kernel ends the loop
+  // alpha by thread 0 alone and broadcast: a division is a sequence of FP64 operations, and 256 threads of
+  // every CTA repeating it cost FP64 issue comparable to a quarter of the vector arithmetic
+  if (threadIdx.x == 0) {
+    const bool bad = !(pq > 0.0) || !isfinite(pq) || !isfinite(num_re) || !isfinite(num_im);
+    sh[8] = bad ? 0.0 : num_re / pq;
+    sh[9] = bad ? 0.0 : num_im / pq;
+    if (blockIdx.x == 0) {
+      ctl->pq = pq;
+      ctl->rho = num_re;
+      ctl->sig_re = num_re;
+      ctl->sig_im = num_im;
+      ctl->alpha = sh[8];
+      ctl->alpha_im = sh[9];
+      if (bad) ctl->status = STST_BREAKDOWN;  // the check kernel ends the loop
+    }
   }
+  __syncthreads();
+  const double a_re = sh[8], a_im = sh[9];
   double arr = 0.0, arp_re = 0.0, arp_im = 0.0;
   for (; i0 < n; i0 += stride) {
 #pragma unroll
     for (int u = 0; u < UPT; ++u) {
       const long long i = i0 + 256 * u;
       if (i < n) {
+        // chains of fused multiply-adds: two FP64 operations per real term instead of a product, a fused
+        // product and an addition
         if constexpr (FLEX) {
-          xv[u].x += a_re * pv[u].x - a_im * pv[u].y;
-          xv[u].y += a_re * pv[u].y + a_im * pv[u].x;
-          rv[u].x -= a_re * qv[u].x - a_im * qv[u].y;
-          rv[u].y -= a_re * qv[u].y + a_im * qv[u].x;
+          xv[u].x = dfma(a_re, pv[u].x, dfma(-a_im, pv[u].y, xv[u].x));
+          xv[u].y = dfma(a_re, pv[u].y, dfma(a_im, pv[u].x, xv[u].y));
+          rv[u].x = dfma(-a_re, qv[u].x, dfma(a_im, qv[u].y, rv[u].x));
+          rv[u].y = dfma(-a_re, qv[u].y, dfma(-a_im, qv[u].x, rv[u].y));
         } else {
           xv[u].x += a_re * pv[u].x;
           xv[u].y += a_re * pv[u].y;
@@ -235,10 +246,12 @@ __global__ void __launch_bounds__(256) k_update_xr(T *__restrict__ x, T *__restr
         }
         x[i] = xv[u];
         r[i] = rv[u];
-        arr += (double)rv[u].x * rv[u].x + (double)rv[u].y * rv[u].y;
+        const double rx = rv[u].x, ry = rv[u].y;
+        arr = dfma(rx, rx, dfma(ry, ry, arr));
         if constexpr (FLEX) {
-          arp_re += (double)pv[u].x * rv[u].x + (double)pv[u].y * rv[u].y;
-          arp_im += (double)pv[u].x * rv[u].y - (double)pv[u].y * rv[u].x;
+          const double px = pv[u].x, py = pv[u].y;
+          arp_re = dfma(px, rx, dfma(py, ry, arp_re));
+          arp_im = dfma(px, ry, dfma(-py, rx, arp_im));
         }
       }
     }
@@ -311,36 +324,50 @@ __global__ void __launch_bounds__(256) k_update_p(T *__restrict__ p, const T *__
   };
   if (i0 < n) load(i0);
   double b_re, b_im = 0.0;
-  bool bad;
+  // beta by thread 0 alone and broadcast (one division per CTA, not per thread)
   if constexpr (FLEX) {
-    const double pq = ctl->pq;
     const double *gp[2] = {pz + 2 * STST_MAXPART, pz + 3 * STST_MAXPART};
     const int gn[2] = {nz, nz};
     double g[2];
     reduce_partials_all(gp, gn, g, sh);
-    b_re = -g[0] / pq;
-    b_im = -g[1] / pq;
-    bad = !isfinite(b_re) || !isfinite(b_im);
+    if (threadIdx.x == 0) {
+      const double pq = ctl->pq;
+      b_re = -g[0] / pq;
+      b_im = -g[1] / pq;
+      const bool bad = !isfinite(b_re) || !isfinite(b_im);
+      sh[8] = bad ? 0.0 : b_re;
+      sh[9] = bad ? 0.0 : b_im;
+      if (bad && blockIdx.x == 0) ctl->status = STST_BREAKDOWN;
+    }
   } else {
-    const double rho_old = ctl->rho;
     const double *rp[1] = {pz};
     const int rn[1] = {nz};
     double rv[1];
     reduce_partials_all(rp, rn, rv, sh);
-    const double rho_new = rv[0];
-    bad = !(rho_new > 0.0) || !isfinite(rho_new);
-    b_re = rho_new / rho_old;
+    if (threadIdx.x == 0) {
+      const double rho_old = ctl->rho, rho_new = rv[0];
+      const bool bad = !(rho_new > 0.0) || !isfinite(rho_new);
+      sh[8] = bad ? 0.0 : rho_new / rho_old;
+      sh[9] = 0.0;
+      if (bad && blockIdx.x == 0) ctl->status = STST_BREAKDOWN;
+    }
   }
-  if (bad) b_re = b_im = 0.0;
-  if (bad && blockIdx.x == 0 && threadIdx.x == 0) ctl->status = STST_BREAKDOWN;
+  __syncthreads();
+  b_re = sh[8];
+  b_im = sh[9];
   for (; i0 < n; i0 += stride) {
 #pragma unroll
     for (int u = 0; u < UPT; ++u) {
       const long long i = i0 + 256 * u;
       if (i < n) {
         const double px = pv[u].x, py = pv[u].y;
-        pv[u].x = zv[u].x + (b_re * px - b_im * py);
-        pv[u].y = zv[u].y + (b_re * py + b_im * px);
+        if constexpr (FLEX) {
+          pv[u].x = dfma(b_re, px, dfma(-b_im, py, (double)zv[u].x));
+          pv[u].y = dfma(b_re, py, dfma(b_im, px, (double)zv[u].y));
+        } else {
+          pv[u].x = dfma(b_re, px, (double)zv[u].x);
+          pv[u].y = dfma(b_re, py, (double)zv[u].y);
+        }
         p[i] = pv[u];
       }
     }
