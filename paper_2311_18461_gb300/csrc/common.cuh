@@ -104,14 +104,17 @@ struct EpiDot {
 
 template <typename TO>
 __device__ __forceinline__ void epi_dot_acc(double (&acc)[4], const EpiDot &ed, long long idx, double vx, double vy) {
+  // chains of fused multiply-adds (two FP64 operations per term, not a product, a fused product and a sum)
   const TO av = ((const TO *)ed.a)[idx];
-  acc[0] += (double)av.x * vx + (double)av.y * vy;
+  const double ax = av.x, ay = av.y;
+  acc[0] = __fma_rn(ax, vx, __fma_rn(ay, vy, acc[0]));
   if (ed.cplx) {
-    acc[1] += (double)av.x * vy - (double)av.y * vx;
+    acc[1] = __fma_rn(ax, vy, __fma_rn(-ay, vx, acc[1]));
     if (ed.b) {
       const TO bv = ((const TO *)ed.b)[idx];
-      acc[2] += (double)bv.x * vx + (double)bv.y * vy;
-      acc[3] += (double)bv.x * vy - (double)bv.y * vx;
+      const double bx = bv.x, by = bv.y;
+      acc[2] = __fma_rn(bx, vx, __fma_rn(by, vy, acc[2]));
+      acc[3] = __fma_rn(bx, vy, __fma_rn(-by, vx, acc[3]));
     }
   }
 }

@@ -231,11 +231,16 @@ __global__ void __launch_bounds__(512) k_eig_tridiag(const double *__restrict__ 
       for (int i = (tid & 31); i < m; i += 32) s += pv[i] * A[(k + 1 + i) * ld + k];
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       const float kk = 0.5f * beta * s;
-      for (int e = tid; e < m * m; e += nth) {
-        int i = e / m, j = e - (e / m) * m;
-        const float vi = A[(k + 1 + i) * ld + k], vj = A[(k + 1 + j) * ld + k];
-        const float wi = pv[i] - kk * vi, wj = pv[j] - kk * vj;
-        A[(k + 1 + i) * ld + (k + 1 + j)] -= vi * wj + wi * vj;
+      // rank-2 update, a row per warp and a column per lane: v_i and w_i are warp-uniform (broadcast
+      // reads) and no thread divides to find its element
+      for (int i = tid >> 5; i < m; i += nth >> 5) {
+        const float vi = A[(k + 1 + i) * ld + k];
+        const float wi = pv[i] - kk * vi;
+        for (int j = tid & 31; j < m; j += 32) {
+          const float vj = A[(k + 1 + j) * ld + k];
+          const float wj = pv[j] - kk * vj;
+          A[(k + 1 + i) * ld + (k + 1 + j)] -= vi * wj + wi * vj;
+        }
       }
     }
     __syncthreads();  // also when beta = 0: bc[1] is rewritten by the next step
@@ -808,8 +813,14 @@ int fd_setup_launch(stst_problem *h) {
       STST_CUDA(cudaMemcpyAsync(h->lam[l], h->lam[src], sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     }
     { STST_PROF("to_f32", st); STST_TRY(launch_to_f32(h->U[l], h->U32[l], (long long)h->dir[l].n * h->dir[l].n, st)); }
-    if (h->prec_mode == STST_PREC_BF16) STST_TRY(launch_u_to_bf16(h->U[l], h->dir[l].n, h->Ubf[l], st));
-    if (h->prec_mode == STST_PREC_FP32) STST_TRY(launch_u_to_tf32(h->U[l], h->dir[l].n, h->Utf[l], st));
+    if (h->prec_mode == STST_PREC_BF16) {
+      STST_PROF("u_to_bf16", st);
+      STST_TRY(launch_u_to_bf16(h->U[l], h->dir[l].n, h->Ubf[l], st));
+    }
+    if (h->prec_mode == STST_PREC_FP32) {
+      STST_PROF("u_to_tf32", st);
+      STST_TRY(launch_u_to_tf32(h->U[l], h->dir[l].n, h->Utf[l], st));
+    }
   }
   // a mapped domain: the eigenvalues scaled per direction by the mean of the metric's diagonal
   // (stst_set_geometry), after any sharing of eigenpairs between directions
