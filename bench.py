@@ -799,6 +799,7 @@ def run_ours(args):
         "time_solver": dict(zip(("segments", "segment_len", "segmented"),
                                 S.stst_time_solver_info(prob.h, 0 if args.prec == "fp64" else 1))),
         "fused_2d_transforms": S.stst_fused_transforms_info(prob.h),
+        "fused_2d_backward_split": S.stst_fused_transforms_split(prob.h)[1],
         "pencil_ctas": S.stst_pencil_info(prob.h),
         "kernels_ms_per_step": {k: round(ms * v, 4) for k, v in sorted(shares.items(), key=lambda kv: -kv[1])},
         "kernels_ms_profiled_solve": {k: round(v[1], 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},

@@ -344,12 +344,14 @@ int stst_set_time_solver(int mode);
  * (t, i_3) take its n_1 x n_2 slab through both products in shared memory; the forward transform is
  * split by rows, the backward one by columns) instead of two mode-product kernels; direction 3 stays
  * a mode-product kernel. Mode 0 (default) chooses per shape when the
- * preconditioner is built (separate kernels or a split S = 1..4, timed under autotune mode 1; else
- * fused with the smallest S that gives two CTAs per SM); 1 = separate kernels; 2 = fused with that
- * default split; 11..14 = fused with S = mode - 10 (the default split where S would leave a part
+ * preconditioner is built (separate kernels or fused, timed under autotune mode 1; fused, the forward
+ * and the backward transform each take the split S = 1..4 that times fastest for it; else fused with
+ * the smallest S that gives two CTAs per SM); 1 = separate kernels; 2 = fused with that default split;
+ * 11..14 = fused with S = mode - 10 for both transforms (the default split where S would leave a part
  * empty). All give bitwise equal preconditioner outputs (same summation order and FP32
  * intermediate). Process-wide, for handles whose preconditioner is built afterwards; STST_ERR_ARG for
- * other modes. stst_fused_transforms_info: S of the handle, 0 when it uses separate kernels.
+ * other modes. stst_fused_transforms_info: S of the handle's forward transform, 0 when it uses separate
+ * kernels.
  */
 int stst_set_fused_transforms(int mode);
 /*
@@ -427,6 +429,9 @@ int stst_persistent_solve(int count, const stst_handle *handles, const double *c
                           void *stream);
 int stst_tensor_products_info(stst_handle h, int *dirs);
 int stst_fused_transforms_info(stst_handle h, int *fused);
+/* The splits S of the handle's fused forward and backward transforms (both 0: separate kernels); either
+ * pointer may be NULL. STST_ERR_HANDLE for an invalid handle. */
+int stst_fused_transforms_split(stst_handle h, int *forward, int *backward);
 int stst_time_solver_info(stst_handle h, int precision, int *segments, int *segment_len, int *segmented);
 /* Name and description of the CUDA error behind the calling thread's last STST_ERR_CUDA (static string). */
 const char *stst_last_cuda_error(void);

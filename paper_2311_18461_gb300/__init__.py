@@ -12,7 +12,7 @@ from ._lib import (StstError, lib, library_path, stst_create, stst_create2, STST
                    stst_rhs_noalloc, stst_rhs_lift, stst_pcg_solve, stst_ir_solve, stst_profile, stst_profile_read,
                    stst_plan_info, stst_pcg_graph_info, stst_set_prec_operator, stst_batch_create, stst_batch_solve, stst_batch_destroy,
                    stst_set_autotune,
-                   stst_set_time_solver, stst_set_fused_transforms, stst_fused_transforms_info,
+                   stst_set_time_solver, stst_set_fused_transforms, stst_fused_transforms_info, stst_fused_transforms_split,
                    stst_set_pencil, stst_pencil_info, stst_set_tensor_products, stst_tensor_products_info,
                    stst_set_geometry, stst_geometry_info, stst_set_fused_matvec, stst_persistent_solve,
                    stst_time_solver_info, stst_last_cuda_error, stst_tile_info, stst_ws_create,
@@ -30,7 +30,7 @@ __all__ = ["StstError", "lib", "library_path", "stst_create", "stst_create2", "S
            "stst_rhs_noalloc", "stst_rhs_lift", "stst_pcg_solve", "stst_ir_solve", "stst_profile", "stst_profile_read",
            "stst_plan_info", "stst_pcg_graph_info", "stst_set_prec_operator", "stst_batch_create", "stst_batch_solve", "stst_batch_destroy",
            "stst_set_autotune", "stst_set_time_solver", "stst_set_fused_transforms",
-           "stst_fused_transforms_info", "stst_set_pencil", "stst_pencil_info", "stst_set_tensor_products", "stst_set_geometry", "stst_set_fused_matvec",
+           "stst_fused_transforms_info", "stst_fused_transforms_split", "stst_set_pencil", "stst_pencil_info", "stst_set_tensor_products", "stst_set_geometry", "stst_set_fused_matvec",
            "stst_persistent_solve",
            "stst_geometry_info",
            "stst_tensor_products_info", "stst_time_solver_info", "stst_last_cuda_error", "stst_tile_info",

@@ -69,6 +69,7 @@ def lib():
             "stst_set_time_solver": [I],
             "stst_set_fused_transforms": [I],
             "stst_fused_transforms_info": [P, IP],
+            "stst_fused_transforms_split": [P, IP, IP],
             "stst_set_pencil": [I],
             "stst_pencil_info": [P, IP],
             "stst_set_tensor_products": [I],
@@ -317,6 +318,12 @@ def stst_fused_transforms_info(h):
     f = ctypes.c_int()
     _chk(lib().stst_fused_transforms_info(h, ctypes.byref(f)), "stst_fused_transforms_info")
     return f.value
+
+
+def stst_fused_transforms_split(h):
+    f, b = ctypes.c_int(), ctypes.c_int()
+    _chk(lib().stst_fused_transforms_split(h, ctypes.byref(f), ctypes.byref(b)), "stst_fused_transforms_split")
+    return f.value, b.value
 
 
 def stst_set_pencil(mode):

@@ -1582,12 +1582,12 @@ int fd_apply(stst_problem *h, const double *r, double *s, int precision, const E
       return launch_pencil<double2, double2>((const double2 *)r, (double2 *)s, h, CL, ed, done, st);
     }
     if (d == 3 && h->fd2d) {
-      const int S = h->fd2d;
+      const int S = h->fd2d, Sb = h->fd2d_b;
       if (in32) STST_TRY((launch_fd2d<float2, float2>((const float2 *)in32, y32, h, 0, none, done, st, S)));
       else STST_TRY((launch_fd2d<double2, float2>((const double2 *)r, y32, h, 0, none, done, st, S)));
       STST_TRY((launch_pencil<float2, float2>(y32, z32, h, CL, none, done, st)));
-      if (out32) return launch_fd2d<float2, float2>(z32, (float2 *)out32, h, 1, ed, done, st, S);
-      return launch_fd2d<float2, double2>(z32, (double2 *)s, h, 1, ed, done, st, S);
+      if (out32) return launch_fd2d<float2, float2>(z32, (float2 *)out32, h, 1, ed, done, st, Sb);
+      return launch_fd2d<float2, double2>(z32, (double2 *)s, h, 1, ed, done, st, Sb);
     }
     // mode products of directions 1 .. d-1 forward (alternating buffers), the pencil, then backward
     float2 *bufs[2] = {y32, z32};
@@ -1624,7 +1624,7 @@ int fd_apply(stst_problem *h, const double *r, double *s, int precision, const E
   }
   if (h->fd2d) {  // modes 1 and 2 of each transform in one kernel per (t, i3) slab; mode 3 (d = 3) separate
     float2 *y32 = (float2 *)bufA;
-    const int S = h->fd2d;
+    const int S = h->fd2d, Sb = h->fd2d_b;
     if (in32) STST_TRY((launch_fd2d<float2, float2>((const float2 *)in32, y32, h, 0, none, done, st, S)));
     else STST_TRY((launch_fd2d<double2, float2>((const double2 *)r, y32, h, 0, none, done, st, S)));
     if (d == 3) {
@@ -1637,8 +1637,8 @@ int fd_apply(stst_problem *h, const double *r, double *s, int precision, const E
     } else {
       STST_TRY(time_solve<float>(h, (void *)y32, done, st));
     }
-    if (out32) return launch_fd2d<float2, float2>(y32, (float2 *)out32, h, 1, ed, done, st, S);
-    return launch_fd2d<float2, double2>(y32, (double2 *)s, h, 1, ed, done, st, S);
+    if (out32) return launch_fd2d<float2, float2>(y32, (float2 *)out32, h, 1, ed, done, st, Sb);
+    return launch_fd2d<float2, double2>(y32, (double2 *)s, h, 1, ed, done, st, Sb);
   }
   float2 *bufs[2] = {(float2 *)bufA, (float2 *)bufB};
   int cur = 0;
@@ -1682,7 +1682,7 @@ int fd_partials_count(stst_problem *h) {
   long long ncols = h->N_dof / h->dir[1].n;
   if (h->prec_mode == STST_PREC_BF16) return tc_partials_count(ncols);
   if (h->pencil && h->prec_mode == STST_PREC_FP32 && h->d == 1) return (int)(h->N_s / h->dir[1].n * h->pencil);
-  if (h->fd2d && h->prec_mode == STST_PREC_FP32 && (!h->pencil || h->d == 3)) return (int)(fd2d_slabs(h) * h->fd2d);
+  if (h->fd2d && h->prec_mode == STST_PREC_FP32 && (!h->pencil || h->d == 3)) return (int)(fd2d_slabs(h) * h->fd2d_b);
   if (h->prec_mode == STST_PREC_FP32 && h->mp_cfg[1].tc && h->Utf[1] &&
       tf32_eligible(h->dir[1].n, h->n_t(), ncols / h->n_t(), h->w_t1))
     return tf32_partials_count(h->dir[1].n, h->n_t(), ncols / h->n_t());
@@ -1756,11 +1756,14 @@ static int tune_ts(stst_problem *h) {
 }
 
 // ---- choice between fused and separate 2D transforms (FP32 preconditioner, d = 2) -------------------
-// h->fd2d = number S of CTAs per (t, x_3) slab of the fused kernel, 0 for the separate mode products.
-// Measured (autotune mode 1): a forward plus a backward transform of each variant timed on work
-// vectors, cached per shape. Otherwise S is the smallest split giving two CTAs per SM.
+// h->fd2d = number S of CTAs per (t, x_3) slab of the fused kernel, 0 for the separate mode products;
+// h->fd2d_b the same for the backward transform. Measured (autotune mode 1): a forward plus a backward
+// transform of each variant timed on work vectors decides fused or separate; then, fused, each
+// transform is timed alone per split in the form the solve runs it (forward: FP64 residual in; backward:
+// FP64 out with the flexible CG's four epilogue inner products), and each keeps its fastest split.
+// Cached per shape. Otherwise S is the smallest split giving two CTAs per SM, for both.
 int g_fd2d_mode = 0;  // 0 chosen per shape, 1 separate kernels, 2 fused where it fits, 10 + S fused with split S
-static std::map<std::tuple<int, int, int, int>, int> g_fd2d_cache;  // (n_t, n_1, n_2, n_3 or 0 for d = 2)
+static std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_fd2d_cache;  // (n_t, n_1, n_2, n_3 or 0)
 
 static int fd2d_default_split(const stst_problem *h) {
   int S = 1;
@@ -1769,14 +1772,14 @@ static int fd2d_default_split(const stst_problem *h) {
 }
 
 static int tune_fd2d(stst_problem *h) {
-  h->fd2d = 0;
+  h->fd2d = h->fd2d_b = 0;
   if (h->prec_mode != STST_PREC_FP32 || !fd2d_fits(h) || g_fd2d_mode == 1) return STST_OK;
   if (g_fd2d_mode > 10 && fd2d_split_ok(h->dir[1].n, h->dir[2].n, g_fd2d_mode - 10)) {
-    h->fd2d = g_fd2d_mode - 10;
+    h->fd2d = h->fd2d_b = g_fd2d_mode - 10;
     return STST_OK;
   }
   if (g_fd2d_mode >= 2 || g_tune_enabled != 1) {
-    h->fd2d = fd2d_default_split(h);
+    h->fd2d = h->fd2d_b = fd2d_default_split(h);
     return STST_OK;
   }
   const auto key = std::make_tuple(h->n_t(), h->dir[1].n, h->dir[2].n, h->d == 3 ? h->dir[3].n : 0);
@@ -1784,7 +1787,8 @@ static int tune_fd2d(stst_problem *h) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_fd2d_cache.find(key);
     if (it != g_fd2d_cache.end()) {
-      h->fd2d = it->second;
+      h->fd2d = it->second.first;
+      h->fd2d_b = it->second.second;
       return STST_OK;
     }
   }
@@ -1830,13 +1834,59 @@ static int tune_fd2d(stst_problem *h) {
       choice = S;
     }
   }
+  // fused: each transform alone per split, in the form the solve runs it (the epilogue's inner products
+  // read two FP64 work vectors and write the preconditioner's partial-sum slots, which every solve
+  // recomputes before reading)
+  int choice_b = choice;
+  if (choice > 0 && status == STST_OK) {
+    double2 *D = (double2 *)h->w_t2;
+    STST_CUDA(cudaMemsetAsync(h->w_t2, 0, sizeof(double2) * h->N_dof, st));
+    EpiDot ed;
+    ed.a = h->w_r;
+    ed.b = h->w_q;
+    ed.part = h->partials + PS_Z * STST_MAXPART;
+    ed.cplx = 1;
+    float best_f = 1e30f, best_b = 1e30f;
+    for (int S = 1; S <= FD2D_MAXS && status == STST_OK; ++S) {
+      if (!fd2d_split_ok(h->dir[1].n, h->dir[2].n, S) ||
+          (long long)fd2d_slabs(h) * S > STST_MAXPART)
+        continue;
+      for (int dir = 0; dir < 2 && status == STST_OK; ++dir) {
+        auto run = [&]() -> int {
+          if (dir == 0) return launch_fd2d<double2, float2>(D, X, h, 0, EpiDot(), nullptr, st, S);
+          return launch_fd2d<float2, double2>(X, D, h, 1, ed, nullptr, st, S);
+        };
+        for (int w = 0; w < 2 && status == STST_OK; ++w) status = run();
+        cudaEventRecord(e0, st);
+        for (int w = 0; w < 5 && status == STST_OK; ++w) status = run();
+        cudaEventRecord(e1, st);
+        const cudaError_t es = cudaEventSynchronize(e1);
+        if (es != cudaSuccess) {
+          stst_last_cuda = es;
+          status = STST_ERR_CUDA;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (status != STST_OK) break;
+        if (dir == 0 && ms < best_f) {
+          best_f = ms;
+          choice = S;
+        }
+        if (dir == 1 && ms < best_b) {
+          best_b = ms;
+          choice_b = S;
+        }
+      }
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   STST_TRY(status);
   h->fd2d = choice;
+  h->fd2d_b = choice_b;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_fd2d_cache[key] = choice;
+    g_fd2d_cache[key] = std::make_pair(choice, choice_b);
   }
   return STST_OK;
 }

@@ -1003,6 +1003,13 @@ int stst_fused_transforms_info(stst_handle h, int *fused) {
   return STST_OK;
 }
 
+int stst_fused_transforms_split(stst_handle h, int *forward, int *backward) {
+  STST_TRY(check(h));
+  if (forward) *forward = h->fd2d;
+  if (backward) *backward = h->fd2d ? h->fd2d_b : 0;
+  return STST_OK;
+}
+
 int stst_set_pencil(int mode) {
   if (mode < 0 || mode > 3) return STST_ERR_ARG;
   g_pencil_mode = mode;

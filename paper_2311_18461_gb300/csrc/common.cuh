@@ -209,6 +209,7 @@ struct stst_problem {
   float mp_us[STST_MAXD + 1];      // its measured time per launch (0: not measured)
   int tuned;
   int fd2d;                        // CTAs per slab of the fused transforms (FP32 preconditioner, d = 2 or 3), 0: separate
+  int fd2d_b;                      // CTAs per slab of the fused backward transform (timed apart from the forward one)
   int eig_src[STST_MAXD + 1];
   double *U[STST_MAXD + 1];
   float *U32[STST_MAXD + 1];

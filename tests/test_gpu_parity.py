@@ -423,19 +423,21 @@ def test_fused_2d_transforms_bitwise(n_el, p):
     """The fused transform kernel (the mode products of directions 1 and 2 of Algorithm 1 steps 2 and 4
     in one kernel per (t, x_3) slab; direction 3 separate when d = 3) gives bitwise the same
     preconditioner output as the separate mode-product kernels; PCG with either takes the same
-    iterations (only the order of the dot-product partial sums differs)."""
+    iterations (only the order of the dot-product partial sums differs). Mode 0 lets the tuner choose,
+    which may give the backward transform another split than the forward one."""
     out = {}
     S.stst_set_pencil(1)  # the separate last-direction kernels, so that the fused transforms run for d = 2
     S.stst_set_tensor_products(1)  # the SIMT mode products, which sum in the fused kernel's order
     try:
-        for mode in (1, 2, 11, 12, 13, 14):
+        for mode in (1, 0, 2, 11, 12, 13, 14):
             S.stst_set_fused_transforms(mode)
             prob = S.Problem(len(n_el) - 1, n_el, p, prec_mode=S.STST_PREC_FP32)
             prob.build_fd()
             fused = S.stst_fused_transforms_info(prob.h)
+            split = S.stst_fused_transforms_split(prob.h)
             z = to_np(prob.apply_prec(to_dev(random_complex(prob.n_dof, 31))))
             x, st, it, rr = prob.pcg(to_dev(random_complex(prob.n_dof, 32)), tol=1e-10, maxit=300)
-            out[mode] = (z, fused, st, it, to_np(x))
+            out[mode] = (z, fused, st, it, to_np(x), split)
             prob.close()
     finally:
         S.stst_set_fused_transforms(0)
@@ -443,7 +445,11 @@ def test_fused_2d_transforms_bitwise(n_el, p):
         S.stst_set_tensor_products(0)
     assert out[1][1] == 0 and out[2][1] >= 1 and out[11][1] == 1
     assert all(out[10 + k][1] in (k, out[2][1]) for k in (2, 3, 4))  # the default where k leaves a part empty
+    assert out[1][5] == (0, 0)
     for mode in (2, 11, 12, 13, 14):
+        assert out[mode][5] == (out[mode][1], out[mode][1]), (mode, out[mode][5])
+    assert out[0][5][0] == out[0][1] and (out[0][5] == (0, 0) or 1 <= out[0][5][1] <= 4), out[0][5]
+    for mode in (0, 2, 11, 12, 13, 14):
         assert np.array_equal(out[1][0], out[mode][0]), (mode, out[mode][1])
         assert out[1][2] == 0 and out[mode][2] == 0 and abs(out[1][3] - out[mode][3]) <= 1
         assert rel_err(out[mode][4], out[1][4]) < 1e-8
