@@ -403,6 +403,9 @@ static int pcg_iteration(stst_problem *h, PcgCtl *ctl, T *x, T *r, T *z, T *p, T
     if (flexible) k_update_xr<T, true><<<gu, 256, 0, st>>>(x, r, p, q, ctl, N, pRR, pRP, gu, pPQ, g, pZ, nz);
     else k_update_xr<T, false><<<gu, 256, 0, st>>>(x, r, p, q, ctl, N, pRR, pRP, gu, pPQ, g, pZ, nz);
   }
+  // 1024 threads: each loads at most one of the (at most 2 x 152) partials, so the loads are one L2 round
+  // trip; one warp looping over them measured slower (9.2 against 7.2 us per iteration on the 2D p = 3
+  // 64^2 x 64 solve) despite its fewer FP64 additions
   { STST_PROF("pcg_scalar", st); k_pcg_check<<<1, 1024, 0, st>>>(ctl, pRR, gu, cond, use_cond); }
   // z = P^{-1} r with the epilogue's inner products: <r, z> (plain: real part; flexible: complex, and <z, q>)
   EpiDot ed;
