@@ -66,17 +66,45 @@ def test_host_side_argument_checks_need_no_gpu():
             assert L.stst_set_pencil(mode) == 0, mode
         for mode in (-1, 4):
             assert L.stst_set_pencil(mode) == ERR_ARG, mode
+        for mode in (0, 1, 2):
+            assert L.stst_set_tensor_products(mode) == 0, mode
+        for mode in (-1, 3):
+            assert L.stst_set_tensor_products(mode) == ERR_ARG, mode
+        for mode in (0, 1):
+            assert L.stst_set_fused_matvec(mode) == 0, mode
+        for mode in (-1, 2):
+            assert L.stst_set_fused_matvec(mode) == ERR_ARG, mode
     finally:
         L.stst_set_autotune(1)
         L.stst_set_time_solver(0)
         L.stst_set_fused_transforms(0)
         L.stst_set_pencil(0)
+        L.stst_set_tensor_products(0)
+        L.stst_set_fused_matvec(0)
     n = ctypes.c_longlong()
     assert L.stst_sizes(None, ctypes.byref(n), None) == ERR_HANDLE
     assert L.stst_pcg_graph_info(None, None, None) == ERR_HANDLE
     assert L.stst_build_fd(None) == ERR_HANDLE
     assert L.stst_set_potential(None, 0, None) == ERR_HANDLE
     assert L.stst_pencil_info(None, None) == ERR_HANDLE
+    assert L.stst_fused_transforms_split(None, None, None) == ERR_HANDLE
+    assert L.stst_tensor_products_info(None, None) == ERR_HANDLE
+    assert L.stst_set_geometry(None, None, None) == ERR_HANDLE
+    assert L.stst_geometry_info(None, None, None, None) == ERR_HANDLE
+    # the persistent solver: counts, arrays and cluster sizes are checked before any handle or CUDA call
+    hs = (ctypes.c_void_p * 1)(None)
+    vp = (ctypes.c_void_p * 1)(None)
+    L.stst_persistent_solve.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    ps = L.stst_persistent_solve
+    assert ps(0, hs, vp, vp, 1e-8, 10, 8, None, None, None, None) == ERR_ARG
+    assert ps(1, None, vp, vp, 1e-8, 10, 8, None, None, None, None) == ERR_ARG
+    assert ps(1, hs, vp, vp, -1.0, 10, 8, None, None, None, None) == ERR_ARG
+    assert ps(1, hs, vp, vp, 1e-8, -1, 8, None, None, None, None) == ERR_ARG
+    for bad_cluster in (3, 32, -1):
+        assert ps(1, hs, vp, vp, 1e-8, 10, bad_cluster, None, None, None, None) == ERR_ARG, bad_cluster
+    assert ps(1, hs, vp, vp, 1e-8, 10, 8, None, None, None, None) == ERR_HANDLE
     out = ctypes.c_int()
     bad = [(0, 4, 1.0, 2), (9, 4, 1.0, 2), (2, 0, 1.0, 2), (2, 4, 0.0, 2), (2, 4, -1.0, 1), (2, 4, 1.0, 3),
            (1, 1, 1.0, 2)]  # the last leaves no function after dropping both ends
