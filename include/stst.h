@@ -156,7 +156,8 @@ int stst_set_potential(stst_handle h, int rank, const double *v_qp);
  * Laplacian along l. For an affine map with sides a_l, s_l = 1 / a_l^2 and the scaled P-hat is the box's own
  * preconditioner up to a constant factor; without the scales the parametric P-hat mismatches the
  * operator's time-space balance and PCG needs more iterations the finer the mesh. Setting or removing a
- * geometry marks the preconditioner stale: call stst_build_fd again. jac = NULL removes the geometry. Least-squares formulation without potential only; stst_rhs, stst_rhs_lift and
+ * geometry marks the preconditioner stale: call stst_build_fd again. jac = NULL removes the geometry.
+ * A handle with a geometry cannot join a batch (stst_batch_create: STST_ERR_STATE). Least-squares formulation without potential only; stst_rhs, stst_rhs_lift and
  * stst_rhs_noalloc (parametric integrals) and stst_ir_solve (FP32 mat-vec) return STST_ERR_STATE while a
  * geometry is set: the caller supplies the mapped-domain load vector. Allocates (about
  * 3 N_s (2p+1)^d doubles and three vectors) and synchronizes the handle's stream.
@@ -302,7 +303,8 @@ int stst_ir_solve(stst_handle h, const double *rhs, double *x, double tol, int m
  * stst_build_fd, then PCG as in stst_pcg_solve with its loop as a conditional WHILE node; the
  * branches share nothing, so the GPU runs them concurrently. Handles must be distinct and must not
  * be used by other calls while a batch solve runs. stream: NULL creates a stream for the batch.
- * Allocates; the handles keep their own workspaces.
+ * Allocates; the handles keep their own workspaces. STST_ERR_STATE for a handle with a geometry
+ * (stst_set_geometry): mapped-domain problems are solved one at a time.
  * stst_batch_solve: one graph launch solving every problem to ||rhs - A x|| <= tol ||rhs|| within
  * maxit iterations; waits for completion. iters, relres, status (host arrays of length count, may be
  * NULL) receive each problem's outcome; the return value is STST_OK or the first non-OK status.

@@ -163,6 +163,7 @@ extern "C" int stst_batch_create(stst_batch *out, int count, const stst_handle *
     if (!rhs[i] || !x[i]) return STST_ERR_ARG;
     for (int j = 0; j < i; ++j)
       if (handles[j] == handles[i]) return STST_ERR_ARG;  // one branch per handle (buffers are per handle)
+    if (handles[i]->geo) return STST_ERR_STATE;  // mapped-domain handles are solved one at a time
   }
   stst_batch_s *b = new (std::nothrow) stst_batch_s();
   if (!b) return STST_ERR_OOM;

@@ -141,6 +141,12 @@ def test_geometry_states_and_errors():
     with pytest.raises(S.StstError) as e:
         prob.rhs(f, None)
     assert e.value.status == S.STST_ERR_STATE
+    # nor does it join a batch (refused before any device work)
+    bb = torch.zeros(prob.n_dof, dtype=torch.complex128, device="cuda")
+    xx = torch.zeros(prob.n_dof, dtype=torch.complex128, device="cuda")
+    with pytest.raises(S.StstError) as e:
+        S.stst_batch_create([prob.h], [bb], [xx])
+    assert e.value.status == S.STST_ERR_STATE
     prob.close()
     # a handle with a potential, or the ultraweak formulation, refuses a geometry
     prob = S.Problem(2, n_el, p)
