@@ -422,8 +422,8 @@ int stst_set_fused_matvec(int mode);
  * (may be NULL). Uses the handles' work vectors, synchronizes their streams, launches on `stream`
  * (NULL: the first handle's stream), allocates and frees about 7 KB per problem, and returns when the
  * solves are done: the largest per-problem status (STST_OK, STST_NOT_CONVERGED, STST_BREAKDOWN), or
- * STST_ERR_ARG / STST_ERR_HANDLE / STST_ERR_STATE (a handle not built, not FP64, with a geometry, or a
- * plan of more than four levels) / STST_ERR_CUDA. Results equal stst_pcg_solve's up to rounding (its
+ * STST_ERR_ARG / STST_ERR_HANDLE / STST_ERR_STATE (a handle not built, not FP64, with a geometry, with a
+ * degree above 4, or with a plan of more than four levels) / STST_ERR_CUDA. Results equal stst_pcg_solve's up to rounding (its
  * sums run in another order).
  */
 int stst_persistent_solve(int count, const stst_handle *handles, const double *const *rhs, double *const *x,
